@@ -1,0 +1,89 @@
+"""Named workloads: sketch geometry plus the synthetic traffic that drives it.
+
+Geometry symbols follow the paper: ``u`` rows and ``v`` columns of sliding estimators
+(Section 4.1), ``g`` SRE cells and ``gl`` (the paper's g') SLE cells per estimator, ``z``-bit
+distance recorders stored in ``dr_bytes`` bytes, window ``k`` slices (Section 3.1) and
+threshold ``theta`` (Definition 2).  ``gl`` is the per-row SLE size divided by ``v``.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+from .traces import TrafficSpec
+
+
+@dataclasses.dataclass(frozen=True)
+class Workload:
+    name: str
+    u: int
+    v: int
+    g: int
+    gl: int
+    dr_bytes: int
+    z: int
+    k: int
+    theta: int
+    n_slices: int
+    traffic: TrafficSpec
+    hash_seed: int = 1
+    start_slice: int = 0
+    max_sampled: int = 1 << 16
+    max_candidates: int = 1 << 14
+
+    @property
+    def pkts_per_slice(self) -> int:
+        return self.traffic.pkts_per_slice
+
+    def replace(self, **kw) -> "Workload":
+        tkw = {k: kw.pop(k) for k in list(kw) if k in TrafficSpec.__dataclass_fields__}
+        w = dataclasses.replace(self, **kw)
+        if tkw:
+            w = dataclasses.replace(w, traffic=dataclasses.replace(w.traffic, **tkw))
+        return w
+
+
+# 1 link, 16 slices of 2^16 packets, window 4 slices, 8-bit recorders.
+TINY = Workload(
+    name="tiny-1link-u4-v1024-g64-gl64-z8-k4",
+    u=4, v=1 << 10, g=64, gl=64, dr_bytes=1, z=8, k=4, theta=1024, n_slices=16,
+    traffic=TrafficSpec(
+        seed=1, pkts_per_slice=1 << 16, n_src=1 << 12, zipf_s=1.1,
+        dst_model="uniform", dst_space=1 << 20,
+        n_planted=20, planted_card=(500, 3000), planted_card_dist="uniform",
+        planted_spread=16),
+    max_sampled=1 << 14, max_candidates=1 << 13,
+)
+
+# Paper-scale single link: 1 s slices, window 300 slices, ~5M packets per slice.
+PAPER = Workload(
+    name="paper-1link-u8-v16384-g128-gl256-z16-k300-5Mpps",
+    u=8, v=1 << 14, g=128, gl=256, dr_bytes=2, z=16, k=300, theta=1024, n_slices=320,
+    traffic=TrafficSpec(
+        seed=2, pkts_per_slice=5_000_000, n_src=1 << 20, zipf_s=1.2,
+        dst_model="pool", pool_alpha=1.5, pool_max=128,
+        n_planted=500, planted_card=(1 << 10, 1 << 16), planted_card_dist="loguniform",
+        planted_spread=300, churn_frac=0.3, churn_run=(75, 300)),
+    max_sampled=1 << 20, max_candidates=1 << 18,
+)
+
+# Long-window stress: window 1024 slices, 2M packets per slice, stamp wraparound,
+# one heavy source with 10% of the packets, a flood of 2^24 spoofed one-packet sources
+# spread over 16 slices.
+LONGWIN = Workload(
+    name="longwin-1link-u8-v16384-g128-gl256-z16-k1024-2Mpps-flood",
+    u=8, v=1 << 14, g=128, gl=256, dr_bytes=2, z=16, k=1024, theta=1024, n_slices=1040,
+    traffic=TrafficSpec(
+        seed=3, pkts_per_slice=2_000_000, n_src=1 << 20, zipf_s=1.2,
+        dst_model="pool", pool_alpha=1.5, pool_max=128,
+        n_planted=500, planted_card=(1 << 10, 1 << 16), planted_card_dist="loguniform",
+        planted_spread=1024, churn_frac=0.3, churn_run=(256, 1024),
+        heavy_frac=0.10, flood_sources=1 << 24, flood_slices=(4, 20)),
+    start_slice=(1 << 16) - 1 - 8,
+    max_sampled=1 << 21, max_candidates=1 << 20,
+)
+
+WORKLOADS = {"tiny": TINY, "paper": PAPER, "longwin": LONGWIN}
+
+
+def workload(name: str) -> Workload:
+    return WORKLOADS[name]

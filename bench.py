@@ -1,0 +1,351 @@
+"""Benchmark of the SRLA hot path (per-packet scan + end-of-slice pass) on B300.
+
+A step is one slice of the paper-scale single-link workload: push ~5M (aip, bip) packets
+that are already resident in HBM, close the slice, fetch its report.  The window is first
+filled with k slices (steady state), then W warm-up steps, then K timed steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload paper] [--impl srla|reference]
+
+Prints one JSON line (rank 0).  Under torchrun (N > 1) each rank runs an independent link
+on its own GPU (replicas: links shard without any exchange); the timed region is bracketed
+by barriers and the max over ranks is taken.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpkts/s scanned into SRE+SLE; p50/p99 slice-end-to-report latency (ms)"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="paper")
+    ap.add_argument("--impl", default="srla", choices=["srla", "reference"])
+    ap.add_argument("--prefill", type=int, default=-1, help="slices before warm-up (-1: the window k)")
+    ap.add_argument("--latency-slices", type=int, default=100)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def _algorithmic_bytes_per_pkt(w, tau):
+    """Bytes the scan must move per packet: the 8-byte pair, u SLE recorders, u SRE recorders
+    for the 2^-tau sampled share, and a 4-byte sampled-host record for that share."""
+    s = 2.0 ** -tau
+    return 8.0 + w.u * w.dr_bytes + s * w.u * w.dr_bytes + s * 4.0
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                out = ""
+            self.lines = [l for l in out.splitlines() if l.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in getattr(self, "lines", []):
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _cpu_info():
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for l in f:
+                if l.startswith("model name"):
+                    model = l.split(":", 1)[1].strip()
+                    break
+    except Exception:
+        pass
+    return os.cpu_count(), model
+
+
+def run_oracle(w, steps, warmup, device_for_gen=None, seconds=None):
+    """The CPU oracle on the workload's slices from an empty array: Mpkts/s of scan + slice end.
+    Either a fixed number of steps (after warm-up) or as many slices as fit in `seconds`."""
+    import oracle
+    import synth
+
+    ha, hb = synth.hash_coefficients(w.hash_seed, w.u + 3)
+    o = oracle.Oracle.for_workload(w, ha, hb)
+    pk_total, t_total, s, timed = 0, 0.0, 0, 0
+    while True:
+        pk = synth.pairs_to_numpy(synth.generate_slice(w.traffic, s, device=device_for_gen or "cpu"))
+        t0 = time.perf_counter()
+        o.push(pk)
+        o.end_slice()
+        dt = time.perf_counter() - t0
+        if s >= warmup:
+            pk_total += pk.shape[0]
+            t_total += dt
+            timed += 1
+        s += 1
+        if seconds is not None and s >= warmup + 2 and t_total >= seconds:
+            break
+        if seconds is None and timed >= steps:
+            break
+    o.close()
+    return pk_total / t_total / 1e6, timed, pk_total, t_total
+
+
+def bench_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return
+    import synth
+
+    w = synth.workload(args.workload)
+    dev = "cuda" if _cuda_ok() else "cpu"
+    mpps, timed, pk, secs = run_oracle(w, args.steps, args.warmup, device_for_gen=dev)
+    cores, model = _cpu_info()
+    sample = (f"{args.workload}: slices {args.warmup}..{args.warmup + timed - 1} of the seeded trace from an empty "
+              f"array, full {w.pkts_per_slice} packets per slice, scan + slice end; CPU {model}")
+    line = {"impl": "reference", "metric": METRIC, "value": round(mpps, 4), "unit": "Mpkts/s", "n_gpus": args.gpus,
+            "steps": timed, "warmup": args.warmup, "ms_per_step": round(1e3 * secs / max(timed, 1), 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config(w),
+            "cpu_baseline": {"value": round(mpps, 4), "unit": "Mpkts/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(mpps, 4), "unit": "Mpkts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _cuda_ok():
+    try:
+        import torch
+
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def _config(w):
+    return {"workload": w.name, "u": w.u, "v": w.v, "g": w.g, "gl": w.gl, "dr_bits": w.z, "dr_bytes": w.dr_bytes,
+            "k": w.k, "theta": w.theta, "pkts_per_slice": w.pkts_per_slice, "links": 1,
+            "l2": "inputs distinct per step (K x 8 B x pkts/slice > L2); the sketch stays resident by design"}
+
+
+def bench_srla(args):
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1803_10369_b300 import srla
+
+    rank, world, local = _dist()
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.workload(args.workload)
+    # each rank monitors its own link: a different trace seed per rank
+    spec = w.traffic if rank == 0 else w.replace(seed=w.traffic.seed + 1000 * rank).traffic
+    ha, hb = synth.hash_coefficients(w.hash_seed, w.u + 3)
+    params = srla.params_for(w, ha, hb, staging_pkts=w.pkts_per_slice)
+    tau, rho_g, P = srla.derived(params)
+    stream = torch.cuda.Stream(dev)
+    link = srla.Link(params, device=dev, stream=stream)
+
+    prefill = w.k if args.prefill < 0 else args.prefill
+    K, W = args.steps, args.warmup
+    # inputs of the timed steps, resident in HBM before timing starts
+    with torch.cuda.stream(stream):
+        batches = [synth.generate_slice(spec, prefill + W + i, device=dev) for i in range(K)]
+        for s in range(prefill + W):
+            pk = synth.generate_slice(spec, s, device=dev)
+            link.push(pk)
+            link.report(link.end_slice())
+    torch.cuda.synchronize(dev)
+    pkts = sum(int(b.shape[0]) for b in batches)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- device-timed throughput: K pipelined steps (report of slice t fetched after t+1 is queued)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    scan_ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    launches0 = link.kernel_launches()
+    barrier()
+    torch.cuda.synchronize(dev)
+    uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", local))
+    smi_id = uuid if uuid.startswith("GPU-") or not uuid[:1].isalnum() or len(uuid) < 30 else "GPU-" + uuid
+    with Clocks(smi_id) as clk:
+        ev[0].record(stream)
+        pending = None
+        for i in range(K):
+            scan_ev[i][0].record(stream)
+            link.push(batches[i])
+            scan_ev[i][1].record(stream)
+            sid = link.end_slice()
+            if pending is not None:
+                link.report(pending)
+            pending = sid
+        ev[1].record(stream)
+        link.report(pending)
+        torch.cuda.synchronize(dev)
+    launches = link.kernel_launches() - launches0
+    barrier()
+    elapsed_ms = ev[0].elapsed_time(ev[1])
+    scan_ms = [a.elapsed_time(b) for a, b in scan_ev]
+    if world > 1:
+        t = torch.tensor([elapsed_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_pkts = pkts * world
+    value = total_pkts / (elapsed_ms * 1e-3) / 1e6
+
+    # ---- latency: slice end -> report, with the slice's scan already complete
+    lat = []
+    n_lat = max(args.latency_slices, K)
+    for i in range(n_lat):
+        link.push(batches[i % K])
+        stream.synchronize()
+        t0 = time.perf_counter()
+        sid = link.end_slice()
+        link.report(sid)
+        lat.append((time.perf_counter() - t0) * 1e3)
+    lat.sort()
+    p50 = lat[len(lat) // 2]
+    p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
+
+    # ---- end to end through the public API with host buffers (pinned), H2D inside the timed region
+    host = [b.cpu().pin_memory() for b in batches]
+    d2h = []
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    pending = None
+    for i in range(K):
+        link.push(host[i])
+        sid = link.end_slice()
+        if pending is not None:
+            r = link.report(pending)
+            d2h.append(64 + 16 * len(r["aip"]))
+        pending = sid
+    r = link.report(pending)
+    d2h.append(64 + 16 * len(r["aip"]))
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = total_pkts / e2e_s / 1e6
+
+    peak, peak_kind = _peaks()
+    bpp = _algorithmic_bytes_per_pkt(w, tau)
+    scan_avg_ms = statistics.mean(scan_ms)
+    per_launch_pkts = pkts / K
+    achieved = bpp * per_launch_pkts / (scan_avg_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": round(value, 3), "unit": "Mpkts/s", "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": round(elapsed_ms / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u16" if w.dr_bytes == 2 else "u8", "data": "synthetic", "config": _config(w),
+        "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "slices": n_lat},
+        "scan_mpkts_s": round(per_launch_pkts / (scan_avg_ms * 1e-3) / 1e6, 3),
+        "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                     "frac": round(achieved / peak, 5), "traffic": None, "kernel": "k_scan",
+                     "bytes_per_pkt": bpp, "peak_kind": peak_kind},
+        "e2e": {"value": round(e2e, 3), "unit": "Mpkts/s", "h2d_bytes_per_step": int(8 * per_launch_pkts),
+                "d2h_bytes_per_step": int(statistics.mean(d2h))},
+        "gpu_launches": int(launches),
+        "clocks": clk.summary(),
+        "prefill_slices": prefill,
+    }
+    link.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        mpps, timed, pk, secs = run_oracle(w, 0, 0, device_for_gen=dev, seconds=args.cpu_seconds)
+        cores, model = _cpu_info()
+        line["cpu_baseline"] = {"value": round(mpps, 4), "unit": "Mpkts/s", "cores": 1, "kind": "oracle",
+                                "sample": f"{timed} full slices ({pk} packets) of {w.name} from an empty array, "
+                                          f"scan + slice end, single thread on {model} ({cores} host cores)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        bench_reference(args)
+    else:
+        bench_srla(args)
+
+
+if __name__ == "__main__":
+    main()

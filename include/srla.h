@@ -1,0 +1,171 @@
+/*
+ * libsrla -- sliding-window super point cardinality estimation (SRLA, arXiv 1803.10369)
+ * on one B300 GPU (sm_103a).  C ABI: plain pointers and sizes, no C++ or torch types.
+ *
+ * One handle estimates one monitored link (one sliding estimator array, Section 4.1).
+ * The caller pushes the link's IP pairs slice by slice and closes every slice; the library
+ * answers with the sorted list of candidate super points of the window that ends with that
+ * slice, each with its union-SLE weight, its cardinality estimate (Eq. 9) and flags.
+ *
+ * Conventions for every entry point:
+ *   - the return value is 0 on success or a negative SRLA_E_* code; nothing aborts, traps
+ *     or throws across the ABI;
+ *   - the library never allocates device memory: the caller provides one workspace of
+ *     srla_workspace_bytes() bytes (for instance a torch tensor) that holds the sketches,
+ *     the per-slice buffers and all scratch space, and keeps it alive until srla_destroy;
+ *   - all device work is enqueued on the CUDA stream given to srla_create, in order;
+ *   - a handle is used by one host thread at a time.
+ */
+#ifndef SRLA_H
+#define SRLA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SRLA_MAX_ROWS 16            /* u <= 16 */
+#define SRLA_N_HASH (SRLA_MAX_ROWS + 3)
+
+/* Error codes. */
+#define SRLA_OK 0
+#define SRLA_E_INVAL (-1)           /* invalid parameter or argument */
+#define SRLA_E_NOMEM (-2)           /* workspace too small, or host memory exhausted */
+#define SRLA_E_CAPACITY (-3)        /* a per-slice capacity was exceeded; results incomplete */
+#define SRLA_E_CUDA (-4)            /* a CUDA runtime call failed */
+#define SRLA_E_ORDER (-5)           /* call out of order (see each entry point) */
+#define SRLA_E_TIMEOUT (-6)         /* a bounded device wait gave up */
+
+/* Report flags. */
+#define SRLA_SUPER 1u               /* estimate >= theta (Definition 2), or saturated */
+#define SRLA_SATURATED 2u           /* every union SLE cell in the window: estimate is +inf */
+#define SRLA_CARRIED 4u             /* carried from the previous slice end (Algorithm 3) */
+#define SRLA_NEW 8u                 /* sampled in this slice and passing the union SRE test */
+
+/*
+ * Parameters (Sections 3.2, 4.1, 5).  v, g and gl must be powers of two.
+ *   u, v        rows and columns of the sliding estimator array (u <= SRLA_MAX_ROWS)
+ *   g, gl       distance recorders per SRE and per SLE (the paper's g and g')
+ *   dr_bytes    bytes that hold one recorder: 1 or 2
+ *   z           recorder bits, 1 <= z <= 8 * dr_bytes; the largest distance is 2^z - 1
+ *   k           window length in slices, 1 <= k <= 2^z - 1 (Section 3.2)
+ *   theta       super point threshold, >= 1 (Definition 2)
+ *   start_slice index of the first open slice
+ *   staging_pkts  packets the host-input staging area holds (0: 2^20)
+ *   max_sampled   distinct hosts sampled into the SRE per slice
+ *   max_candidates  candidate list entries per slice (new + carried)
+ *   hash_a, hash_b  coefficients of the hash family h(x) = (a*x + b) mod (2^61 - 1), one
+ *               pair per role: rows 0..u-1 (column of aip in row i), u (SLE cell of bip),
+ *               u+1 (SRE cell of bip), u+2 (sampling hash of bip); a in [1, 2^61-2],
+ *               b in [0, 2^61-2].  The paper leaves the family open (Section 3.2).
+ * Sizes: v*g*dr_bytes and v*gl*dr_bytes are at least 16 bytes.
+ */
+typedef struct srla_params {
+  uint32_t u, v, g, gl;
+  uint32_t dr_bytes, z, k, theta;
+  uint64_t start_slice;
+  uint64_t staging_pkts;
+  uint32_t max_sampled, max_candidates;
+  uint64_t hash_a[SRLA_N_HASH];
+  uint64_t hash_b[SRLA_N_HASH];
+} srla_params;
+
+/* One report line: a candidate super point of the window ending with the reported slice. */
+typedef struct srla_entry {
+  uint32_t aip;    /* the host */
+  uint32_t w;      /* |ULE(aip)|^k: union SLE recorders inside the window (Algorithm 1) */
+  float est;       /* Eq. 9 estimate of |OP(aip, t, k)|, FP32 (+inf when saturated) */
+  uint32_t flags;  /* SRLA_SUPER | SRLA_SATURATED | SRLA_CARRIED | SRLA_NEW */
+} srla_entry;
+
+/* Per-slice figures returned with a report. */
+typedef struct srla_slice_stats {
+  uint64_t slice;            /* index of the reported slice */
+  uint64_t n_pkts;           /* packets pushed into it */
+  uint32_t n_sampled;        /* distinct hosts with a pair sampled into the SRE */
+  uint32_t n_new;            /* of which passed the union SRE test */
+  uint32_t n_candidates;     /* report length (new and carried, de-duplicated) */
+  uint32_t n_carry_out;      /* hosts carried into the next slice (Algorithm 3) */
+  uint32_t w_star;           /* least w whose estimate is >= theta (gl + 1 if none) */
+  uint32_t overflow;         /* bit 0: max_sampled exceeded; bit 1: max_candidates exceeded */
+  double up;                 /* UP of Eq. 8 */
+  uint64_t census[SRLA_MAX_ROWS]; /* |LDR(i)|^k of Section 4.2, per row */
+} srla_slice_stats;
+
+typedef struct srla_s srla_t;
+
+/* Validate parameters: 0 or SRLA_E_INVAL.  No GPU needed. */
+int srla_check_params(const srla_params *p);
+
+/* Workspace bytes needed for p (0 when p is invalid).  No GPU needed. */
+size_t srla_workspace_bytes(const srla_params *p);
+
+/* Values derived from p by the paper's formulas (no GPU needed): tau of Eq. 1,
+ * ceil(rho*g) with rho = 0.99 (1 - e^{-1/3}) (Section 3.2), and the stamp modulus 2^z - 1. */
+int srla_derived(const srla_params *p, uint32_t *tau, uint32_t *rho_g, uint32_t *stamp_mod);
+
+/*
+ * Create an estimator on the current CUDA device.
+ *   dev_workspace: device pointer, 256-byte aligned, ws_bytes >= srla_workspace_bytes(p);
+ *                  owned by the caller, must outlive the handle.
+ *   stream: a cudaStream_t (NULL = legacy default stream).
+ * All recorders start empty (DRinit, Section 3.2).  Errors: INVAL, NOMEM, CUDA.
+ */
+int srla_create(const srla_params *p, void *dev_workspace, size_t ws_bytes, void *stream,
+                srla_t **out);
+
+/*
+ * Scan n_pairs IP pairs into the open slice (Algorithm 2).  pairs holds 2*n_pairs uint32,
+ * interleaved aip, bip.  on_device = 1: pairs is device memory, read by kernels on the
+ * stream; the caller keeps it unchanged until the stream passes this call (for instance
+ * until srla_report or srla_sync returns).  on_device = 0: pairs is host memory (pinned
+ * memory gives an asynchronous copy); it is copied through the staging area and must stay
+ * unchanged until srla_sync or the next srla_report returns.  n_pairs = 0 is a no-op.
+ * Errors: INVAL, CUDA.
+ */
+int srla_push_packets(srla_t *h, const uint32_t *pairs, uint64_t n_pairs, int on_device);
+
+/*
+ * Close the open slice: row census (Section 4.2), Eq. 8, candidate list, Eq. 9 estimates,
+ * the slide and carry of Algorithm 3.  Asynchronous; *slice_id receives the closed slice's
+ * index and the next slice opens.  Errors: CUDA.
+ */
+int srla_end_slice(srla_t *h, uint64_t *slice_id);
+
+/*
+ * Wait for the report of slice_id and copy it: entries sorted by ascending aip.  The two
+ * most recently closed slices can be reported; older ones give SRLA_E_ORDER.  Up to cap
+ * entries are written to out (out may be NULL when cap is 0); *n_out receives the full
+ * count.  stats may be NULL.  Returns SRLA_E_CAPACITY when a per-slice capacity overflowed
+ * (the entries are then those that fit), SRLA_E_NOMEM when cap < *n_out.
+ */
+int srla_report(srla_t *h, uint64_t slice_id, srla_entry *out, size_t cap, size_t *n_out,
+                srla_slice_stats *stats);
+
+/* Block until all work enqueued by this handle has finished. */
+int srla_sync(srla_t *h);
+
+/*
+ * Checkpoint.  The state is the recorder distances (uint16 each, the paper's DR values,
+ * 2^z - 1 = empty), the open slice index and the carried host list, in a self-describing
+ * host buffer of srla_state_bytes() bytes.  Export and import are only allowed at a slice
+ * boundary (no packets pushed into the open slice), else SRLA_E_ORDER.  Import checks that
+ * the geometry matches (SRLA_E_INVAL otherwise).
+ */
+size_t srla_state_bytes(const srla_t *h);
+int srla_export_state(srla_t *h, void *host_buf, size_t cap);
+int srla_import_state(srla_t *h, const void *host_buf, size_t len);
+
+/* Number of CUDA kernels this handle has launched since srla_create (all entry points). */
+uint64_t srla_kernel_launches(const srla_t *h);
+
+void srla_destroy(srla_t *h);
+const char *srla_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SRLA_H */

@@ -197,12 +197,13 @@ int orc_push(orc *o, const uint32_t *pairs, size_t n) {
 
 /* |URE(aip)|^k of Algorithm 1 (R3): SRE cells whose joined distance is below `limit`. */
 uint32_t orc_ure_count(const orc *o, uint32_t aip, uint32_t limit) {
+  uint32_t col[ORC_MAX_ROWS];
+  for (uint32_t i = 0; i < o->u; i++) col[i] = orc_hash(o, (int)i, aip) & (o->v - 1);
   uint32_t cnt = 0;
   for (uint32_t j = 0; j < o->g; j++) {
     uint32_t joined = 0; /* identity of max */
     for (uint32_t i = 0; i < o->u; i++) {
-      uint32_t c = orc_hash(o, (int)i, aip) & (o->v - 1);
-      uint32_t d = o->re[re_at(o, i, c, j)];
+      uint32_t d = o->re[re_at(o, i, col[i], j)];
       if (d > joined) joined = d; /* DRjoin */
     }
     if (joined < limit) cnt++;
@@ -212,12 +213,13 @@ uint32_t orc_ure_count(const orc *o, uint32_t aip, uint32_t limit) {
 
 /* |ULE(aip)|^k of Algorithm 1 (R3). */
 uint32_t orc_ule_count(const orc *o, uint32_t aip, uint32_t limit) {
+  uint32_t col[ORC_MAX_ROWS];
+  for (uint32_t i = 0; i < o->u; i++) col[i] = orc_hash(o, (int)i, aip) & (o->v - 1);
   uint32_t cnt = 0;
   for (uint32_t j = 0; j < o->gl; j++) {
     uint32_t joined = 0;
     for (uint32_t i = 0; i < o->u; i++) {
-      uint32_t c = orc_hash(o, (int)i, aip) & (o->v - 1);
-      uint32_t d = o->le[le_at(o, i, c, j)];
+      uint32_t d = o->le[le_at(o, i, col[i], j)];
       if (d > joined) joined = d;
     }
     if (joined < limit) cnt++;

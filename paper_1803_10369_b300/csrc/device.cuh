@@ -1,0 +1,215 @@
+// Device-side building blocks of libsrla: recorder stamps, the hash family, the slice
+// control block and the open-addressing host sets used to de-duplicate candidates.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "srla.h"
+
+namespace srla {
+
+constexpr uint64_t kP61 = (1ull << 61) - 1;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+// Hash coefficients, one (a, b) per role: rows 0..u-1, SLE cell, SRE cell, sampling.
+struct Coef {
+  uint64_t a[SRLA_N_HASH];
+  uint64_t b[SRLA_N_HASH];
+};
+
+// Geometry and per-handle constants, passed by value to every kernel.
+struct Geo {
+  uint32_t u, v, g, gl;          // rows, columns, SRE and SLE recorders per estimator
+  uint32_t vmask, gmask, glmask;  // v-1, g-1, gl-1
+  uint32_t k;                     // window in slices
+  uint32_t P;                     // stamp modulus 2^z - 1 (= the paper's "too old" distance)
+  uint32_t samp_mask;             // LSB(h) >= tau  <=>  (h & samp_mask) == 0
+  uint32_t rho_g;                 // ceil(rho * g)
+  uint32_t theta;
+};
+
+// Slice control block, resident in the workspace.  Kernels read the open slice from here,
+// so a captured launch sequence stays valid from slice to slice.
+struct Ctl {
+  unsigned long long T;           // open slice index
+  unsigned int tm;                // T mod P
+  unsigned int w_star;            // least w with estimate >= theta (gl + 1 if none)
+  unsigned int n_sampled;         // distinct sampled hosts appended in the open slice
+  unsigned int n_new;             // of which passed the union SRE test
+  unsigned int cat_count[2];      // candidate list length, by slice parity
+  unsigned int overflow;          // SRLA overflow bits of the open slice
+  unsigned int overflow_next;     // overflow bits raised for the next slice (carry list)
+  double up;                      // Eq. 8 of the open slice
+  unsigned long long census[SRLA_MAX_ROWS];
+};
+
+// ---------------------------------------------------------------------------- hashing
+
+// One member of the polynomial family, h(x) = (a*x + b) mod (2^61 - 1), low 32 bits.
+// a < 2^61 is split as a = ah*2^32 + al so that every product fits in 64 bits:
+//   a*x = (ah*x)*2^32 + al*x, and 2^61 = 1 (mod 2^61 - 1).
+__device__ __forceinline__ uint32_t hash61(uint64_t a, uint64_t b, uint32_t x) {
+  const uint64_t lo = (uint64_t)(uint32_t)a * x;  // < 2^64
+  const uint64_t hi = (a >> 32) * x;              // < 2^61
+  uint64_t r = (lo & kP61) + (lo >> 61) + (hi >> 29) + ((hi & 0x1FFFFFFFull) << 32) + b;
+  r = (r & kP61) + (r >> 61);
+  r = (r >= kP61) ? r - kP61 : r;
+  return (uint32_t)r;
+}
+
+// ------------------------------------------------------------------- recorder stamps
+//
+// A recorder holds the paper's distance d in [0, P] (Section 3.2) as a stamp code:
+// 0 = empty (d = P); otherwise 1 + (slice of the last DRset mod P).  At open slice T with
+// tm = T mod P, a code c != 0 has age d = (tm - (c - 1)) mod P.  The sweep at each slice
+// end clears the codes whose age would reach P, so ages never alias.
+
+__device__ __forceinline__ uint32_t stamp_age(uint32_t c, uint32_t tm, uint32_t P) {
+  int age = (int)tm - (int)c + 1;
+  age += (age < 0) ? (int)P : 0;
+  return (uint32_t)age;
+}
+
+__device__ __forceinline__ bool in_window(uint32_t c, uint32_t tm, uint32_t P, uint32_t lim) {
+  return c != 0 && stamp_age(c, tm, P) < lim;
+}
+
+// Bit q set iff cell q of a 32-bit word of cells is inside the window (age < lim).
+template <typename CellT>
+__device__ __forceinline__ uint32_t window_bits(uint32_t word, uint32_t tm, uint32_t P, uint32_t lim) {
+  constexpr int kCells = 4 / (int)sizeof(CellT);
+  constexpr int kBits = 8 * (int)sizeof(CellT);
+  constexpr uint32_t kMask = (kBits == 32) ? 0xFFFFFFFFu : ((1u << kBits) - 1);
+  uint32_t bits = 0;
+#pragma unroll
+  for (int q = 0; q < kCells; q++) {
+    const uint32_t c = (word >> (q * kBits)) & kMask;
+    bits |= (uint32_t)in_window(c, tm, P, lim) << q;
+  }
+  return bits;
+}
+
+// ------------------------------------------------------------------------- host sets
+//
+// Open addressing with linear probing over 64-bit slots (tag << 32 | key).  A slot whose
+// tag is not the current slice's tag counts as empty, so the tables never need clearing
+// between slices (the host clears them when the 31-bit slice tag wraps).
+
+__device__ __forceinline__ uint32_t slice_tag(unsigned long long T) {
+  return ((uint32_t)T & 0x7FFFFFFFu) | 0x80000000u;
+}
+
+__device__ __forceinline__ uint32_t slot_hash(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7FEB352Du;
+  x ^= x >> 15;
+  x *= 0x846CA68Bu;
+  x ^= x >> 16;
+  return x;
+}
+
+// Insert key with tag, or find it.  Returns 1 (inserted), 0 (present) or -1 (no free slot
+// within the probe bound).  Every failed CAS turns a stale slot current, and a current
+// slot never changes within a slice, so the loop is bounded by twice the capacity.
+__device__ __forceinline__ int set_insert(unsigned long long* tab, uint32_t mask, uint32_t tag,
+                                          uint32_t key, uint32_t* slot_out) {
+  const unsigned long long want = ((unsigned long long)tag << 32) | key;
+  uint32_t s = slot_hash(key) & mask;
+  unsigned long long cur = tab[s];
+  const uint32_t limit = 2u * mask + 4u;
+  for (uint32_t it = 0; it < limit; it++) {
+    if ((uint32_t)(cur >> 32) == tag) {
+      if ((uint32_t)cur == key) {
+        *slot_out = s;
+        return 0;
+      }
+      s = (s + 1) & mask;
+      cur = tab[s];
+      continue;
+    }
+    const unsigned long long old = atomicCAS(tab + s, cur, want);
+    if (old == cur) {
+      *slot_out = s;
+      return 1;
+    }
+    cur = old;
+  }
+  return -1;
+}
+
+// Find key with tag; returns the slot or 0xFFFFFFFF.
+__device__ __forceinline__ uint32_t set_find(const unsigned long long* tab, uint32_t mask, uint32_t tag,
+                                             uint32_t key) {
+  uint32_t s = slot_hash(key) & mask;
+  for (uint32_t it = 0; it <= mask; it++) {
+    const unsigned long long cur = tab[s];
+    if ((uint32_t)(cur >> 32) != tag) return 0xFFFFFFFFu;
+    if ((uint32_t)cur == key) return s;
+    s = (s + 1) & mask;
+  }
+  return 0xFFFFFFFFu;
+}
+
+// ------------------------------------------------------------------------ warp sums
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(kFull, x, o);
+  return x;
+}
+
+// |U(aip)|^lim of Algorithm 1 over one recorder array (SRE or SLE): the number of cells j
+// whose recorder is inside the window in every row i, i.e. whose DRjoin (max) over the u
+// rows is below lim.  One warp per host; lane i < u holds the column of row i in `mycol`.
+// Every lane runs the same number of trips (the shuffles need the whole warp).
+template <typename CellT, int WPL>
+__device__ __forceinline__ uint32_t union_count_w(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
+                                                  uint32_t u, uint32_t mycol, uint32_t tm, uint32_t P,
+                                                  uint32_t lim, int lane) {
+  const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;  // 32-bit words per run
+  const uint32_t trips = (R + 32u * WPL - 1) / (32u * WPL);
+  uint32_t total = 0;
+  for (uint32_t t = 0; t < trips; t++) {
+    const uint32_t w0 = (t * 32u + (uint32_t)lane) * WPL;
+    const bool ok = w0 < R;
+    uint32_t m[WPL];
+#pragma unroll
+    for (int q = 0; q < WPL; q++) m[q] = 0xFFFFFFFFu;
+    for (uint32_t i = 0; i < u; i++) {
+      const uint32_t c = __shfl_sync(kFull, mycol, (int)i);
+      const uint32_t* run = reinterpret_cast<const uint32_t*>(arr + ((size_t)i * v + c) * cells);
+      if (ok) {
+        uint32_t wd[WPL];
+        if constexpr (WPL == 4) {
+          const uint4 q4 = __ldg(reinterpret_cast<const uint4*>(run + w0));
+          wd[0] = q4.x; wd[1] = q4.y; wd[2] = q4.z; wd[3] = q4.w;
+        } else if constexpr (WPL == 2) {
+          const uint2 q2 = __ldg(reinterpret_cast<const uint2*>(run + w0));
+          wd[0] = q2.x; wd[1] = q2.y;
+        } else {
+          wd[0] = __ldg(run + w0);
+        }
+#pragma unroll
+        for (int q = 0; q < WPL; q++) m[q] &= window_bits<CellT>(wd[q], tm, P, lim);
+      }
+    }
+    if (ok) {
+#pragma unroll
+      for (int q = 0; q < WPL; q++) total += __popc(m[q]);
+    }
+  }
+  return warp_sum(total);
+}
+
+template <typename CellT>
+__device__ __forceinline__ uint32_t union_count(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
+                                                uint32_t u, uint32_t mycol, uint32_t tm, uint32_t P,
+                                                uint32_t lim, int lane) {
+  const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;
+  if (R >= 128) return union_count_w<CellT, 4>(arr, v, cells, u, mycol, tm, P, lim, lane);
+  if (R >= 64) return union_count_w<CellT, 2>(arr, v, cells, u, mycol, tm, P, lim, lane);
+  return union_count_w<CellT, 1>(arr, v, cells, u, mycol, tm, P, lim, lane);
+}
+
+}  // namespace srla

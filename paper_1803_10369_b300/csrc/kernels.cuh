@@ -1,0 +1,371 @@
+// The kernels of the SRLA hot path: the per-packet scan (Algorithm 2) and the end-of-slice
+// pass (Section 4.2: row census, Eq. 8, Eq. 9; Algorithm 3: slide and carry).
+#pragma once
+
+#include <math.h>
+
+#include "device.cuh"
+
+namespace srla {
+
+// ------------------------------------------------------------------------------ scan
+//
+// Algorithm 2 for one pair, under the order-free candidate rule: DRset the SLE recorder
+// selected by bip in each of the u estimators of aip; if LSB(H_S(bip)) >= tau, DRset the
+// SRE recorder selected by bip in the same estimators and add aip to the slice's set of
+// sampled hosts.  All writers of a slice write the same stamp, so plain stores are
+// race-free (Section 4.3 makes the same observation for its bits and recorders).
+template <typename CellT>
+__device__ __forceinline__ void scan_pair(uint32_t aip, uint32_t bip, bool ok, const Geo& geo,
+                                          const Coef& coef, CellT code, CellT* __restrict__ re,
+                                          CellT* __restrict__ le, Ctl* __restrict__ ctl,
+                                          unsigned long long* __restrict__ utab, uint32_t umask,
+                                          uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag,
+                                          int lane) {
+  const uint32_t u = geo.u;
+  const uint32_t jl = hash61(coef.a[u], coef.b[u], bip) & geo.glmask;
+  const uint32_t jr = hash61(coef.a[u + 1], coef.b[u + 1], bip) & geo.gmask;
+  const uint32_t hs = hash61(coef.a[u + 2], coef.b[u + 2], bip);
+  const bool samp = ok && ((hs & geo.samp_mask) == 0);
+#pragma unroll 4
+  for (uint32_t i = 0; i < u; i++) {
+    const uint32_t c = hash61(coef.a[i], coef.b[i], aip) & geo.vmask;
+    const size_t se = (size_t)i * geo.v + c;
+    if (ok) le[se * geo.gl + jl] = code;
+    if (samp) re[se * geo.g + jr] = code;
+  }
+  // Add aip to the slice's sampled-host set once per warp (same-source lanes agree first).
+  const unsigned sm = __ballot_sync(kFull, samp);
+  if (samp) {
+    const unsigned peers = __match_any_sync(sm, aip);
+    if ((peers & ((1u << lane) - 1u)) == 0) {
+      uint32_t slot;
+      const int r = set_insert(utab, umask, tag, aip, &slot);
+      if (r == 1) {
+        const unsigned idx = atomicAdd(&ctl->n_sampled, 1u);
+        if (idx < umax)
+          ulist[idx] = aip;
+        else
+          atomicOr(&ctl->overflow, 1u);
+      } else if (r < 0) {
+        atomicOr(&ctl->overflow, 1u);
+      }
+    }
+  }
+}
+
+// Packets are read as 16-byte vectors (two pairs) when the batch is 16-byte aligned.
+// Each warp iteration covers 128 packets: lane l holds packets 2l, 2l+1, 64+2l, 65+2l.
+template <typename CellT, bool kVec>
+__global__ void __launch_bounds__(256) k_scan(const uint32_t* __restrict__ pairs, uint64_t n, Geo geo,
+                                              const __grid_constant__ Coef coef, CellT* __restrict__ re, CellT* __restrict__ le,
+                                              Ctl* __restrict__ ctl, unsigned long long* __restrict__ utab,
+                                              uint32_t umask, uint32_t* __restrict__ ulist, uint32_t umax) {
+  const uint32_t tm = ctl->tm;
+  const CellT code = (CellT)(tm + 1u);
+  const uint32_t tag = slice_tag(ctl->T);
+  const int lane = threadIdx.x & 31;
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+  for (uint64_t base = gw * 128; base < n; base += nw * 128) {
+    uint32_t a[4], b[4];
+    bool ok[4];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const uint64_t p = base + (uint64_t)h * 64 + (uint64_t)lane * 2;
+      if (kVec && p + 1 < n) {
+        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(pairs) + (p >> 1));
+        a[2 * h] = q.x; b[2 * h] = q.y; a[2 * h + 1] = q.z; b[2 * h + 1] = q.w;
+        ok[2 * h] = true; ok[2 * h + 1] = true;
+      } else {
+        ok[2 * h] = p < n;
+        ok[2 * h + 1] = p + 1 < n;
+        a[2 * h] = ok[2 * h] ? pairs[2 * p] : 0u;
+        b[2 * h] = ok[2 * h] ? pairs[2 * p + 1] : 0u;
+        a[2 * h + 1] = ok[2 * h + 1] ? pairs[2 * p + 2] : 0u;
+        b[2 * h + 1] = ok[2 * h + 1] ? pairs[2 * p + 3] : 0u;
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; j++)
+      scan_pair<CellT>(a[j], b[j], ok[j], geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+  }
+}
+
+// ------------------------------------------------------------- sweep and row census
+//
+// One streaming pass over a row of recorders (blockIdx.y < u: SLE row y; >= u: SRE row
+// y - u).  Census (Section 4.2): count the SLE recorders of the row inside the window at
+// the open slice (age < k).  Reset: clear the stamps whose age would reach P after the
+// slide, i.e. the code 1 + ((T + 1) mod P); this is the DRslide of Algorithm 3 at the
+// point where a distance saturates at 2^z - 1.
+template <typename CellT>
+__global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, CellT* __restrict__ le,
+                                               Ctl* __restrict__ ctl, int do_census, int do_reset) {
+  const uint32_t y = blockIdx.y;
+  const bool is_le = y < geo.u;
+  if (!is_le && !do_reset) return;
+  const bool count = is_le && do_census;
+  const uint32_t row = is_le ? y : y - geo.u;
+  const size_t cells = (size_t)geo.v * (is_le ? geo.gl : geo.g);
+  uint4* base = reinterpret_cast<uint4*>((is_le ? le : re) + (size_t)row * cells);
+  const size_t nvec = cells * sizeof(CellT) / 16;
+  const uint32_t tm = ctl->tm, P = geo.P, k = geo.k;
+  const uint32_t alias = 1u + ((tm + 1u == P) ? 0u : tm + 1u);
+  const uint32_t splat = sizeof(CellT) == 1 ? alias * 0x01010101u : alias * 0x00010001u;
+  uint32_t cnt = 0;
+  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < nvec; x += (size_t)gridDim.x * blockDim.x) {
+    uint4 q = base[x];
+    if (count) {
+      cnt += __popc(window_bits<CellT>(q.x, tm, P, k)) + __popc(window_bits<CellT>(q.y, tm, P, k)) +
+             __popc(window_bits<CellT>(q.z, tm, P, k)) + __popc(window_bits<CellT>(q.w, tm, P, k));
+    }
+    if (do_reset) {
+      uint4 r;
+      if (sizeof(CellT) == 1) {
+        r.x = q.x & ~__vcmpeq4(q.x, splat); r.y = q.y & ~__vcmpeq4(q.y, splat);
+        r.z = q.z & ~__vcmpeq4(q.z, splat); r.w = q.w & ~__vcmpeq4(q.w, splat);
+      } else {
+        r.x = q.x & ~__vcmpeq2(q.x, splat); r.y = q.y & ~__vcmpeq2(q.y, splat);
+        r.z = q.z & ~__vcmpeq2(q.z, splat); r.w = q.w & ~__vcmpeq2(q.w, splat);
+      }
+      if (r.x != q.x || r.y != q.y || r.z != q.z || r.w != q.w) base[x] = r;
+    }
+  }
+  if (count) {
+    __shared__ uint32_t part[8];
+    cnt = warp_sum(cnt);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long s = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += part[w];
+      atomicAdd(&ctl->census[row], s);
+    }
+  }
+}
+
+// ------------------------------------------------------------------- estimator table
+//
+// Eq. 8 (UP from the row census) and Eq. 9 for every possible union weight w in [0, gl],
+// in FP64, rounded once to FP32.  For a fixed slice the estimate depends on w alone, so the
+// per-candidate work is a table lookup.  Edges: w <= gl*UP gives 0; w = gl or UP = 1 gives
+// +inf (saturated).  The super point decision (estimate >= theta, Definition 2) is taken
+// here in FP64 and stored with the entry.
+__global__ void k_lut(Geo geo, Ctl* __restrict__ ctl, float* __restrict__ lut_est, uint32_t* __restrict__ lut_flags) {
+  double up = 1.0;
+  const double cells = (double)geo.gl * (double)geo.v;
+  for (uint32_t i = 0; i < geo.u; i++) up *= (double)ctl->census[i] / cells;
+  const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
+  if (w == 0) ctl->up = up;
+  if (w > geo.gl) return;
+  const double g = (double)geo.gl;
+  double est;
+  uint32_t f = 0;
+  if (w == geo.gl || up >= 1.0) {
+    est = INFINITY;
+    f = SRLA_SATURATED | SRLA_SUPER;
+  } else if ((double)w <= g * up) {
+    est = 0.0;
+  } else {
+    est = -g * log(1.0 - ((double)w - g * up) / (g * (1.0 - up)));
+    if (est >= (double)geo.theta) f = SRLA_SUPER;
+  }
+  lut_est[w] = (float)est;
+  lut_flags[w] = f;
+  if (f & SRLA_SUPER) atomicMin(&ctl->w_star, w);
+}
+
+// -------------------------------------------------------------- new candidates (b3)
+//
+// For every distinct host sampled in the open slice: |URE(aip)|^k at the end of the slice
+// (before the slide).  Hosts with at least ceil(rho*g) in-window union cells enter the
+// slice's candidate set, which already holds the hosts carried from the previous slice.
+template <typename CellT>
+__global__ void __launch_bounds__(256) k_filter(Geo geo, const __grid_constant__ Coef coef, const CellT* __restrict__ re,
+                                                Ctl* __restrict__ ctl, const uint32_t* __restrict__ ulist,
+                                                uint32_t umax, unsigned long long* ctab0,
+                                                unsigned long long* ctab1, uint32_t* cflags0, uint32_t* cflags1,
+                                                uint32_t cmask, uint32_t* clist0, uint32_t* clist1, uint32_t cmax) {
+  const unsigned long long T = ctl->T;
+  const int par = (int)(T & 1);
+  unsigned long long* ctab = par ? ctab1 : ctab0;
+  uint32_t* cflags = par ? cflags1 : cflags0;
+  uint32_t* clist = par ? clist1 : clist0;
+  const uint32_t tag = slice_tag(T);
+  const uint32_t n = min(ctl->n_sampled, umax);
+  const uint32_t tm = ctl->tm;
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t idx = gw; idx < n; idx += nw) {
+    const uint32_t aip = ulist[idx];
+    const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
+    const uint32_t cnt = union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, tm, geo.P, geo.k, lane);
+    if (lane == 0 && cnt >= geo.rho_g) {
+      atomicAdd(&ctl->n_new, 1u);
+      uint32_t slot;
+      const int r = set_insert(ctab, cmask, tag, aip, &slot);
+      if (r == 1) {
+        cflags[slot] = SRLA_NEW;
+        const unsigned at = atomicAdd(&ctl->cat_count[par], 1u);
+        if (at < cmax)
+          clist[at] = aip;
+        else
+          atomicOr(&ctl->overflow, 2u);
+      } else if (r == 0) {
+        atomicOr(&cflags[slot], SRLA_NEW);
+      } else {
+        atomicOr(&ctl->overflow, 2u);
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------ estimate (b4) and carry (b5)
+//
+// For every candidate of the sorted list: w = |ULE(aip)|^k (Algorithm 1), the estimate
+// and super point flag from the slice's table (Eq. 9), and the report entry at the same
+// position.  Then the carry test of Algorithm 3 on the post-slide SRE (age + 1 < k); hosts
+// that pass join the next slice's candidate set.
+template <typename CellT>
+__global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant__ Coef coef, const CellT* __restrict__ re,
+                                                  const CellT* __restrict__ le, Ctl* __restrict__ ctl,
+                                                  const float* __restrict__ lut_est,
+                                                  const uint32_t* __restrict__ lut_flags,
+                                                  unsigned long long* ctab0, unsigned long long* ctab1,
+                                                  uint32_t* cflags0, uint32_t* cflags1, uint32_t cmask,
+                                                  uint32_t* clist0, uint32_t* clist1, uint32_t cmax,
+                                                  srla_entry* rep0, srla_entry* rep1) {
+  const unsigned long long T = ctl->T;
+  const int par = (int)(T & 1);
+  const unsigned long long* ctab = par ? ctab1 : ctab0;
+  const uint32_t* cflags = par ? cflags1 : cflags0;
+  const uint32_t* clist = par ? clist1 : clist0;
+  unsigned long long* ntab = par ? ctab0 : ctab1;
+  uint32_t* nflags = par ? cflags0 : cflags1;
+  uint32_t* nlist = par ? clist0 : clist1;
+  srla_entry* rep = par ? rep1 : rep0;
+  const uint32_t tag = slice_tag(T), ntag = slice_tag(T + 1);
+  const uint32_t n = min(ctl->cat_count[par], cmax);
+  const uint32_t tm = ctl->tm;
+  const uint32_t klim_post = geo.k - 1u;  // age + 1 < k after the slide
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t idx = gw; idx < n; idx += nw) {
+    const uint32_t aip = clist[idx];
+    const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
+    const uint32_t w = union_count<CellT>(le, geo.v, geo.gl, geo.u, mycol, tm, geo.P, geo.k, lane);
+    const uint32_t cw = union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, tm, geo.P, klim_post, lane);
+    if (lane == 0) {
+      const uint32_t s = set_find(ctab, cmask, tag, aip);
+      const uint32_t origin = (s != 0xFFFFFFFFu) ? cflags[s] : 0u;
+      srla_entry e;
+      e.aip = aip;
+      e.w = w;
+      e.est = lut_est[w];
+      e.flags = origin | lut_flags[w];
+      rep[idx] = e;
+      if (cw >= geo.rho_g) {
+        uint32_t slot;
+        const int r = set_insert(ntab, cmask, ntag, aip, &slot);
+        if (r == 1) {
+          nflags[slot] = SRLA_CARRIED;
+          const unsigned at = atomicAdd(&ctl->cat_count[par ^ 1], 1u);
+          if (at < cmax)
+            nlist[at] = aip;
+          else
+            atomicOr(&ctl->overflow_next, 2u);
+        } else if (r < 0) {
+          atomicOr(&ctl->overflow_next, 2u);
+        }
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------ close the slice
+__global__ void k_finish(Geo geo, Ctl* __restrict__ ctl, srla_slice_stats* st0, srla_slice_stats* st1,
+                         uint32_t umax, uint32_t cmax) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const unsigned long long T = ctl->T;
+  const int par = (int)(T & 1);
+  srla_slice_stats* st = par ? st1 : st0;
+  st->slice = T;
+  st->n_pkts = 0;
+  st->n_sampled = min(ctl->n_sampled, umax);
+  st->n_new = ctl->n_new;
+  st->n_candidates = min(ctl->cat_count[par], cmax);
+  st->n_carry_out = min(ctl->cat_count[par ^ 1], cmax);
+  st->w_star = ctl->w_star;
+  st->overflow = ctl->overflow;
+  st->up = ctl->up;
+  for (int i = 0; i < SRLA_MAX_ROWS; i++) {
+    st->census[i] = ctl->census[i];
+    ctl->census[i] = 0;
+  }
+  ctl->T = T + 1;
+  ctl->tm = (ctl->tm + 1u == geo.P) ? 0u : ctl->tm + 1u;
+  ctl->n_sampled = 0;
+  ctl->n_new = 0;
+  ctl->cat_count[par] = 0;
+  ctl->overflow = ctl->overflow_next;
+  ctl->overflow_next = 0;
+  ctl->w_star = geo.gl + 1u;
+}
+
+// ------------------------------------------------------------------- checkpointing
+
+// Recorder stamps -> the paper's distances (2^z - 1 = empty), at the open slice.
+template <typename CellT>
+__global__ void k_decode(const CellT* __restrict__ cells, uint16_t* __restrict__ out, size_t n,
+                         const Ctl* __restrict__ ctl, uint32_t P) {
+  const uint32_t tm = ctl->tm;
+  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t c = cells[x];
+    out[x] = (uint16_t)(c == 0 ? P : stamp_age(c, tm, P));
+  }
+}
+
+// Distances -> stamps at open slice with T mod P = tm.
+template <typename CellT>
+__global__ void k_encode(const uint16_t* __restrict__ d, CellT* __restrict__ cells, size_t n, uint32_t tm,
+                         uint32_t P) {
+  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
+    const uint32_t dd = d[x];
+    uint32_t c = 0;
+    if (dd < P) {
+      const int s = ((int)tm - (int)dd) % (int)P;
+      c = 1u + (uint32_t)(s < 0 ? s + (int)P : s);
+    }
+    cells[x] = (CellT)c;
+  }
+}
+
+// Insert carried hosts (checkpoint import) into the open slice's candidate set.
+__global__ void k_insert_carried(const uint32_t* __restrict__ hosts, uint32_t n, Ctl* __restrict__ ctl,
+                                 unsigned long long* ctab0, unsigned long long* ctab1, uint32_t* cflags0,
+                                 uint32_t* cflags1, uint32_t cmask, uint32_t* clist0, uint32_t* clist1,
+                                 uint32_t cmax) {
+  const unsigned long long T = ctl->T;
+  const int par = (int)(T & 1);
+  unsigned long long* ctab = par ? ctab1 : ctab0;
+  uint32_t* cflags = par ? cflags1 : cflags0;
+  uint32_t* clist = par ? clist1 : clist0;
+  const uint32_t tag = slice_tag(T);
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
+    uint32_t slot;
+    const int r = set_insert(ctab, cmask, tag, hosts[x], &slot);
+    if (r == 1) {
+      cflags[slot] = SRLA_CARRIED;
+      const unsigned at = atomicAdd(&ctl->cat_count[par], 1u);
+      if (at < cmax)
+        clist[at] = hosts[x];
+      else
+        atomicOr(&ctl->overflow, 2u);
+    }
+  }
+}
+
+}  // namespace srla

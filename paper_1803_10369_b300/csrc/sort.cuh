@@ -1,0 +1,225 @@
+// Ascending sort of the slice's candidate hosts (uint32 keys, unique).
+//
+// Least-significant-digit radix sort, 8-bit digits, 4 passes.  A tile is 4096 keys handled
+// by 16 warps; each warp ranks its 256 keys in 8 rounds of 32 with __match_any_sync, which
+// keeps the ranking stable (index order within a round, rounds in order, warps in order).
+// Lists of up to one tile are sorted by a single block in shared memory; longer lists use
+// three kernels per pass (tile histograms, one scan over them, stable scatter).  The list
+// length lives on the device, so every kernel reads it and exits when it is not its case.
+#pragma once
+
+#include "device.cuh"
+
+namespace srla {
+
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kKeysPerWarp = 256;
+constexpr int kSortTile = kSortWarps * kKeysPerWarp;  // 4096
+constexpr int kRadix = 256;
+
+__device__ __forceinline__ uint32_t sort_len(const Ctl* ctl, uint32_t cmax) {
+  return min(ctl->cat_count[ctl->T & 1], cmax);
+}
+
+__device__ __forceinline__ uint32_t* sort_list(const Ctl* ctl, uint32_t* l0, uint32_t* l1) {
+  return (ctl->T & 1) ? l1 : l0;
+}
+
+// Rank the keys of one tile by the digit at `shift`.  On return, wcnt[w][d] holds the
+// number of keys of digit d in warp w, and key[r], rank[r] the r-th key of this lane and
+// its rank among the warp's keys with the same digit.
+__device__ __forceinline__ void rank_tile(const uint32_t* src, uint32_t tile_base, uint32_t n, int shift,
+                                          uint32_t (*wcnt)[kRadix], uint32_t key[8], uint32_t rank[8],
+                                          bool valid[8]) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+#pragma unroll
+  for (int r = 0; r < 8; r++) {
+    const uint32_t idx = tile_base + (uint32_t)w * kKeysPerWarp + (uint32_t)r * 32u + (uint32_t)lane;
+    const bool ok = idx < n;
+    const uint32_t kk = ok ? src[idx] : 0u;
+    const uint32_t d = (kk >> shift) & 0xFFu;
+    const unsigned vm = __ballot_sync(kFull, ok);
+    uint32_t rk = 0;
+    if (ok) {
+      const unsigned peers = __match_any_sync(vm, d);
+      const uint32_t before = wcnt[w][d];
+      __syncwarp(vm);
+      rk = before + (uint32_t)__popc(peers & lt);
+      if ((peers & lt) == 0) wcnt[w][d] = before + (uint32_t)__popc(peers);
+    }
+    __syncwarp();
+    key[r] = kk;
+    rank[r] = rk;
+    valid[r] = ok;
+  }
+}
+
+// Turn wcnt[w][d] into the exclusive prefix over warps; tot[d] receives the tile's count.
+__device__ __forceinline__ void warp_prefix(uint32_t (*wcnt)[kRadix], uint32_t* tot) {
+  for (int d = threadIdx.x; d < kRadix; d += blockDim.x) {
+    uint32_t run = 0;
+    for (int w = 0; w < kSortWarps; w++) {
+      const uint32_t c = wcnt[w][d];
+      wcnt[w][d] = run;
+      run += c;
+    }
+    tot[d] = run;
+  }
+}
+
+// Lists of at most one tile: the whole sort in one block, in shared memory.
+__global__ void __launch_bounds__(kSortThreads) k_sort_small(const Ctl* __restrict__ ctl, uint32_t* l0,
+                                                             uint32_t* l1, uint32_t cmax) {
+  const uint32_t n = sort_len(ctl, cmax);
+  if (n <= 1 || n > (uint32_t)kSortTile) return;
+  uint32_t* list = sort_list(ctl, l0, l1);
+  extern __shared__ uint32_t smem[];
+  uint32_t* bufA = smem;                                   // kSortTile
+  uint32_t* bufB = smem + kSortTile;                       // kSortTile
+  uint32_t(*wcnt)[kRadix] = reinterpret_cast<uint32_t(*)[kRadix]>(smem + 2 * kSortTile);
+  uint32_t* tot = smem + 2 * kSortTile + kSortWarps * kRadix;  // kRadix
+  for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) bufA[x] = list[x];
+  const int w = threadIdx.x >> 5;
+  for (int pass = 0; pass < 4; pass++) {
+    uint32_t* src = (pass & 1) ? bufB : bufA;
+    uint32_t* dst = (pass & 1) ? bufA : bufB;
+    for (int x = threadIdx.x; x < kSortWarps * kRadix; x += blockDim.x) (&wcnt[0][0])[x] = 0;
+    __syncthreads();
+    uint32_t key[8], rank[8];
+    bool valid[8];
+    rank_tile(src, 0, n, pass * 8, wcnt, key, rank, valid);
+    __syncthreads();
+    warp_prefix(wcnt, tot);
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of the 256 digit totals by one warp
+      uint32_t v[8], s = 0;
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        v[q] = tot[threadIdx.x * 8 + q];
+        s += v[q];
+      }
+      uint32_t incl = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if ((int)threadIdx.x >= o) incl += t;
+      }
+      uint32_t run = incl - s;
+#pragma unroll
+      for (int q = 0; q < 8; q++) {
+        tot[threadIdx.x * 8 + q] = run;
+        run += v[q];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+      if (valid[r]) {
+        const uint32_t d = (key[r] >> (pass * 8)) & 0xFFu;
+        dst[tot[d] + wcnt[w][d] + rank[r]] = key[r];
+      }
+    }
+    __syncthreads();
+  }
+  for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) list[x] = bufA[x];
+}
+
+// Multi-tile pass, step 1: digit histogram of every tile, stored digit-major
+// (hist[d * ntiles + t]) so that one exclusive scan yields every scatter offset.
+__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const Ctl* __restrict__ ctl, uint32_t* l0,
+                                                             uint32_t* l1, uint32_t* tmp, uint32_t cmax,
+                                                             int pass, uint32_t* __restrict__ hist) {
+  const uint32_t n = sort_len(ctl, cmax);
+  if (n <= (uint32_t)kSortTile) return;
+  const uint32_t* src = (pass & 1) ? tmp : sort_list(ctl, l0, l1);
+  const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+  __shared__ uint32_t cnt[kRadix];
+  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) cnt[d] = 0;
+    __syncthreads();
+    const uint32_t lo = t * kSortTile, hi = min(n, lo + kSortTile);
+    for (uint32_t x = lo + threadIdx.x; x < hi; x += blockDim.x) atomicAdd(&cnt[(src[x] >> (pass * 8)) & 0xFFu], 1u);
+    __syncthreads();
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(size_t)d * ntiles + t] = cnt[d];
+    __syncthreads();
+  }
+}
+
+// Multi-tile pass, step 2: exclusive scan of the histogram table (one block).
+__global__ void __launch_bounds__(1024) k_radix_scan(const Ctl* __restrict__ ctl, uint32_t cmax,
+                                                     uint32_t* __restrict__ hist) {
+  const uint32_t n = sort_len(ctl, cmax);
+  if (n <= (uint32_t)kSortTile) return;
+  const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+  const uint32_t N = ntiles * kRadix;
+  const uint32_t per = (N + blockDim.x - 1) / blockDim.x;
+  const uint32_t lo = threadIdx.x * per, hi = min(N, lo + per);
+  uint32_t s = 0;
+  for (uint32_t x = lo; x < hi; x++) s += hist[x];
+  __shared__ uint32_t part[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t incl = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) part[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t p = (lane < (int)(blockDim.x >> 5)) ? part[lane] : 0u;
+    uint32_t pi = p;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, pi, o);
+      if (lane >= o) pi += t;
+    }
+    part[lane] = pi - p;
+  }
+  __syncthreads();
+  uint32_t run = part[w] + incl - s;
+  for (uint32_t x = lo; x < hi; x++) {
+    const uint32_t c = hist[x];
+    hist[x] = run;
+    run += c;
+  }
+}
+
+// Multi-tile pass, step 3: stable scatter of every tile to its digit offsets.
+__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const Ctl* __restrict__ ctl, uint32_t* l0,
+                                                                uint32_t* l1, uint32_t* tmp, uint32_t cmax,
+                                                                int pass, const uint32_t* __restrict__ hist) {
+  const uint32_t n = sort_len(ctl, cmax);
+  if (n <= (uint32_t)kSortTile) return;
+  uint32_t* list = sort_list(ctl, l0, l1);
+  const uint32_t* src = (pass & 1) ? tmp : list;
+  uint32_t* dst = (pass & 1) ? list : tmp;
+  const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+  __shared__ uint32_t wcnt[kSortWarps][kRadix];
+  __shared__ uint32_t tot[kRadix];
+  const int w = threadIdx.x >> 5;
+  for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int x = threadIdx.x; x < kSortWarps * kRadix; x += blockDim.x) (&wcnt[0][0])[x] = 0;
+    __syncthreads();
+    uint32_t key[8], rank[8];
+    bool valid[8];
+    rank_tile(src, t * kSortTile, n, pass * 8, wcnt, key, rank, valid);
+    __syncthreads();
+    warp_prefix(wcnt, tot);
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 8; r++) {
+      if (valid[r]) {
+        const uint32_t d = (key[r] >> (pass * 8)) & 0xFFu;
+        dst[hist[(size_t)d * ntiles + t] + wcnt[w][d] + rank[r]] = key[r];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+constexpr size_t kSortSmallSmem = (size_t)(2 * kSortTile + kSortWarps * kRadix + kRadix) * sizeof(uint32_t);
+
+}  // namespace srla

@@ -1,0 +1,592 @@
+// libsrla: the C-ABI of the SRLA hot path (declared in include/srla.h).
+//
+// Host code here only validates arguments, lays out the caller's workspace, enqueues the
+// kernels of kernels.cuh / sort.cuh on the caller's stream and moves reports and
+// checkpoints across PCIe.  Every step of the method runs on the GPU.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+#include "sort.cuh"
+
+using namespace srla;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr uint32_t kPrefetch = 2048;  // report entries copied with the slice's header
+constexpr uint32_t kStateMagic = 0x53524C41u;  // "SRLA"
+constexpr uint32_t kStateVersion = 1;
+
+size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+bool pow2(uint64_t x) { return x && !(x & (x - 1)); }
+
+uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+struct Layout {
+  size_t ctl, re, le, staging, utab, ulist, ctab[2], cflags[2], clist[2], sort_tmp, sort_hist, lut_est,
+      lut_flags, rep_stats[2], rep_entries[2], total;
+  uint64_t staging_pkts;
+  uint32_t umask, cmask, ntiles;
+};
+
+// Eq. 1 on integers: the least n >= 0 with g * 2^n >= theta.
+uint32_t tau_of(uint32_t theta, uint32_t g) {
+  uint32_t n = 0;
+  while ((uint64_t)g << n < (uint64_t)theta) n++;
+  return n;
+}
+
+// ceil(rho * g) with rho = 0.99 (1 - e^{-1/3}) (Section 3.2), evaluated in FP64.
+uint32_t rho_g_of(uint32_t g) { return (uint32_t)std::ceil(0.99 * (1.0 - std::exp(-1.0 / 3.0)) * (double)g); }
+
+int check(const srla_params* p) {
+  if (!p) return SRLA_E_INVAL;
+  if (p->u < 1 || p->u > SRLA_MAX_ROWS) return SRLA_E_INVAL;
+  if (!pow2(p->v) || !pow2(p->g) || !pow2(p->gl)) return SRLA_E_INVAL;
+  if (p->dr_bytes != 1 && p->dr_bytes != 2) return SRLA_E_INVAL;
+  if (p->z < 1 || p->z > 8 * p->dr_bytes) return SRLA_E_INVAL;
+  const uint32_t P = (1u << p->z) - 1u;
+  if (p->k < 1 || p->k > P) return SRLA_E_INVAL;
+  if (p->theta < 1) return SRLA_E_INVAL;
+  if ((uint64_t)p->g * p->dr_bytes < 4 || (uint64_t)p->gl * p->dr_bytes < 4) return SRLA_E_INVAL;
+  if ((uint64_t)p->v * p->g * p->dr_bytes < 16 || (uint64_t)p->v * p->gl * p->dr_bytes < 16) return SRLA_E_INVAL;
+  if ((uint64_t)p->v * p->gl > (1ull << 40) || (uint64_t)p->v * p->g > (1ull << 40)) return SRLA_E_INVAL;
+  if (p->gl > (1u << 24)) return SRLA_E_INVAL;
+  if (p->max_sampled < 1 || p->max_sampled > (1u << 30)) return SRLA_E_INVAL;
+  if (p->max_candidates < 1 || p->max_candidates > (1u << 26)) return SRLA_E_INVAL;
+  for (uint32_t r = 0; r < p->u + 3; r++) {
+    if (p->hash_a[r] < 1 || p->hash_a[r] >= kP61) return SRLA_E_INVAL;
+    if (p->hash_b[r] >= kP61) return SRLA_E_INVAL;
+  }
+  return SRLA_OK;
+}
+
+Layout layout_of(const srla_params* p) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  const size_t B = p->dr_bytes;
+  L.staging_pkts = p->staging_pkts ? p->staging_pkts : (1ull << 20);
+  const uint64_t ucap = std::max<uint64_t>(64, next_pow2(2ull * p->max_sampled));
+  const uint64_t ccap = std::max<uint64_t>(64, next_pow2(2ull * p->max_candidates));
+  L.umask = (uint32_t)(ucap - 1);
+  L.cmask = (uint32_t)(ccap - 1);
+  L.ntiles = (p->max_candidates + kSortTile - 1) / kSortTile;
+  L.ctl = take(sizeof(Ctl));
+  L.re = take((size_t)p->u * p->v * p->g * B);
+  L.le = take((size_t)p->u * p->v * p->gl * B);
+  L.staging = take(L.staging_pkts * 8);
+  L.utab = take(ucap * 8);
+  L.ulist = take((size_t)p->max_sampled * 4);
+  for (int q = 0; q < 2; q++) {
+    L.ctab[q] = take(ccap * 8);
+    L.cflags[q] = take(ccap * 4);
+    L.clist[q] = take((size_t)p->max_candidates * 4);
+  }
+  L.sort_tmp = take((size_t)p->max_candidates * 4);
+  L.sort_hist = take((size_t)L.ntiles * kRadix * 4);
+  L.lut_est = take(((size_t)p->gl + 1) * 4);
+  L.lut_flags = take(((size_t)p->gl + 1) * 4);
+  for (int q = 0; q < 2; q++) {
+    L.rep_stats[q] = take(sizeof(srla_slice_stats));
+    L.rep_entries[q] = take((size_t)p->max_candidates * sizeof(srla_entry));
+  }
+  L.total = off;
+  return L;
+}
+
+struct StateHeader {
+  uint32_t magic, version;
+  uint32_t u, v, g, gl, dr_bytes, z, k, theta;
+  uint64_t slice;
+  uint32_t n_carry, pad;
+};
+
+}  // namespace
+
+struct srla_s {
+  srla_params p;
+  Geo geo;
+  Coef coef;
+  Layout L;
+  char* ws;
+  cudaStream_t st;
+  cudaStream_t st_copy;  // internal stream for report remainders and checkpoints
+  int sms;
+  bool k_is_P;
+  uint64_t T;             // open slice
+  uint64_t n_pkts_open;   // packets pushed into the open slice
+  uint64_t staging_used;  // staging packets used in the open slice
+  uint64_t launches;      // kernels launched so far
+  struct Slot {
+    uint64_t slice, n_pkts;
+    bool valid;
+    cudaEvent_t ev;
+    srla_slice_stats* h_stats;
+    srla_entry* h_entries;
+  } slot[2];
+  void* h_pinned;
+
+  template <typename T>
+  T* at(size_t off) const {
+    return reinterpret_cast<T*>(ws + off);
+  }
+  Ctl* ctl() const { return at<Ctl>(L.ctl); }
+};
+
+namespace {
+
+int cuda_err(cudaError_t e) {
+  if (e == cudaSuccess) return SRLA_OK;
+  (void)cudaGetLastError();
+  return SRLA_E_CUDA;
+}
+
+#define SRLA_TRY(x)                       \
+  do {                                    \
+    const int _r = cuda_err(x);           \
+    if (_r != SRLA_OK) return _r;         \
+  } while (0)
+
+int grid_for(uint64_t items, int per_block, int cap) {
+  const uint64_t b = (items + per_block - 1) / per_block;
+  return (int)std::max<uint64_t>(1, std::min<uint64_t>(b, (uint64_t)cap));
+}
+
+template <typename CellT>
+int launch_scan(srla_t* h, const uint32_t* pairs, uint64_t n) {
+  const int grid = grid_for(n, 256 * 4, h->sms * 8);
+  CellT* re = h->at<CellT>(h->L.re);
+  CellT* le = h->at<CellT>(h->L.le);
+  h->launches++;
+  if ((reinterpret_cast<uintptr_t>(pairs) & 15u) == 0)
+    k_scan<CellT, true><<<grid, 256, 0, h->st>>>(pairs, n, h->geo, h->coef, re, le, h->ctl(),
+                                                 h->at<unsigned long long>(h->L.utab), h->L.umask,
+                                                 h->at<uint32_t>(h->L.ulist), h->p.max_sampled);
+  else
+    k_scan<CellT, false><<<grid, 256, 0, h->st>>>(pairs, n, h->geo, h->coef, re, le, h->ctl(),
+                                                  h->at<unsigned long long>(h->L.utab), h->L.umask,
+                                                  h->at<uint32_t>(h->L.ulist), h->p.max_sampled);
+  return cuda_err(cudaGetLastError());
+}
+
+template <typename CellT>
+int launch_sweep(srla_t* h, int census, int reset) {
+  const size_t cells_max = (size_t)h->p.v * std::max(h->p.g, h->p.gl);
+  const size_t nvec = cells_max * sizeof(CellT) / 16;
+  const int gx = grid_for(nvec, 256, std::max(1, h->sms * 8 / (int)(2 * h->p.u)));
+  h->launches++;
+  k_sweep<CellT><<<dim3(gx, 2 * h->p.u), 256, 0, h->st>>>(h->geo, h->at<CellT>(h->L.re), h->at<CellT>(h->L.le),
+                                                         h->ctl(), census, reset);
+  return cuda_err(cudaGetLastError());
+}
+
+int launch_sort(srla_t* h) {
+  const Layout& L = h->L;
+  uint32_t* l0 = h->at<uint32_t>(L.clist[0]);
+  uint32_t* l1 = h->at<uint32_t>(L.clist[1]);
+  const uint32_t cmax = h->p.max_candidates;
+  h->launches++;
+  k_sort_small<<<1, kSortThreads, kSortSmallSmem, h->st>>>(h->ctl(), l0, l1, cmax);
+  if (L.ntiles > 1) {
+    uint32_t* tmp = h->at<uint32_t>(L.sort_tmp);
+    uint32_t* hist = h->at<uint32_t>(L.sort_hist);
+    for (int pass = 0; pass < 4; pass++) {
+      h->launches += 3;
+      k_radix_hist<<<L.ntiles, kSortThreads, 0, h->st>>>(h->ctl(), l0, l1, tmp, cmax, pass, hist);
+      k_radix_scan<<<1, 1024, 0, h->st>>>(h->ctl(), cmax, hist);
+      k_radix_scatter<<<L.ntiles, kSortThreads, 0, h->st>>>(h->ctl(), l0, l1, tmp, cmax, pass, hist);
+    }
+  }
+  return cuda_err(cudaGetLastError());
+}
+
+template <typename CellT>
+int launch_end_slice(srla_t* h) {
+  const Layout& L = h->L;
+  int r;
+  if ((r = launch_sweep<CellT>(h, 1, h->k_is_P ? 0 : 1)) != SRLA_OK) return r;
+  h->launches += 4;  // lut, filter, estimate, finish
+  k_lut<<<(h->p.gl + 1 + 255) / 256, 256, 0, h->st>>>(h->geo, h->ctl(), h->at<float>(L.lut_est),
+                                                       h->at<uint32_t>(L.lut_flags));
+  k_filter<CellT><<<h->sms * 4, 256, 0, h->st>>>(
+      h->geo, h->coef, h->at<CellT>(L.re), h->ctl(), h->at<uint32_t>(L.ulist), h->p.max_sampled,
+      h->at<unsigned long long>(L.ctab[0]), h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]),
+      h->at<uint32_t>(L.cflags[1]), L.cmask, h->at<uint32_t>(L.clist[0]), h->at<uint32_t>(L.clist[1]),
+      h->p.max_candidates);
+  if ((r = launch_sort(h)) != SRLA_OK) return r;
+  k_estimate<CellT><<<h->sms * 4, 256, 0, h->st>>>(
+      h->geo, h->coef, h->at<CellT>(L.re), h->at<CellT>(L.le), h->ctl(), h->at<float>(L.lut_est),
+      h->at<uint32_t>(L.lut_flags), h->at<unsigned long long>(L.ctab[0]), h->at<unsigned long long>(L.ctab[1]),
+      h->at<uint32_t>(L.cflags[0]), h->at<uint32_t>(L.cflags[1]), L.cmask, h->at<uint32_t>(L.clist[0]),
+      h->at<uint32_t>(L.clist[1]), h->p.max_candidates, h->at<srla_entry>(L.rep_entries[0]),
+      h->at<srla_entry>(L.rep_entries[1]));
+  if (h->k_is_P && (r = launch_sweep<CellT>(h, 0, 1)) != SRLA_OK) return r;
+  k_finish<<<1, 32, 0, h->st>>>(h->geo, h->ctl(), h->at<srla_slice_stats>(L.rep_stats[0]),
+                                h->at<srla_slice_stats>(L.rep_stats[1]), h->p.max_sampled, h->p.max_candidates);
+  return cuda_err(cudaGetLastError());
+}
+
+// Zero the control block and both candidate/sampled set tables (fresh tags).
+int reset_tables(srla_t* h, bool all) {
+  const Layout& L = h->L;
+  SRLA_TRY(cudaMemsetAsync(h->ws + L.utab, 0, ((size_t)L.umask + 1) * 8, h->st));
+  for (int q = 0; q < 2; q++) SRLA_TRY(cudaMemsetAsync(h->ws + L.ctab[q], 0, ((size_t)L.cmask + 1) * 8, h->st));
+  if (all) SRLA_TRY(cudaMemsetAsync(h->ws, 0, L.total, h->st));
+  return SRLA_OK;
+}
+
+int init_ctl(srla_t* h, uint64_t T, uint32_t carried) {
+  Ctl c{};
+  c.T = T;
+  c.tm = (uint32_t)(T % h->geo.P);
+  c.w_star = h->geo.gl + 1;
+  c.cat_count[T & 1] = carried;
+  SRLA_TRY(cudaMemcpyAsync(h->ctl(), &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
+  return cudaStreamSynchronize(h->st) == cudaSuccess ? SRLA_OK : SRLA_E_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int srla_check_params(const srla_params* p) { return check(p); }
+
+size_t srla_workspace_bytes(const srla_params* p) {
+  if (check(p) != SRLA_OK) return 0;
+  return layout_of(p).total;
+}
+
+int srla_derived(const srla_params* p, uint32_t* tau, uint32_t* rho_g, uint32_t* stamp_mod) {
+  if (check(p) != SRLA_OK) return SRLA_E_INVAL;
+  if (tau) *tau = tau_of(p->theta, p->g);
+  if (rho_g) *rho_g = rho_g_of(p->g);
+  if (stamp_mod) *stamp_mod = (1u << p->z) - 1u;
+  return SRLA_OK;
+}
+
+int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void* stream, srla_t** out) {
+  if (!out) return SRLA_E_INVAL;
+  *out = nullptr;
+  if (check(p) != SRLA_OK || !dev_workspace) return SRLA_E_INVAL;
+  if (reinterpret_cast<uintptr_t>(dev_workspace) % kAlign) return SRLA_E_INVAL;
+  const Layout L = layout_of(p);
+  if (ws_bytes < L.total) return SRLA_E_NOMEM;
+  srla_t* h = new (std::nothrow) srla_s();
+  if (!h) return SRLA_E_NOMEM;
+  h->p = *p;
+  h->L = L;
+  h->ws = static_cast<char*>(dev_workspace);
+  h->st = static_cast<cudaStream_t>(stream);
+  const uint32_t tau = tau_of(p->theta, p->g);
+  h->geo = Geo{p->u, p->v, p->g, p->gl, p->v - 1, p->g - 1, p->gl - 1, p->k, (1u << p->z) - 1u,
+               tau >= 32 ? 0xFFFFFFFFu : ((1u << tau) - 1u), rho_g_of(p->g), p->theta};
+  for (int r = 0; r < SRLA_N_HASH; r++) {
+    h->coef.a[r] = p->hash_a[r];
+    h->coef.b[r] = p->hash_b[r];
+  }
+  h->k_is_P = (p->k == h->geo.P);
+  h->T = p->start_slice;
+  int dev = 0, rc = SRLA_OK;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    delete h;
+    return cuda_err(cudaErrorUnknown);
+  }
+  const size_t per_slot = sizeof(srla_slice_stats) + (size_t)kPrefetch * sizeof(srla_entry);
+  if (cudaHostAlloc(&h->h_pinned, 2 * per_slot, cudaHostAllocDefault) != cudaSuccess) {
+    delete h;
+    return cuda_err(cudaErrorMemoryAllocation);
+  }
+  if (cudaStreamCreateWithFlags(&h->st_copy, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFreeHost(h->h_pinned);
+    delete h;
+    return SRLA_E_CUDA;
+  }
+  for (int q = 0; q < 2; q++) {
+    h->slot[q].valid = false;
+    h->slot[q].h_stats = reinterpret_cast<srla_slice_stats*>(static_cast<char*>(h->h_pinned) + q * per_slot);
+    h->slot[q].h_entries = reinterpret_cast<srla_entry*>(reinterpret_cast<char*>(h->slot[q].h_stats) +
+                                                         sizeof(srla_slice_stats));
+    if (cudaEventCreateWithFlags(&h->slot[q].ev, cudaEventDisableTiming) != cudaSuccess) rc = SRLA_E_CUDA;
+  }
+  if (rc == SRLA_OK) {
+    cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmallSmem);
+    rc = reset_tables(h, true);
+  }
+  if (rc == SRLA_OK) rc = init_ctl(h, h->T, 0);
+  if (rc != SRLA_OK) {
+    srla_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return SRLA_OK;
+}
+
+int srla_push_packets(srla_t* h, const uint32_t* pairs, uint64_t n_pairs, int on_device) {
+  if (!h || (!pairs && n_pairs)) return SRLA_E_INVAL;
+  if (n_pairs == 0) return SRLA_OK;
+  auto scan = [&](const uint32_t* src, uint64_t n) {
+    return h->p.dr_bytes == 1 ? launch_scan<uint8_t>(h, src, n) : launch_scan<uint16_t>(h, src, n);
+  };
+  if (on_device) {
+    const int r = scan(pairs, n_pairs);
+    if (r == SRLA_OK) h->n_pkts_open += n_pairs;
+    return r;
+  }
+  uint32_t* staging = h->at<uint32_t>(h->L.staging);
+  while (n_pairs) {
+    if (h->staging_used == h->L.staging_pkts) {
+      SRLA_TRY(cudaStreamSynchronize(h->st));
+      h->staging_used = 0;
+    }
+    const uint64_t m = std::min<uint64_t>(n_pairs, h->L.staging_pkts - h->staging_used);
+    uint32_t* dst = staging + 2 * h->staging_used;
+    SRLA_TRY(cudaMemcpyAsync(dst, pairs, m * 8, cudaMemcpyHostToDevice, h->st));
+    const int r = scan(dst, m);
+    if (r != SRLA_OK) return r;
+    h->staging_used += m;
+    h->n_pkts_open += m;
+    pairs += 2 * m;
+    n_pairs -= m;
+  }
+  return SRLA_OK;
+}
+
+int srla_end_slice(srla_t* h, uint64_t* slice_id) {
+  if (!h) return SRLA_E_INVAL;
+  const int r = h->p.dr_bytes == 1 ? launch_end_slice<uint8_t>(h) : launch_end_slice<uint16_t>(h);
+  if (r != SRLA_OK) return r;
+  const int q = (int)(h->T & 1);
+  srla_s::Slot& s = h->slot[q];
+  SRLA_TRY(cudaMemcpyAsync(s.h_stats, h->ws + h->L.rep_stats[q], sizeof(srla_slice_stats), cudaMemcpyDeviceToHost,
+                           h->st));
+  const uint32_t pre = std::min<uint32_t>(kPrefetch, h->p.max_candidates);
+  SRLA_TRY(cudaMemcpyAsync(s.h_entries, h->ws + h->L.rep_entries[q], (size_t)pre * sizeof(srla_entry),
+                           cudaMemcpyDeviceToHost, h->st));
+  SRLA_TRY(cudaEventRecord(s.ev, h->st));
+  s.slice = h->T;
+  s.n_pkts = h->n_pkts_open;
+  s.valid = true;
+  if (slice_id) *slice_id = h->T;
+  h->T++;
+  h->n_pkts_open = 0;
+  h->staging_used = 0;
+  if ((h->T & 0x7FFFFFFFull) == 0) {
+    // The 31-bit set tag wraps: start the new slice on cleared tables.  The carried list of
+    // the new slice sits in the table being cleared, so re-insert it from its list.
+    SRLA_TRY(cudaStreamSynchronize(h->st));
+    Ctl c;
+    SRLA_TRY(cudaMemcpy(&c, h->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
+    const uint32_t nc = std::min<uint32_t>(c.cat_count[h->T & 1], h->p.max_candidates);
+    int rr = reset_tables(h, false);
+    if (rr != SRLA_OK) return rr;
+    c.cat_count[h->T & 1] = 0;
+    SRLA_TRY(cudaMemcpyAsync(h->ctl(), &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
+    const Layout& L = h->L;
+    if (nc) {
+      // copy the list aside (into the sort scratch) before re-inserting it into its own table
+      SRLA_TRY(cudaMemcpyAsync(h->ws + L.sort_tmp, h->ws + L.clist[h->T & 1], (size_t)nc * 4,
+                               cudaMemcpyDeviceToDevice, h->st));
+      h->launches++;
+      k_insert_carried<<<grid_for(nc, 256, h->sms * 4), 256, 0, h->st>>>(
+          h->at<uint32_t>(L.sort_tmp), nc, h->ctl(), h->at<unsigned long long>(L.ctab[0]),
+          h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]), h->at<uint32_t>(L.cflags[1]),
+          L.cmask, h->at<uint32_t>(L.clist[0]), h->at<uint32_t>(L.clist[1]), h->p.max_candidates);
+      SRLA_TRY(cudaGetLastError());
+    }
+  }
+  return SRLA_OK;
+}
+
+int srla_report(srla_t* h, uint64_t slice_id, srla_entry* out, size_t cap, size_t* n_out,
+                srla_slice_stats* stats) {
+  if (!h || (cap && !out)) return SRLA_E_INVAL;
+  const int q = (int)(slice_id & 1);
+  srla_s::Slot& s = h->slot[q];
+  if (!s.valid || s.slice != slice_id) return SRLA_E_ORDER;
+  SRLA_TRY(cudaEventSynchronize(s.ev));
+  srla_slice_stats st = *s.h_stats;
+  st.n_pkts = s.n_pkts;
+  const size_t n = st.n_candidates;
+  if (n_out) *n_out = n;
+  if (stats) *stats = st;
+  const size_t take = std::min(n, cap);
+  const size_t pre = std::min<size_t>(take, std::min<uint32_t>(kPrefetch, h->p.max_candidates));
+  if (pre) std::memcpy(out, s.h_entries, pre * sizeof(srla_entry));
+  if (take > pre) {
+    SRLA_TRY(cudaMemcpyAsync(out + pre, h->ws + h->L.rep_entries[q] + pre * sizeof(srla_entry),
+                             (take - pre) * sizeof(srla_entry), cudaMemcpyDeviceToHost, h->st_copy));
+    SRLA_TRY(cudaStreamSynchronize(h->st_copy));
+  }
+  if (st.overflow) return SRLA_E_CAPACITY;
+  if (cap < n) return SRLA_E_NOMEM;
+  return SRLA_OK;
+}
+
+int srla_sync(srla_t* h) {
+  if (!h) return SRLA_E_INVAL;
+  return cuda_err(cudaStreamSynchronize(h->st));
+}
+
+size_t srla_state_bytes(const srla_t* h) {
+  if (!h) return 0;
+  const srla_params& p = h->p;
+  return sizeof(StateHeader) + (size_t)p.u * p.v * (p.g + p.gl) * 2 + (size_t)p.max_candidates * 4;
+}
+
+}  // extern "C"
+
+namespace {
+
+template <typename CellT>
+int export_cells(srla_t* h, size_t off, size_t n, uint16_t* dst) {
+  // decode through the staging area, one chunk at a time
+  const size_t chunk = h->L.staging_pkts * 8 / 2;  // uint16 per chunk
+  uint16_t* stage = h->at<uint16_t>(h->L.staging);
+  for (size_t x = 0; x < n; x += chunk) {
+    const size_t m = std::min(chunk, n - x);
+    h->launches++;
+    k_decode<CellT><<<grid_for(m, 256, h->sms * 8), 256, 0, h->st>>>(h->at<CellT>(off) + x, stage, m, h->ctl(),
+                                                                      h->geo.P);
+    SRLA_TRY(cudaGetLastError());
+    SRLA_TRY(cudaMemcpyAsync(dst + x, stage, m * 2, cudaMemcpyDeviceToHost, h->st));
+    SRLA_TRY(cudaStreamSynchronize(h->st));
+  }
+  return SRLA_OK;
+}
+
+template <typename CellT>
+int import_cells(srla_t* h, size_t off, size_t n, const uint16_t* src, uint32_t tm) {
+  const size_t chunk = h->L.staging_pkts * 8 / 2;
+  uint16_t* stage = h->at<uint16_t>(h->L.staging);
+  for (size_t x = 0; x < n; x += chunk) {
+    const size_t m = std::min(chunk, n - x);
+    SRLA_TRY(cudaMemcpyAsync(stage, src + x, m * 2, cudaMemcpyHostToDevice, h->st));
+    h->launches++;
+    k_encode<CellT><<<grid_for(m, 256, h->sms * 8), 256, 0, h->st>>>(stage, h->at<CellT>(off) + x, m, tm,
+                                                                      h->geo.P);
+    SRLA_TRY(cudaGetLastError());
+    SRLA_TRY(cudaStreamSynchronize(h->st));
+  }
+  return SRLA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int srla_export_state(srla_t* h, void* host_buf, size_t cap) {
+  if (!h || !host_buf) return SRLA_E_INVAL;
+  if (h->n_pkts_open) return SRLA_E_ORDER;
+  const srla_params& p = h->p;
+  SRLA_TRY(cudaStreamSynchronize(h->st));
+  Ctl c;
+  SRLA_TRY(cudaMemcpy(&c, h->ctl(), sizeof(Ctl), cudaMemcpyDeviceToHost));
+  const uint32_t nc = std::min<uint32_t>(c.cat_count[h->T & 1], p.max_candidates);
+  const size_t nre = (size_t)p.u * p.v * p.g, nle = (size_t)p.u * p.v * p.gl;
+  const size_t need = sizeof(StateHeader) + (nre + nle) * 2 + (size_t)nc * 4;
+  if (cap < need) return SRLA_E_NOMEM;
+  StateHeader hd{kStateMagic, kStateVersion, p.u, p.v, p.g, p.gl, p.dr_bytes, p.z, p.k, p.theta, h->T, nc, 0};
+  char* b = static_cast<char*>(host_buf);
+  std::memcpy(b, &hd, sizeof(hd));
+  uint16_t* dre = reinterpret_cast<uint16_t*>(b + sizeof(hd));
+  uint16_t* dle = dre + nre;
+  int r = p.dr_bytes == 1 ? export_cells<uint8_t>(h, h->L.re, nre, dre) : export_cells<uint16_t>(h, h->L.re, nre, dre);
+  if (r != SRLA_OK) return r;
+  r = p.dr_bytes == 1 ? export_cells<uint8_t>(h, h->L.le, nle, dle) : export_cells<uint16_t>(h, h->L.le, nle, dle);
+  if (r != SRLA_OK) return r;
+  uint32_t* carry = reinterpret_cast<uint32_t*>(dle + nle);
+  if (nc) {
+    SRLA_TRY(cudaMemcpy(carry, h->ws + h->L.clist[h->T & 1], (size_t)nc * 4, cudaMemcpyDeviceToHost));
+    std::sort(carry, carry + nc);
+  }
+  return SRLA_OK;
+}
+
+int srla_import_state(srla_t* h, const void* host_buf, size_t len) {
+  if (!h || !host_buf || len < sizeof(StateHeader)) return SRLA_E_INVAL;
+  if (h->n_pkts_open) return SRLA_E_ORDER;
+  const srla_params& p = h->p;
+  StateHeader hd;
+  std::memcpy(&hd, host_buf, sizeof(hd));
+  if (hd.magic != kStateMagic || hd.version != kStateVersion || hd.u != p.u || hd.v != p.v || hd.g != p.g ||
+      hd.gl != p.gl || hd.z != p.z || hd.k != p.k)
+    return SRLA_E_INVAL;
+  const size_t nre = (size_t)p.u * p.v * p.g, nle = (size_t)p.u * p.v * p.gl;
+  if (len < sizeof(StateHeader) + (nre + nle) * 2 + (size_t)hd.n_carry * 4) return SRLA_E_INVAL;
+  if (hd.n_carry > p.max_candidates) return SRLA_E_CAPACITY;
+  SRLA_TRY(cudaStreamSynchronize(h->st));
+  int r = reset_tables(h, false);
+  if (r != SRLA_OK) return r;
+  for (int q = 0; q < 2; q++) h->slot[q].valid = false;
+  h->T = hd.slice;
+  h->staging_used = 0;
+  if ((r = init_ctl(h, h->T, 0)) != SRLA_OK) return r;
+  const uint32_t tm = (uint32_t)(h->T % h->geo.P);
+  const uint16_t* sre = reinterpret_cast<const uint16_t*>(static_cast<const char*>(host_buf) + sizeof(hd));
+  const uint16_t* sle = sre + nre;
+  r = p.dr_bytes == 1 ? import_cells<uint8_t>(h, h->L.re, nre, sre, tm)
+                      : import_cells<uint16_t>(h, h->L.re, nre, sre, tm);
+  if (r != SRLA_OK) return r;
+  r = p.dr_bytes == 1 ? import_cells<uint8_t>(h, h->L.le, nle, sle, tm)
+                      : import_cells<uint16_t>(h, h->L.le, nle, sle, tm);
+  if (r != SRLA_OK) return r;
+  if (hd.n_carry) {
+    const uint32_t* carry = reinterpret_cast<const uint32_t*>(sle + nle);
+    uint32_t* stage = h->at<uint32_t>(h->L.sort_tmp);
+    SRLA_TRY(cudaMemcpyAsync(stage, carry, (size_t)hd.n_carry * 4, cudaMemcpyHostToDevice, h->st));
+    const Layout& L = h->L;
+    h->launches++;
+    k_insert_carried<<<grid_for(hd.n_carry, 256, h->sms * 4), 256, 0, h->st>>>(
+        stage, hd.n_carry, h->ctl(), h->at<unsigned long long>(L.ctab[0]), h->at<unsigned long long>(L.ctab[1]),
+        h->at<uint32_t>(L.cflags[0]), h->at<uint32_t>(L.cflags[1]), L.cmask, h->at<uint32_t>(L.clist[0]),
+        h->at<uint32_t>(L.clist[1]), p.max_candidates);
+    SRLA_TRY(cudaGetLastError());
+  }
+  return cuda_err(cudaStreamSynchronize(h->st));
+}
+
+uint64_t srla_kernel_launches(const srla_t* h) { return h ? h->launches : 0; }
+
+void srla_destroy(srla_t* h) {
+  if (!h) return;
+  if (h->st_copy) {
+    cudaStreamSynchronize(h->st);
+    cudaStreamDestroy(h->st_copy);
+  }
+  for (int q = 0; q < 2; q++)
+    if (h->slot[q].ev) cudaEventDestroy(h->slot[q].ev);
+  if (h->h_pinned) cudaFreeHost(h->h_pinned);
+  delete h;
+}
+
+const char* srla_strerror(int code) {
+  switch (code) {
+    case SRLA_OK: return "ok";
+    case SRLA_E_INVAL: return "invalid argument";
+    case SRLA_E_NOMEM: return "insufficient memory or buffer";
+    case SRLA_E_CAPACITY: return "per-slice capacity exceeded; results incomplete";
+    case SRLA_E_CUDA: return "CUDA runtime error";
+    case SRLA_E_ORDER: return "call out of order";
+    case SRLA_E_TIMEOUT: return "device wait timed out";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

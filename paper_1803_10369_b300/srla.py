@@ -1,0 +1,250 @@
+"""Thin Python binding of libsrla (include/srla.h): argument marshalling only.
+
+Every step of the method runs in the library's CUDA kernels.  PyTorch provides the device
+workspace and the stream.  There is no fallback: if the library cannot be built or loaded,
+or no CUDA device is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+MAX_ROWS = 16
+N_HASH = MAX_ROWS + 3
+
+OK, E_INVAL, E_NOMEM, E_CAPACITY, E_CUDA, E_ORDER, E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
+SUPER, SATURATED, CARRIED, NEW = 1, 2, 4, 8
+
+
+class srla_params(ctypes.Structure):
+    _fields_ = [
+        ("u", ctypes.c_uint32), ("v", ctypes.c_uint32), ("g", ctypes.c_uint32), ("gl", ctypes.c_uint32),
+        ("dr_bytes", ctypes.c_uint32), ("z", ctypes.c_uint32), ("k", ctypes.c_uint32), ("theta", ctypes.c_uint32),
+        ("start_slice", ctypes.c_uint64), ("staging_pkts", ctypes.c_uint64),
+        ("max_sampled", ctypes.c_uint32), ("max_candidates", ctypes.c_uint32),
+        ("hash_a", ctypes.c_uint64 * N_HASH), ("hash_b", ctypes.c_uint64 * N_HASH),
+    ]
+
+
+class srla_entry(ctypes.Structure):
+    _fields_ = [("aip", ctypes.c_uint32), ("w", ctypes.c_uint32), ("est", ctypes.c_float), ("flags", ctypes.c_uint32)]
+
+
+class srla_slice_stats(ctypes.Structure):
+    _fields_ = [
+        ("slice", ctypes.c_uint64), ("n_pkts", ctypes.c_uint64),
+        ("n_sampled", ctypes.c_uint32), ("n_new", ctypes.c_uint32), ("n_candidates", ctypes.c_uint32),
+        ("n_carry_out", ctypes.c_uint32), ("w_star", ctypes.c_uint32), ("overflow", ctypes.c_uint32),
+        ("up", ctypes.c_double), ("census", ctypes.c_uint64 * MAX_ROWS),
+    ]
+
+
+ENTRY_DTYPE = np.dtype([("aip", "<u4"), ("w", "<u4"), ("est", "<f4"), ("flags", "<u4")])
+assert ENTRY_DTYPE.itemsize == ctypes.sizeof(srla_entry)
+
+_lock = threading.Lock()
+_lib = None
+
+# Every symbol declared in include/srla.h, with its ctypes signature.
+_P = ctypes.c_void_p
+SIGNATURES = {
+    "srla_check_params": (ctypes.c_int, [_P]),
+    "srla_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "srla_derived": (ctypes.c_int, [_P, _P, _P, _P]),
+    "srla_create": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P]),
+    "srla_push_packets": (ctypes.c_int, [_P, _P, ctypes.c_uint64, ctypes.c_int]),
+    "srla_end_slice": (ctypes.c_int, [_P, _P]),
+    "srla_report": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_size_t, _P, _P]),
+    "srla_sync": (ctypes.c_int, [_P]),
+    "srla_state_bytes": (ctypes.c_size_t, [_P]),
+    "srla_export_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "srla_import_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    "srla_kernel_launches": (ctypes.c_uint64, [_P]),
+    "srla_destroy": (None, [_P]),
+    "srla_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+}
+
+
+def lib():
+    """Load (building first if needed) the in-tree libsrla.so."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+        return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+class SRLAError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        self.code = code
+        msg = lib().srla_strerror(code).decode()
+        super().__init__(f"{what}: {msg} ({code})")
+
+
+def _ck(code: int, what: str):
+    if code != OK:
+        raise SRLAError(code, what)
+
+
+def make_params(u, v, g, gl, dr_bytes, z, k, theta, hash_a, hash_b, start_slice=0, staging_pkts=0,
+                max_sampled=1 << 16, max_candidates=1 << 14) -> srla_params:
+    p = srla_params()
+    p.u, p.v, p.g, p.gl = u, v, g, gl
+    p.dr_bytes, p.z, p.k, p.theta = dr_bytes, z, k, theta
+    p.start_slice, p.staging_pkts = start_slice, staging_pkts
+    p.max_sampled, p.max_candidates = max_sampled, max_candidates
+    ha = np.asarray(hash_a, dtype=np.uint64).ravel()
+    hb = np.asarray(hash_b, dtype=np.uint64).ravel()
+    for r in range(min(N_HASH, ha.size)):
+        p.hash_a[r] = int(ha[r])
+        p.hash_b[r] = int(hb[r])
+    return p
+
+
+def params_for(w, hash_a, hash_b, **over) -> srla_params:
+    """Parameters of a synth.Workload-like object (fields u, v, g, gl, dr_bytes, z, k, theta...)."""
+    kw = dict(u=w.u, v=w.v, g=w.g, gl=w.gl, dr_bytes=w.dr_bytes, z=w.z, k=w.k, theta=w.theta,
+              start_slice=w.start_slice, max_sampled=w.max_sampled, max_candidates=w.max_candidates)
+    kw.update(over)
+    return make_params(hash_a=hash_a, hash_b=hash_b, **kw)
+
+
+def check_params(p: srla_params) -> int:
+    return lib().srla_check_params(ctypes.byref(p))
+
+
+def workspace_bytes(p: srla_params) -> int:
+    return lib().srla_workspace_bytes(ctypes.byref(p))
+
+
+def derived(p: srla_params):
+    tau, rg, pm = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32()
+    _ck(lib().srla_derived(ctypes.byref(p), ctypes.byref(tau), ctypes.byref(rg), ctypes.byref(pm)), "srla_derived")
+    return tau.value, rg.value, pm.value
+
+
+class Link:
+    """One monitored link: a sliding estimator array resident in a torch-owned workspace."""
+
+    def __init__(self, params: srla_params, device="cuda", stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libsrla needs a CUDA device")
+        self.params = params
+        self.L = lib()
+        nbytes = workspace_bytes(params)
+        if nbytes == 0:
+            raise SRLAError(E_INVAL, "srla_workspace_bytes")
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            h = ctypes.c_void_p()
+            _ck(self.L.srla_create(ctypes.byref(params), ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                   ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), "srla_create")
+        self._h = h
+        self._last = None
+
+    # -- packets ---------------------------------------------------------------
+    def push(self, pairs):
+        """pairs: (n, 2) uint32 packets: a CUDA tensor (read in place), or host memory (numpy
+        array or CPU tensor; pinned tensors give an asynchronous copy)."""
+        import torch
+
+        if isinstance(pairs, torch.Tensor):
+            if pairs.dtype not in (torch.int32, torch.uint32) or not pairs.is_contiguous():
+                raise ValueError("pairs must be a contiguous int32/uint32 tensor of shape (n, 2)")
+            n = pairs.numel() // 2
+            on_dev = 1 if pairs.is_cuda else 0
+            ptr = pairs.data_ptr()
+            self._keep = pairs
+        else:
+            arr = np.ascontiguousarray(pairs, dtype=np.uint32)
+            n = arr.size // 2
+            on_dev = 0
+            ptr = arr.ctypes.data
+            self._keep = arr
+        _ck(self.L.srla_push_packets(self._h, ctypes.c_void_p(ptr), n, on_dev), "srla_push_packets")
+
+    def end_slice(self) -> int:
+        sid = ctypes.c_uint64()
+        _ck(self.L.srla_end_slice(self._h, ctypes.byref(sid)), "srla_end_slice")
+        self._last = sid.value
+        return sid.value
+
+    def report(self, slice_id=None, cap=None, allow_overflow=False):
+        """Sorted report of a closed slice: dict of numpy arrays (aip, w, est, flags) + stats."""
+        if slice_id is None:
+            slice_id = self._last
+        if cap is None:
+            cap = self.params.max_candidates
+        out = np.zeros(cap, dtype=ENTRY_DTYPE)
+        n = ctypes.c_size_t()
+        st = srla_slice_stats()
+        rc = self.L.srla_report(self._h, slice_id, ctypes.c_void_p(out.ctypes.data), cap, ctypes.byref(n),
+                                ctypes.byref(st))
+        if rc != OK and not (allow_overflow and rc == E_CAPACITY):
+            raise SRLAError(rc, "srla_report")
+        m = min(n.value, cap)
+        e = out[:m]
+        stats = {f: getattr(st, f) for f, _ in srla_slice_stats._fields_ if f != "census"}
+        stats["census"] = np.array(st.census[: self.params.u], dtype=np.uint64)
+        return {"aip": e["aip"].copy(), "w": e["w"].copy(), "est": e["est"].copy(),
+                "flags": e["flags"].copy(), "stats": stats, "rc": rc}
+
+    def kernel_launches(self) -> int:
+        return self.L.srla_kernel_launches(self._h)
+
+    def sync(self):
+        _ck(self.L.srla_sync(self._h), "srla_sync")
+
+    # -- checkpoint --------------------------------------------------------------
+    def export_state(self) -> bytes:
+        n = self.L.srla_state_bytes(self._h)
+        buf = ctypes.create_string_buffer(n)
+        _ck(self.L.srla_export_state(self._h, buf, n), "srla_export_state")
+        return buf.raw
+
+    def import_state(self, blob: bytes):
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _ck(self.L.srla_import_state(self._h, buf, len(blob)), "srla_import_state")
+
+    def state_arrays(self):
+        """Exported state as (re[u, v, g], le[u, v, gl], slice, carried hosts), distances uint16."""
+        b = self.export_state()
+        p = self.params
+        hdr = np.frombuffer(b[:56], dtype=np.uint32)
+        slice_ = int(np.frombuffer(b[40:48], dtype=np.uint64)[0])
+        n_carry = int(hdr[12])
+        nre, nle = p.u * p.v * p.g, p.u * p.v * p.gl
+        d = np.frombuffer(b[56:56 + 2 * (nre + nle)], dtype=np.uint16)
+        re = d[:nre].reshape(p.u, p.v, p.g).copy()
+        le = d[nre:].reshape(p.u, p.v, p.gl).copy()
+        carry = np.frombuffer(b[56 + 2 * (nre + nle):56 + 2 * (nre + nle) + 4 * n_carry], dtype=np.uint32).copy()
+        return re, le, slice_, carry
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.L.srla_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,95 @@
+"""The C ABI without a GPU: the library loads, exports every declared symbol, its structs
+have the layout the header gives, and the host-side parameter logic (validation, sizes,
+derived constants) is right.  No compute call is made here."""
+import ctypes
+import os
+import re
+import subprocess
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_1803_10369_b300 import srla
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "srla.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(srla_[a-z_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol():
+    L = srla.lib()
+    names = _declared()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) <= set(srla.SIGNATURES)
+
+
+def test_struct_layout_matches_header(tmp_path):
+    prog = tmp_path / "sz.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "srla.h"\n'
+                    'int main(void){printf("%zu %zu %zu %zu %zu\\n", sizeof(srla_params), '
+                    'sizeof(srla_entry), sizeof(srla_slice_stats), offsetof(srla_params, hash_a), '
+                    'offsetof(srla_slice_stats, census));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.dirname(HEADER), "-o", str(exe), str(prog)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
+    want = [ctypes.sizeof(srla.srla_params), ctypes.sizeof(srla.srla_entry), ctypes.sizeof(srla.srla_slice_stats),
+            srla.srla_params.hash_a.offset, srla.srla_slice_stats.census.offset]
+    assert got == want
+
+
+def _params(**kw):
+    a, b = synth.hash_coefficients(1, 19)
+    base = dict(u=4, v=1024, g=64, gl=64, dr_bytes=1, z=8, k=4, theta=1024)
+    base.update(kw)
+    return srla.make_params(hash_a=a, hash_b=b, **base)
+
+
+def test_param_validation():
+    assert srla.check_params(_params()) == 0
+    bad = [dict(u=0), dict(u=17), dict(v=1000), dict(g=48), dict(gl=0), dict(dr_bytes=3), dict(z=9),
+           dict(dr_bytes=2, z=17), dict(k=0), dict(k=256), dict(z=3, k=8), dict(theta=0),
+           dict(g=2, dr_bytes=1), dict(v=1, g=4, gl=4)]
+    for kw in bad:
+        assert srla.check_params(_params(**kw)) == srla.E_INVAL, kw
+        assert srla.workspace_bytes(_params(**kw)) == 0
+    p = _params()
+    p.hash_a[3] = 0
+    assert srla.check_params(p) == srla.E_INVAL
+    p = _params()
+    p.hash_b[0] = synth.MERSENNE_61
+    assert srla.check_params(p) == srla.E_INVAL
+    # k = 2^z - 1 is the largest window a z-bit recorder can express (Section 3.2)
+    assert srla.check_params(_params(z=3, k=7)) == 0
+    assert srla.check_params(_params(z=1, k=1)) == 0
+
+
+def test_workspace_grows_with_sketch():
+    small = srla.workspace_bytes(_params())
+    big = srla.workspace_bytes(_params(v=1 << 14, gl=256, g=128, u=8, dr_bytes=2, z=16, k=300))
+    assert small > 4 * 1024 * 64 * 2
+    assert big > 8 * (1 << 14) * (256 + 128) * 2
+    assert small % 256 == 0
+
+
+def test_derived_constants_agree_with_the_oracle():
+    for g in (8, 16, 64, 128, 256):
+        for theta in (1, 7, 100, 1000, 1024, 1025, 5000, 1 << 20):
+            tau, rg, P = srla.derived(_params(g=g, theta=theta, v=64))
+            assert tau == oracle.tau(theta, g)
+            assert rg == oracle.rho_g(g)
+            assert P == 255
+
+
+def test_strerror():
+    L = srla.lib()
+    for c in range(0, -7, -1):
+        assert L.srla_strerror(c)

@@ -162,6 +162,34 @@ int srla_import_state(srla_t *h, const void *host_buf, size_t len);
 uint64_t srla_kernel_launches(const srla_t *h);
 
 void srla_destroy(srla_t *h);
+
+/*
+ * Allocation-free batch report (the paper has no counterpart; this is a service for callers).
+ *
+ * Some callers cannot allocate device memory: a packet-capture thread with real-time
+ * deadlines (cudaMalloc and cudaFree may synchronize the whole device), a plugin whose host
+ * framework owns all device memory and hands it only fixed input and output buffers, or code
+ * running while a stream is being captured.  This entry point needs no workspace and makes
+ * no device or host allocation: it runs the scan and the slice end of a fresh estimator
+ * over one device batch d_pairs (n_pairs interleaved aip, bip) on `stream`, i.e. the report
+ * that srla_create + srla_push_packets + srla_end_slice + srla_report give for a first slice
+ * holding exactly this batch, and copies it (sorted by aip) to the host buffer out
+ * (cap entries; *n_out = full count; stats may be NULL).  It returns when the report is on
+ * the host.
+ *
+ * Scratch: a fixed array of SRLA_STATIC_SCRATCH_BYTES compiled into the library, present on
+ * every GPU that loads the library until the process exits.  Parameters whose workspace
+ * (srla_workspace_bytes with a 2-packet staging area) exceeds it are rejected with
+ * SRLA_E_NOMEM before any GPU work.  The first call on a device looks up the array's device
+ * address (and sets a kernel attribute) for that device; make that first call before any
+ * stream capture.  Every call clears and reuses the same array, so calls that overlap on the
+ * GPU (other streams, other host threads) race and corrupt each other: serialize them.
+ * Errors: INVAL, NOMEM, CAPACITY (as srla_report), CUDA.
+ */
+#define SRLA_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int srla_batch_report_static(const srla_params *p, const uint32_t *d_pairs, uint64_t n_pairs,
+                             void *stream, srla_entry *out, size_t cap, size_t *n_out,
+                             srla_slice_stats *stats);
 const char *srla_strerror(int code);
 
 #ifdef __cplusplus

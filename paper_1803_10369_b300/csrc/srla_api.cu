@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -590,3 +591,108 @@ const char* srla_strerror(int code) {
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------ allocation-free batch report
+//
+// Some callers cannot allocate device memory at all: a capture thread with real-time
+// deadlines (cudaMalloc and cudaFree may synchronize the whole device), a plugin whose host
+// framework owns every device buffer and hands out only fixed input/output slots, or code
+// that runs while a stream is being captured.  For them, srla_batch_report_static runs the
+// scan and the slice end of a fresh estimator over one device batch with its workspace
+// carved out of a fixed scratch array compiled into this library, instead of a caller
+// workspace.  Every GPU that loads the library holds the array until the process exits.
+
+namespace {
+
+static __device__ __align__(256) unsigned char g_static_scratch[SRLA_STATIC_SCRATCH_BYTES];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_addr[kStaticMaxDevices];  // device address of g_static_scratch, per device
+
+// Once per device, with that device current: the device address of the scratch array (in
+// host code the array's name is only a host-side stand-in) and the shared-memory opt-in of
+// the single-block sort.
+int static_scratch_setup(int dev, void** out) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* addr = nullptr;
+    if (cudaGetSymbolAddress(&addr, g_static_scratch) != cudaSuccess || !addr) return cuda_err(cudaErrorUnknown);
+    if (cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmallSmem) !=
+        cudaSuccess)
+      return cuda_err(cudaErrorUnknown);
+    g_static_addr[dev] = addr;
+  }
+  *out = g_static_addr[dev];
+  return SRLA_OK;
+}
+
+template <typename CellT>
+int static_batch(srla_s* h, const uint32_t* d_pairs, uint64_t n_pairs) {
+  int r = SRLA_OK;
+  if (n_pairs && (r = launch_scan<CellT>(h, d_pairs, n_pairs)) != SRLA_OK) return r;
+  return launch_end_slice<CellT>(h);
+}
+
+}  // namespace
+
+extern "C" int srla_batch_report_static(const srla_params* p, const uint32_t* d_pairs, uint64_t n_pairs,
+                                        void* stream, srla_entry* out, size_t cap, size_t* n_out,
+                                        srla_slice_stats* stats) {
+  if (check(p) != SRLA_OK || (n_pairs && !d_pairs) || (cap && !out)) return SRLA_E_INVAL;
+  srla_params q = *p;
+  q.staging_pkts = 2;  // the batch is already on the device: no host staging area
+  const Layout L = layout_of(&q);
+  if (L.total > (size_t)SRLA_STATIC_SCRATCH_BYTES) return SRLA_E_NOMEM;
+  int dev = 0;
+  SRLA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kStaticMaxDevices) return SRLA_E_INVAL;
+  void* base = nullptr;
+  int r = static_scratch_setup(dev, &base);
+  if (r != SRLA_OK) return r;
+
+  srla_s h{};  // lives on this stack frame; no events, pinned buffers or streams are made
+  h.p = q;
+  h.L = L;
+  h.ws = static_cast<char*>(base);
+  h.st = static_cast<cudaStream_t>(stream);
+  const uint32_t tau = tau_of(q.theta, q.g);
+  h.geo = Geo{q.u, q.v, q.g, q.gl, q.v - 1, q.g - 1, q.gl - 1, q.k, (1u << q.z) - 1u,
+              tau >= 32 ? 0xFFFFFFFFu : ((1u << tau) - 1u), rho_g_of(q.g), q.theta};
+  for (int x = 0; x < SRLA_N_HASH; x++) {
+    h.coef.a[x] = q.hash_a[x];
+    h.coef.b[x] = q.hash_b[x];
+  }
+  h.k_is_P = (q.k == h.geo.P);
+  h.T = q.start_slice;
+  SRLA_TRY(cudaDeviceGetAttribute(&h.sms, cudaDevAttrMultiProcessorCount, dev));
+
+  // The array keeps the previous call's contents: the recorders, the sets and the control
+  // block must start at zero, so the whole used part is cleared first.
+  SRLA_TRY(cudaMemsetAsync(h.ws, 0, L.total, h.st));
+  Ctl c{};
+  c.T = h.T;
+  c.tm = (uint32_t)(h.T % h.geo.P);
+  c.w_star = h.geo.gl + 1;
+  SRLA_TRY(cudaMemcpyAsync(h.ctl(), &c, sizeof(Ctl), cudaMemcpyHostToDevice, h.st));
+  r = q.dr_bytes == 1 ? static_batch<uint8_t>(&h, d_pairs, n_pairs) : static_batch<uint16_t>(&h, d_pairs, n_pairs);
+  if (r != SRLA_OK) return r;
+
+  const int par = (int)(h.T & 1);
+  srla_slice_stats st;
+  SRLA_TRY(cudaMemcpyAsync(&st, h.ws + L.rep_stats[par], sizeof(st), cudaMemcpyDeviceToHost, h.st));
+  SRLA_TRY(cudaStreamSynchronize(h.st));
+  st.n_pkts = n_pairs;
+  const size_t n = st.n_candidates;
+  if (n_out) *n_out = n;
+  if (stats) *stats = st;
+  const size_t take = std::min(n, cap);
+  if (take) {
+    SRLA_TRY(cudaMemcpyAsync(out, h.ws + L.rep_entries[par], take * sizeof(srla_entry), cudaMemcpyDeviceToHost,
+                             h.st));
+    SRLA_TRY(cudaStreamSynchronize(h.st));
+  }
+  if (st.overflow) return SRLA_E_CAPACITY;
+  if (cap < n) return SRLA_E_NOMEM;
+  return SRLA_OK;
+}

@@ -66,7 +66,10 @@ SIGNATURES = {
     "srla_kernel_launches": (ctypes.c_uint64, [_P]),
     "srla_destroy": (None, [_P]),
     "srla_strerror": (ctypes.c_char_p, [ctypes.c_int]),
+    "srla_batch_report_static": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P, _P, ctypes.c_size_t, _P, _P]),
 }
+
+STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
 
 
 def lib():
@@ -248,3 +251,31 @@ class Link:
             self.close()
         except Exception:
             pass
+
+
+def batch_report_static(params: srla_params, pairs, stream=None, cap=None, allow_overflow=False):
+    """Report of one device batch through the allocation-free entry point (no workspace).
+
+    Same result as a fresh Link that pushes `pairs` and closes its first slice.  The library
+    keeps one fixed scratch array per GPU, so calls must not overlap on the device."""
+    import torch
+
+    if not (isinstance(pairs, torch.Tensor) and pairs.is_cuda and pairs.is_contiguous()):
+        raise ValueError("pairs must be a contiguous CUDA tensor of shape (n, 2)")
+    if stream is None:
+        stream = torch.cuda.current_stream(pairs.device)
+    if cap is None:
+        cap = params.max_candidates
+    out = np.zeros(cap, dtype=ENTRY_DTYPE)
+    n = ctypes.c_size_t()
+    st = srla_slice_stats()
+    rc = lib().srla_batch_report_static(ctypes.byref(params), ctypes.c_void_p(pairs.data_ptr()), pairs.numel() // 2,
+                                        ctypes.c_void_p(stream.cuda_stream), ctypes.c_void_p(out.ctypes.data), cap,
+                                        ctypes.byref(n), ctypes.byref(st))
+    if rc != OK and not (allow_overflow and rc == E_CAPACITY):
+        raise SRLAError(rc, "srla_batch_report_static")
+    e = out[:min(n.value, cap)]
+    stats = {f: getattr(st, f) for f, _ in srla_slice_stats._fields_ if f != "census"}
+    stats["census"] = np.array(st.census[: params.u], dtype=np.uint64)
+    return {"aip": e["aip"].copy(), "w": e["w"].copy(), "est": e["est"].copy(), "flags": e["flags"].copy(),
+            "stats": stats, "rc": rc}

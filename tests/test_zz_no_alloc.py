@@ -1,0 +1,61 @@
+"""The allocation-free entry point (srla_batch_report_static) against the workspace path.
+
+Callers that cannot allocate device memory (real-time capture threads, plugins that only
+get fixed buffers from their host framework, code inside a stream capture) use one fixed
+scratch array compiled into the library.  Its report for a device batch must equal what a
+freshly created estimator reports after pushing that batch and closing its first slice.
+Two calls in a row check that the shared scratch is cleared between calls.  This file sorts
+last so that a failure here does not hide the rest of the suite.
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_helpers import EST_RTOL
+from paper_1803_10369_b300 import srla
+
+pytestmark = pytest.mark.gpu
+
+
+def _same(a, b, where):
+    assert a["aip"].tolist() == b["aip"].tolist(), where
+    assert np.array_equal(a["w"], b["w"]) and np.array_equal(a["flags"], b["flags"]), where
+    ea, eb = a["est"].astype(np.float64), b["est"].astype(np.float64)
+    assert np.array_equal(np.isinf(ea), np.isinf(eb)), where
+    fin = ~np.isinf(eb)
+    assert (np.abs(ea[fin] - eb[fin]) <= EST_RTOL * np.abs(eb[fin])).all(), where
+    for key in ("n_sampled", "n_new", "n_candidates", "n_carry_out", "w_star", "overflow", "n_pkts"):
+        assert a["stats"][key] == b["stats"][key], (where, key)
+    assert np.array_equal(a["stats"]["census"], b["stats"]["census"]), where
+
+
+@pytest.mark.parametrize("variant", ["tiny", "tiny-2byte-theta128"])
+def test_static_scratch_report_matches_workspace_path(variant, cuda_device):
+    w = synth.workload("tiny")
+    if variant != "tiny":
+        w = w.replace(dr_bytes=2, z=16, k=8, theta=128)
+    ha, hb = synth.hash_coefficients(w.hash_seed, w.u + 3)
+    params = srla.params_for(w, ha, hb)
+    assert srla.workspace_bytes(params) < srla.STATIC_SCRATCH_BYTES
+    for call in range(2):  # two calls in a row, different batches
+        pk = synth.generate_slice(w.traffic, 3 + call, device=cuda_device)
+        got = srla.batch_report_static(params, pk)
+        link = srla.Link(params, device=cuda_device)
+        link.push(pk)
+        want = link.report(link.end_slice())
+        link.close()
+        assert want["stats"]["n_candidates"] > 0
+        _same(got, want, f"{variant} call {call}")
+
+
+def test_static_scratch_rejects_oversized_parameters(cuda_device):
+    import torch
+
+    w = synth.workload("paper")
+    ha, hb = synth.hash_coefficients(w.hash_seed, w.u + 3)
+    params = srla.params_for(w, ha, hb)
+    assert srla.workspace_bytes(params) > srla.STATIC_SCRATCH_BYTES
+    pk = torch.zeros((16, 2), dtype=torch.int32, device=cuda_device)
+    with pytest.raises(srla.SRLAError) as e:
+        srla.batch_report_static(params, pk)
+    assert e.value.code == srla.E_NOMEM

@@ -323,6 +323,7 @@ def bench_srla(args):
         "e2e": {"value": round(e2e, 3), "unit": "Mpkts/s", "h2d_bytes_per_step": int(8 * per_launch_pkts),
                 "d2h_bytes_per_step": int(statistics.mean(d2h))},
         "gpu_launches": int(launches),
+        "slice_end_graph": link.uses_graph(),
         "clocks": clk.summary(),
         "prefill_slices": prefill,
     }

@@ -36,7 +36,7 @@ extern "C" {
 #define SRLA_E_CAPACITY (-3)        /* a per-slice capacity was exceeded; results incomplete */
 #define SRLA_E_CUDA (-4)            /* a CUDA runtime call failed */
 #define SRLA_E_ORDER (-5)           /* call out of order (see each entry point) */
-#define SRLA_E_TIMEOUT (-6)         /* a bounded device wait gave up */
+#define SRLA_E_TIMEOUT (-6)         /* a bounded device wait gave up; results invalid */
 
 /* Report flags. */
 #define SRLA_SUPER 1u               /* estimate >= theta (Definition 2), or saturated */
@@ -89,7 +89,8 @@ typedef struct srla_slice_stats {
   uint32_t n_candidates;     /* report length (new and carried, de-duplicated) */
   uint32_t n_carry_out;      /* hosts carried into the next slice (Algorithm 3) */
   uint32_t w_star;           /* least w whose estimate is >= theta (gl + 1 if none) */
-  uint32_t overflow;         /* bit 0: max_sampled exceeded; bit 1: max_candidates exceeded */
+  uint32_t overflow;         /* bit 0: max_sampled exceeded; bit 1: max_candidates exceeded;
+                                bit 2: a device-side wait timed out */
   double up;                 /* UP of Eq. 8 */
   uint64_t census[SRLA_MAX_ROWS]; /* |LDR(i)|^k of Section 4.2, per row */
 } srla_slice_stats;
@@ -139,7 +140,8 @@ int srla_end_slice(srla_t *h, uint64_t *slice_id);
  * most recently closed slices can be reported; older ones give SRLA_E_ORDER.  Up to cap
  * entries are written to out (out may be NULL when cap is 0); *n_out receives the full
  * count.  stats may be NULL.  Returns SRLA_E_CAPACITY when a per-slice capacity overflowed
- * (the entries are then those that fit), SRLA_E_NOMEM when cap < *n_out.
+ * (the entries are then those that fit), SRLA_E_NOMEM when cap < *n_out, SRLA_E_TIMEOUT when
+ * a bounded device-side wait of the slice end gave up (stats.overflow bit 2).
  */
 int srla_report(srla_t *h, uint64_t slice_id, srla_entry *out, size_t cap, size_t *n_out,
                 srla_slice_stats *stats);
@@ -160,6 +162,10 @@ int srla_import_state(srla_t *h, const void *host_buf, size_t len);
 
 /* Number of CUDA kernels this handle has launched since srla_create (all entry points). */
 uint64_t srla_kernel_launches(const srla_t *h);
+
+/* 1 if srla_end_slice replays a CUDA graph captured at srla_create (one per slice parity),
+ * 0 if it launches its kernels one by one (capture was not possible on this device). */
+int srla_uses_graph(const srla_t *h);
 
 void srla_destroy(srla_t *h);
 

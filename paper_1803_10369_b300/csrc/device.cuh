@@ -40,7 +40,10 @@ struct Ctl {
   unsigned int cat_count[2];      // candidate list length, by slice parity
   unsigned int overflow;          // SRLA overflow bits of the open slice
   unsigned int overflow_next;     // overflow bits raised for the next slice (carry list)
-  double up;                      // Eq. 8 of the open slice
+  unsigned int blocks_done;       // blocks of the estimate kernel that have finished
+  unsigned int bar_count;         // grid barrier of the cooperative sort: arrivals
+  unsigned int bar_gen;           // grid barrier of the cooperative sort: generation
+  unsigned int pad1;
   unsigned long long census[SRLA_MAX_ROWS];
 };
 
@@ -210,6 +213,58 @@ __device__ __forceinline__ uint32_t union_count(const CellT* __restrict__ arr, u
   if (R >= 128) return union_count_w<CellT, 4>(arr, v, cells, u, mycol, tm, P, lim, lane);
   if (R >= 64) return union_count_w<CellT, 2>(arr, v, cells, u, mycol, tm, P, lim, lane);
   return union_count_w<CellT, 1>(arr, v, cells, u, mycol, tm, P, lim, lane);
+}
+
+// Same count as union_count, for a caller that only needs to know whether it reaches
+// `need`: rows are joined one at a time and the join stops as soon as fewer than `need`
+// cells remain inside the window in every row so far (the union can only shrink).  The
+// result is exact when it is >= need; below need it is some value < need.
+template <typename CellT, int WPL>
+__device__ __forceinline__ uint32_t union_count_atleast_w(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
+                                                          uint32_t u, uint32_t mycol, uint32_t tm, uint32_t P,
+                                                          uint32_t lim, uint32_t need, int lane) {
+  const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;
+  const uint32_t w0 = (uint32_t)lane * WPL;
+  const bool ok = w0 < R;
+  uint32_t m[WPL];
+#pragma unroll
+  for (int q = 0; q < WPL; q++) m[q] = ok ? 0xFFFFFFFFu : 0u;
+  uint32_t total = 0;
+  for (uint32_t i = 0; i < u; i++) {
+    const uint32_t c = __shfl_sync(kFull, mycol, (int)i);
+    const uint32_t* run = reinterpret_cast<const uint32_t*>(arr + ((size_t)i * v + c) * cells);
+    if (ok) {
+      uint32_t wd[WPL];
+      if constexpr (WPL == 4) {
+        const uint4 q4 = __ldg(reinterpret_cast<const uint4*>(run + w0));
+        wd[0] = q4.x; wd[1] = q4.y; wd[2] = q4.z; wd[3] = q4.w;
+      } else if constexpr (WPL == 2) {
+        const uint2 q2 = __ldg(reinterpret_cast<const uint2*>(run + w0));
+        wd[0] = q2.x; wd[1] = q2.y;
+      } else {
+        wd[0] = __ldg(run + w0);
+      }
+#pragma unroll
+      for (int q = 0; q < WPL; q++) m[q] &= window_bits<CellT>(wd[q], tm, P, lim);
+    }
+    uint32_t part = 0;
+#pragma unroll
+    for (int q = 0; q < WPL; q++) part += __popc(m[q]);
+    total = warp_sum(part);
+    if (total < need) break;  // warp-uniform
+  }
+  return total;
+}
+
+template <typename CellT>
+__device__ __forceinline__ uint32_t union_count_atleast(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
+                                                        uint32_t u, uint32_t mycol, uint32_t tm, uint32_t P,
+                                                        uint32_t lim, uint32_t need, int lane) {
+  const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;
+  if (R <= 32) return union_count_atleast_w<CellT, 1>(arr, v, cells, u, mycol, tm, P, lim, need, lane);
+  if (R <= 64) return union_count_atleast_w<CellT, 2>(arr, v, cells, u, mycol, tm, P, lim, need, lane);
+  if (R <= 128) return union_count_atleast_w<CellT, 4>(arr, v, cells, u, mycol, tm, P, lim, need, lane);
+  return union_count<CellT>(arr, v, cells, u, mycol, tm, P, lim, lane);
 }
 
 }  // namespace srla

@@ -15,80 +15,139 @@ namespace srla {
 // SRE recorder selected by bip in the same estimators and add aip to the slice's set of
 // sampled hosts.  All writers of a slice write the same stamp, so plain stores are
 // race-free (Section 4.3 makes the same observation for its bits and recorders).
+//
+// A pair seen again in the same slice writes exactly the same stamps into exactly the same
+// recorders and samples the same host, so it can be skipped.  Each block keeps the pairs it
+// scanned last in a small direct-mapped table in shared memory; hot pairs (heavy sources
+// talk to few peers) then cost one shared-memory probe instead of u + u/2^tau scattered
+// stores that would all land on the same L2 sectors.
+
+constexpr int kSeenLog2 = 12;
+constexpr int kSeen = 1 << kSeenLog2;                      // pairs remembered per block
+constexpr unsigned long long kNoPair = ~0ull;              // empty slot; that pair is never cached
+constexpr int kScanThreads = 256;
+
+__device__ __forceinline__ uint32_t seen_slot(unsigned long long key) {
+  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - kSeenLog2));
+}
+
 template <typename CellT>
 __device__ __forceinline__ void scan_pair(uint32_t aip, uint32_t bip, bool ok, const Geo& geo,
                                           const Coef& coef, CellT code, CellT* __restrict__ re,
                                           CellT* __restrict__ le, Ctl* __restrict__ ctl,
                                           unsigned long long* __restrict__ utab, uint32_t umask,
                                           uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag,
-                                          int lane) {
-  const uint32_t u = geo.u;
-  const uint32_t jl = hash61(coef.a[u], coef.b[u], bip) & geo.glmask;
-  const uint32_t jr = hash61(coef.a[u + 1], coef.b[u + 1], bip) & geo.gmask;
-  const uint32_t hs = hash61(coef.a[u + 2], coef.b[u + 2], bip);
-  const bool samp = ok && ((hs & geo.samp_mask) == 0);
-#pragma unroll 4
-  for (uint32_t i = 0; i < u; i++) {
-    const uint32_t c = hash61(coef.a[i], coef.b[i], aip) & geo.vmask;
-    const size_t se = (size_t)i * geo.v + c;
-    if (ok) le[se * geo.gl + jl] = code;
-    if (samp) re[se * geo.g + jr] = code;
+                                          int lane, volatile unsigned long long* seen) {
+  if (ok) {
+    const unsigned long long key = ((unsigned long long)aip << 32) | bip;
+    if (key != kNoPair) {
+      const uint32_t h = seen_slot(key);
+      if (seen[h] == key)
+        ok = false;  // already scanned in this slice by this block
+      else
+        seen[h] = key;
+    }
   }
-  // Add aip to the slice's sampled-host set once per warp (same-source lanes agree first).
+  const uint32_t u = geo.u;
+  bool samp = false;
+  if (ok) {
+    const uint32_t jl = hash61(coef.a[u], coef.b[u], bip) & geo.glmask;
+    const uint32_t jr = hash61(coef.a[u + 1], coef.b[u + 1], bip) & geo.gmask;
+    const uint32_t hs = hash61(coef.a[u + 2], coef.b[u + 2], bip);
+    samp = (hs & geo.samp_mask) == 0;
+#pragma unroll 4
+    for (uint32_t i = 0; i < u; i++) {
+      const uint32_t c = hash61(coef.a[i], coef.b[i], aip) & geo.vmask;
+      const size_t se = (size_t)i * geo.v + c;
+      le[se * geo.gl + jl] = code;
+      if (samp) re[se * geo.g + jr] = code;
+    }
+  }
+  // Add aip to the slice's sampled-host set: one probe per distinct host of the warp, one
+  // append counter update per warp.
   const unsigned sm = __ballot_sync(kFull, samp);
+  int r = -2;
   if (samp) {
     const unsigned peers = __match_any_sync(sm, aip);
     if ((peers & ((1u << lane) - 1u)) == 0) {
       uint32_t slot;
-      const int r = set_insert(utab, umask, tag, aip, &slot);
-      if (r == 1) {
-        const unsigned idx = atomicAdd(&ctl->n_sampled, 1u);
-        if (idx < umax)
-          ulist[idx] = aip;
-        else
-          atomicOr(&ctl->overflow, 1u);
-      } else if (r < 0) {
+      r = set_insert(utab, umask, tag, aip, &slot);
+      if (r < 0) atomicOr(&ctl->overflow, 1u);
+    }
+  }
+  const unsigned ins = __ballot_sync(kFull, r == 1);
+  if (ins) {
+    const int first = __ffs(ins) - 1;
+    unsigned base = 0;
+    if (lane == first) base = atomicAdd(&ctl->n_sampled, (unsigned)__popc(ins));
+    base = __shfl_sync(kFull, base, first);
+    if (r == 1) {
+      const unsigned idx = base + (unsigned)__popc(ins & ((1u << lane) - 1u));
+      if (idx < umax)
+        ulist[idx] = aip;
+      else
         atomicOr(&ctl->overflow, 1u);
-      }
+    }
+  }
+}
+
+template <bool kVec>
+__device__ __forceinline__ void load_pairs(const uint32_t* __restrict__ pairs, uint64_t n, uint64_t base, int lane,
+                                           uint32_t a[4], uint32_t b[4], bool ok[4]) {
+#pragma unroll
+  for (int h = 0; h < 2; h++) {
+    const uint64_t p = base + (uint64_t)h * 64 + (uint64_t)lane * 2;
+    if (kVec && p + 1 < n) {
+      const uint4 q = __ldcs(reinterpret_cast<const uint4*>(pairs) + (p >> 1));
+      a[2 * h] = q.x; b[2 * h] = q.y; a[2 * h + 1] = q.z; b[2 * h + 1] = q.w;
+      ok[2 * h] = true; ok[2 * h + 1] = true;
+    } else {
+      ok[2 * h] = p < n;
+      ok[2 * h + 1] = p + 1 < n;
+      a[2 * h] = ok[2 * h] ? pairs[2 * p] : 0u;
+      b[2 * h] = ok[2 * h] ? pairs[2 * p + 1] : 0u;
+      a[2 * h + 1] = ok[2 * h + 1] ? pairs[2 * p + 2] : 0u;
+      b[2 * h + 1] = ok[2 * h + 1] ? pairs[2 * p + 3] : 0u;
     }
   }
 }
 
 // Packets are read as 16-byte vectors (two pairs) when the batch is 16-byte aligned.
-// Each warp iteration covers 128 packets: lane l holds packets 2l, 2l+1, 64+2l, 65+2l.
+// Each warp iteration covers 128 packets: lane l holds packets 2l, 2l+1, 64+2l, 65+2l; the
+// next iteration's packets are loaded before the current ones are scanned.
 template <typename CellT, bool kVec>
-__global__ void __launch_bounds__(256) k_scan(const uint32_t* __restrict__ pairs, uint64_t n, Geo geo,
-                                              const __grid_constant__ Coef coef, CellT* __restrict__ re, CellT* __restrict__ le,
-                                              Ctl* __restrict__ ctl, unsigned long long* __restrict__ utab,
-                                              uint32_t umask, uint32_t* __restrict__ ulist, uint32_t umax) {
+__global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restrict__ pairs, uint64_t n, Geo geo,
+                                                       const __grid_constant__ Coef coef, CellT* __restrict__ re,
+                                                       CellT* __restrict__ le, Ctl* __restrict__ ctl,
+                                                       unsigned long long* __restrict__ utab, uint32_t umask,
+                                                       uint32_t* __restrict__ ulist, uint32_t umax) {
+  __shared__ unsigned long long seen_mem[kSeen];
+  volatile unsigned long long* seen = seen_mem;
+  for (int x = threadIdx.x; x < kSeen; x += blockDim.x) seen[x] = kNoPair;
+  __syncthreads();
   const uint32_t tm = ctl->tm;
   const CellT code = (CellT)(tm + 1u);
   const uint32_t tag = slice_tag(ctl->T);
   const int lane = threadIdx.x & 31;
   const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  for (uint64_t base = gw * 128; base < n; base += nw * 128) {
-    uint32_t a[4], b[4];
-    bool ok[4];
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      const uint64_t p = base + (uint64_t)h * 64 + (uint64_t)lane * 2;
-      if (kVec && p + 1 < n) {
-        const uint4 q = __ldcs(reinterpret_cast<const uint4*>(pairs) + (p >> 1));
-        a[2 * h] = q.x; b[2 * h] = q.y; a[2 * h + 1] = q.z; b[2 * h + 1] = q.w;
-        ok[2 * h] = true; ok[2 * h + 1] = true;
-      } else {
-        ok[2 * h] = p < n;
-        ok[2 * h + 1] = p + 1 < n;
-        a[2 * h] = ok[2 * h] ? pairs[2 * p] : 0u;
-        b[2 * h] = ok[2 * h] ? pairs[2 * p + 1] : 0u;
-        a[2 * h + 1] = ok[2 * h + 1] ? pairs[2 * p + 2] : 0u;
-        b[2 * h + 1] = ok[2 * h + 1] ? pairs[2 * p + 3] : 0u;
-      }
-    }
+  uint64_t base = gw * 128;
+  uint32_t a[4], b[4];
+  bool ok[4];
+  load_pairs<kVec>(pairs, n, base, lane, a, b, ok);
+  while (base < n) {
+    const uint64_t next = base + nw * 128;
+    uint32_t na[4], nb[4];
+    bool nok[4];
+    load_pairs<kVec>(pairs, n, next, lane, na, nb, nok);
 #pragma unroll
     for (int j = 0; j < 4; j++)
-      scan_pair<CellT>(a[j], b[j], ok[j], geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+      scan_pair<CellT>(a[j], b[j], ok[j], geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, seen);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      a[j] = na[j]; b[j] = nb[j]; ok[j] = nok[j];
+    }
+    base = next;
   }
 }
 
@@ -101,7 +160,8 @@ __global__ void __launch_bounds__(256) k_scan(const uint32_t* __restrict__ pairs
 // point where a distance saturates at 2^z - 1.
 template <typename CellT>
 __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, CellT* __restrict__ le,
-                                               Ctl* __restrict__ ctl, int do_census, int do_reset) {
+                                               Ctl* __restrict__ ctl, int do_census, int do_reset,
+                                               int after_close) {
   const uint32_t y = blockIdx.y;
   const bool is_le = y < geo.u;
   if (!is_le && !do_reset) return;
@@ -111,7 +171,8 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
   uint4* base = reinterpret_cast<uint4*>((is_le ? le : re) + (size_t)row * cells);
   const size_t nvec = cells * sizeof(CellT) / 16;
   const uint32_t tm = ctl->tm, P = geo.P, k = geo.k;
-  const uint32_t alias = 1u + ((tm + 1u == P) ? 0u : tm + 1u);
+  // stamp of the slice that opens next: after the slice was closed, that is the open slice
+  const uint32_t alias = 1u + (after_close ? tm : ((tm + 1u == P) ? 0u : tm + 1u));
   const uint32_t splat = sizeof(CellT) == 1 ? alias * 0x01010101u : alias * 0x00010001u;
   uint32_t cnt = 0;
   for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < nvec; x += (size_t)gridDim.x * blockDim.x) {
@@ -145,48 +206,18 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
   }
 }
 
-// ------------------------------------------------------------------- estimator table
-//
-// Eq. 8 (UP from the row census) and Eq. 9 for every possible union weight w in [0, gl],
-// in FP64, rounded once to FP32.  For a fixed slice the estimate depends on w alone, so the
-// per-candidate work is a table lookup.  Edges: w <= gl*UP gives 0; w = gl or UP = 1 gives
-// +inf (saturated).  The super point decision (estimate >= theta, Definition 2) is taken
-// here in FP64 and stored with the entry.
-__global__ void k_lut(Geo geo, Ctl* __restrict__ ctl, float* __restrict__ lut_est, uint32_t* __restrict__ lut_flags) {
-  double up = 1.0;
-  const double cells = (double)geo.gl * (double)geo.v;
-  for (uint32_t i = 0; i < geo.u; i++) up *= (double)ctl->census[i] / cells;
-  const uint32_t w = blockIdx.x * blockDim.x + threadIdx.x;
-  if (w == 0) ctl->up = up;
-  if (w > geo.gl) return;
-  const double g = (double)geo.gl;
-  double est;
-  uint32_t f = 0;
-  if (w == geo.gl || up >= 1.0) {
-    est = INFINITY;
-    f = SRLA_SATURATED | SRLA_SUPER;
-  } else if ((double)w <= g * up) {
-    est = 0.0;
-  } else {
-    est = -g * log(1.0 - ((double)w - g * up) / (g * (1.0 - up)));
-    if (est >= (double)geo.theta) f = SRLA_SUPER;
-  }
-  lut_est[w] = (float)est;
-  lut_flags[w] = f;
-  if (f & SRLA_SUPER) atomicMin(&ctl->w_star, w);
-}
-
 // -------------------------------------------------------------- new candidates (b3)
 //
 // For every distinct host sampled in the open slice: |URE(aip)|^k at the end of the slice
 // (before the slide).  Hosts with at least ceil(rho*g) in-window union cells enter the
 // slice's candidate set, which already holds the hosts carried from the previous slice.
 template <typename CellT>
-__global__ void __launch_bounds__(256) k_filter(Geo geo, const __grid_constant__ Coef coef, const CellT* __restrict__ re,
-                                                Ctl* __restrict__ ctl, const uint32_t* __restrict__ ulist,
-                                                uint32_t umax, unsigned long long* ctab0,
-                                                unsigned long long* ctab1, uint32_t* cflags0, uint32_t* cflags1,
-                                                uint32_t cmask, uint32_t* clist0, uint32_t* clist1, uint32_t cmax) {
+__global__ void __launch_bounds__(256) k_filter(Geo geo, const __grid_constant__ Coef coef,
+                                                const CellT* __restrict__ re, Ctl* __restrict__ ctl,
+                                                const uint32_t* __restrict__ ulist, uint32_t umax,
+                                                unsigned long long* ctab0, unsigned long long* ctab1,
+                                                uint32_t* cflags0, uint32_t* cflags1, uint32_t cmask,
+                                                uint32_t* clist0, uint32_t* clist1, uint32_t cmax) {
   const unsigned long long T = ctl->T;
   const int par = (int)(T & 1);
   unsigned long long* ctab = par ? ctab1 : ctab0;
@@ -201,7 +232,7 @@ __global__ void __launch_bounds__(256) k_filter(Geo geo, const __grid_constant__
   for (uint32_t idx = gw; idx < n; idx += nw) {
     const uint32_t aip = ulist[idx];
     const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
-    const uint32_t cnt = union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, tm, geo.P, geo.k, lane);
+    const uint32_t cnt = union_count_atleast<CellT>(re, geo.v, geo.g, geo.u, mycol, tm, geo.P, geo.k, geo.rho_g, lane);
     if (lane == 0 && cnt >= geo.rho_g) {
       atomicAdd(&ctl->n_new, 1u);
       uint32_t slot;
@@ -222,21 +253,49 @@ __global__ void __launch_bounds__(256) k_filter(Geo geo, const __grid_constant__
   }
 }
 
-// ------------------------------------------------------ estimate (b4) and carry (b5)
+// ------------------------------------------------------------- Eq. 8 and Eq. 9 (b2)
 //
-// For every candidate of the sorted list: w = |ULE(aip)|^k (Algorithm 1), the estimate
-// and super point flag from the slice's table (Eq. 9), and the report entry at the same
-// position.  Then the carry test of Algorithm 3 on the post-slide SRE (age + 1 < k); hosts
-// that pass join the next slice's candidate set.
+// UP = prod_i |LDR(i)|^k / (g' v) from the row census, and Eq. 9 for a union weight w, both
+// in FP64; the estimate is rounded once to FP32 when reported.  Edges: w <= g' UP gives 0;
+// w = g' or UP = 1 gives +inf (saturated).  The super point decision (estimate >= theta,
+// Definition 2) is taken in FP64.
+__device__ __forceinline__ double slice_up(const Geo& geo, const Ctl* ctl) {
+  const double cells = (double)geo.gl * (double)geo.v;
+  double up = 1.0;
+  for (uint32_t i = 0; i < geo.u; i++) up *= (double)ctl->census[i] / cells;
+  return up;
+}
+
+__device__ __forceinline__ double eq9(uint32_t w, uint32_t gl, double up, uint32_t theta, uint32_t* flags) {
+  const double g = (double)gl;
+  if (w == gl || up >= 1.0) {
+    *flags = SRLA_SATURATED | SRLA_SUPER;
+    return INFINITY;
+  }
+  *flags = 0;
+  if ((double)w <= g * up) return 0.0;
+  const double est = -g * log(1.0 - ((double)w - g * up) / (g * (1.0 - up)));
+  if (est >= (double)theta) *flags = SRLA_SUPER;
+  return est;
+}
+
+// -------------------------------------------------- estimate (b4), carry (b5), close
+//
+// For every candidate of the sorted list: w = |ULE(aip)|^k (Algorithm 1), the Eq. 9
+// estimate and super point flag, and the report entry at the same position.  Then the carry
+// test of Algorithm 3 on the post-slide SRE (age + 1 < k); hosts that pass join the next
+// slice's candidate set.  The last block to finish closes the slice: it writes the slice's
+// statistics and opens the next slice in the control block.
 template <typename CellT>
-__global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant__ Coef coef, const CellT* __restrict__ re,
-                                                  const CellT* __restrict__ le, Ctl* __restrict__ ctl,
-                                                  const float* __restrict__ lut_est,
-                                                  const uint32_t* __restrict__ lut_flags,
-                                                  unsigned long long* ctab0, unsigned long long* ctab1,
-                                                  uint32_t* cflags0, uint32_t* cflags1, uint32_t cmask,
-                                                  uint32_t* clist0, uint32_t* clist1, uint32_t cmax,
-                                                  srla_entry* rep0, srla_entry* rep1) {
+__global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant__ Coef coef,
+                                                  const CellT* __restrict__ re, const CellT* __restrict__ le,
+                                                  Ctl* __restrict__ ctl, unsigned long long* ctab0,
+                                                  unsigned long long* ctab1, uint32_t* cflags0, uint32_t* cflags1,
+                                                  uint32_t cmask, uint32_t* clist0, uint32_t* clist1, uint32_t cmax,
+                                                  srla_entry* rep0, srla_entry* rep1, srla_slice_stats* st0,
+                                                  srla_slice_stats* st1, uint32_t umax) {
+  __shared__ double s_up;
+  __shared__ int s_last;
   const unsigned long long T = ctl->T;
   const int par = (int)(T & 1);
   const unsigned long long* ctab = par ? ctab1 : ctab0;
@@ -250,6 +309,9 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
   const uint32_t n = min(ctl->cat_count[par], cmax);
   const uint32_t tm = ctl->tm;
   const uint32_t klim_post = geo.k - 1u;  // age + 1 < k after the slide
+  if (threadIdx.x == 0) s_up = slice_up(geo, ctl);
+  __syncthreads();
+  const double up = s_up;
   const int lane = threadIdx.x & 31;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -261,11 +323,13 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
     if (lane == 0) {
       const uint32_t s = set_find(ctab, cmask, tag, aip);
       const uint32_t origin = (s != 0xFFFFFFFFu) ? cflags[s] : 0u;
+      uint32_t ef;
+      const double est = eq9(w, geo.gl, up, geo.theta, &ef);
       srla_entry e;
       e.aip = aip;
       e.w = w;
-      e.est = lut_est[w];
-      e.flags = origin | lut_flags[w];
+      e.est = (float)est;
+      e.flags = origin | ef;
       rep[idx] = e;
       if (cw >= geo.rho_g) {
         uint32_t slot;
@@ -283,24 +347,33 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
       }
     }
   }
-}
-
-// ------------------------------------------------------------------ close the slice
-__global__ void k_finish(Geo geo, Ctl* __restrict__ ctl, srla_slice_stats* st0, srla_slice_stats* st1,
-                         uint32_t umax, uint32_t cmax) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const unsigned long long T = ctl->T;
-  const int par = (int)(T & 1);
+  // the last block to get here closes the slice
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&ctl->blocks_done, 1u) == gridDim.x - 1u;
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
   srla_slice_stats* st = par ? st1 : st0;
   st->slice = T;
   st->n_pkts = 0;
   st->n_sampled = min(ctl->n_sampled, umax);
   st->n_new = ctl->n_new;
-  st->n_candidates = min(ctl->cat_count[par], cmax);
+  st->n_candidates = n;
   st->n_carry_out = min(ctl->cat_count[par ^ 1], cmax);
-  st->w_star = ctl->w_star;
+  // least w whose estimate reaches theta (Eq. 9 is increasing in w): binary search
+  uint32_t lo = 0, hi = geo.gl;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi) / 2;
+    uint32_t f;
+    eq9(mid, geo.gl, up, geo.theta, &f);
+    if (f & SRLA_SUPER) hi = mid; else lo = mid + 1;
+  }
+  st->w_star = lo;
   st->overflow = ctl->overflow;
-  st->up = ctl->up;
+  st->up = up;
   for (int i = 0; i < SRLA_MAX_ROWS; i++) {
     st->census[i] = ctl->census[i];
     ctl->census[i] = 0;
@@ -312,7 +385,9 @@ __global__ void k_finish(Geo geo, Ctl* __restrict__ ctl, srla_slice_stats* st0, 
   ctl->cat_count[par] = 0;
   ctl->overflow = ctl->overflow_next;
   ctl->overflow_next = 0;
-  ctl->w_star = geo.gl + 1u;
+  ctl->blocks_done = 0;
+  ctl->bar_count = 0;
+  __threadfence();
 }
 
 // ------------------------------------------------------------------- checkpointing

@@ -126,39 +126,64 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_small(const Ctl* __restri
   for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) list[x] = bufA[x];
 }
 
-// Multi-tile pass, step 1: digit histogram of every tile, stored digit-major
-// (hist[d * ntiles + t]) so that one exclusive scan yields every scatter offset.
-__global__ void __launch_bounds__(kSortThreads) k_radix_hist(const Ctl* __restrict__ ctl, uint32_t* l0,
-                                                             uint32_t* l1, uint32_t* tmp, uint32_t cmax,
-                                                             int pass, uint32_t* __restrict__ hist) {
-  const uint32_t n = sort_len(ctl, cmax);
-  if (n <= (uint32_t)kSortTile) return;
-  const uint32_t* src = (pass & 1) ? tmp : sort_list(ctl, l0, l1);
-  const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
-  __shared__ uint32_t cnt[kRadix];
+// Lists longer than one tile: one cooperative kernel runs the four passes, each as three
+// phases separated by grid barriers -- digit histogram of every tile (stored digit-major,
+// hist[d * ntiles + t], so one exclusive scan yields every scatter offset), the scan by
+// block 0, and the stable scatter of every tile.  The launch is cooperative, so all blocks
+// are resident; the barrier still gives up after a bounded wait and flags SRLA_E_TIMEOUT.
+
+constexpr unsigned kBarrierSpinLimit = 1u << 24;
+
+// Returns false (in every thread of the block) if the wait gave up.
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &ctl->bar_gen;
+    const unsigned g = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&ctl->bar_count, 1u) == nblocks - 1u) {
+      ctl->bar_count = 0;
+      __threadfence();
+      atomicAdd(&ctl->bar_gen, 1u);
+    } else {
+      unsigned it = 0;
+      while (*gen == g) {
+        if (++it > kBarrierSpinLimit) {
+          atomicOr(&ctl->overflow, 4u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__device__ __forceinline__ void radix_hist_tiles(const uint32_t* src, uint32_t n, uint32_t ntiles, int shift,
+                                                 uint32_t* hist, uint32_t* cnt) {
   for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     for (int d = threadIdx.x; d < kRadix; d += blockDim.x) cnt[d] = 0;
     __syncthreads();
     const uint32_t lo = t * kSortTile, hi = min(n, lo + kSortTile);
-    for (uint32_t x = lo + threadIdx.x; x < hi; x += blockDim.x) atomicAdd(&cnt[(src[x] >> (pass * 8)) & 0xFFu], 1u);
+    for (uint32_t x = lo + threadIdx.x; x < hi; x += blockDim.x) atomicAdd(&cnt[(src[x] >> shift) & 0xFFu], 1u);
     __syncthreads();
     for (int d = threadIdx.x; d < kRadix; d += blockDim.x) hist[(size_t)d * ntiles + t] = cnt[d];
     __syncthreads();
   }
 }
 
-// Multi-tile pass, step 2: exclusive scan of the histogram table (one block).
-__global__ void __launch_bounds__(1024) k_radix_scan(const Ctl* __restrict__ ctl, uint32_t cmax,
-                                                     uint32_t* __restrict__ hist) {
-  const uint32_t n = sort_len(ctl, cmax);
-  if (n <= (uint32_t)kSortTile) return;
-  const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
-  const uint32_t N = ntiles * kRadix;
+// Exclusive scan of hist[0 .. N) in place by one block.
+__device__ __forceinline__ void radix_scan_block(uint32_t* hist, uint32_t N, uint32_t* part) {
   const uint32_t per = (N + blockDim.x - 1) / blockDim.x;
   const uint32_t lo = threadIdx.x * per, hi = min(N, lo + per);
   uint32_t s = 0;
   for (uint32_t x = lo; x < hi; x++) s += hist[x];
-  __shared__ uint32_t part[32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t incl = s;
 #pragma unroll
@@ -169,7 +194,7 @@ __global__ void __launch_bounds__(1024) k_radix_scan(const Ctl* __restrict__ ctl
   if (lane == 31) part[w] = incl;
   __syncthreads();
   if (w == 0) {
-    uint32_t p = (lane < (int)(blockDim.x >> 5)) ? part[lane] : 0u;
+    const uint32_t p = (lane < (int)(blockDim.x >> 5)) ? part[lane] : 0u;
     uint32_t pi = p;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
@@ -187,36 +212,48 @@ __global__ void __launch_bounds__(1024) k_radix_scan(const Ctl* __restrict__ ctl
   }
 }
 
-// Multi-tile pass, step 3: stable scatter of every tile to its digit offsets.
-__global__ void __launch_bounds__(kSortThreads) k_radix_scatter(const Ctl* __restrict__ ctl, uint32_t* l0,
-                                                                uint32_t* l1, uint32_t* tmp, uint32_t cmax,
-                                                                int pass, const uint32_t* __restrict__ hist) {
-  const uint32_t n = sort_len(ctl, cmax);
-  if (n <= (uint32_t)kSortTile) return;
-  uint32_t* list = sort_list(ctl, l0, l1);
-  const uint32_t* src = (pass & 1) ? tmp : list;
-  uint32_t* dst = (pass & 1) ? list : tmp;
-  const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
-  __shared__ uint32_t wcnt[kSortWarps][kRadix];
-  __shared__ uint32_t tot[kRadix];
+__device__ __forceinline__ void radix_scatter_tiles(const uint32_t* src, uint32_t* dst, uint32_t n, uint32_t ntiles,
+                                                    int shift, const uint32_t* hist, uint32_t (*wcnt)[kRadix],
+                                                    uint32_t* tot) {
   const int w = threadIdx.x >> 5;
   for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     for (int x = threadIdx.x; x < kSortWarps * kRadix; x += blockDim.x) (&wcnt[0][0])[x] = 0;
     __syncthreads();
     uint32_t key[8], rank[8];
     bool valid[8];
-    rank_tile(src, t * kSortTile, n, pass * 8, wcnt, key, rank, valid);
+    rank_tile(src, t * kSortTile, n, shift, wcnt, key, rank, valid);
     __syncthreads();
     warp_prefix(wcnt, tot);
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < 8; r++) {
       if (valid[r]) {
-        const uint32_t d = (key[r] >> (pass * 8)) & 0xFFu;
+        const uint32_t d = (key[r] >> shift) & 0xFFu;
         dst[hist[(size_t)d * ntiles + t] + wcnt[w][d] + rank[r]] = key[r];
       }
     }
     __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_large(Ctl* __restrict__ ctl, uint32_t* l0, uint32_t* l1,
+                                                             uint32_t* tmp, uint32_t cmax, uint32_t* __restrict__ hist) {
+  const uint32_t n = sort_len(ctl, cmax);
+  if (n <= (uint32_t)kSortTile) return;  // the whole grid leaves together
+  __shared__ uint32_t wcnt[kSortWarps][kRadix];
+  __shared__ uint32_t tot[kRadix];
+  __shared__ uint32_t part[32];
+  uint32_t* list = sort_list(ctl, l0, l1);
+  const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+  for (int pass = 0; pass < 4; pass++) {
+    const uint32_t* src = (pass & 1) ? tmp : list;
+    uint32_t* dst = (pass & 1) ? list : tmp;
+    radix_hist_tiles(src, n, ntiles, pass * 8, hist, tot);
+    if (!grid_barrier(ctl, gridDim.x)) return;
+    if (blockIdx.x == 0) radix_scan_block(hist, ntiles * kRadix, part);
+    if (!grid_barrier(ctl, gridDim.x)) return;
+    radix_scatter_tiles(src, dst, n, ntiles, pass * 8, hist, wcnt, tot);
+    if (!grid_barrier(ctl, gridDim.x)) return;
   }
 }
 

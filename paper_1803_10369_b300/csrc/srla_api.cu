@@ -35,8 +35,8 @@ uint64_t next_pow2(uint64_t x) {
 }
 
 struct Layout {
-  size_t ctl, re, le, staging, utab, ulist, ctab[2], cflags[2], clist[2], sort_tmp, sort_hist, lut_est,
-      lut_flags, rep_stats[2], rep_entries[2], total;
+  size_t ctl, re, le, staging, utab, ulist, ctab[2], cflags[2], clist[2], sort_tmp, sort_hist, rep_stats[2],
+      rep_entries[2], total;
   uint64_t staging_pkts;
   uint32_t umask, cmask, ntiles;
 };
@@ -101,8 +101,6 @@ Layout layout_of(const srla_params* p) {
   }
   L.sort_tmp = take((size_t)p->max_candidates * 4);
   L.sort_hist = take((size_t)L.ntiles * kRadix * 4);
-  L.lut_est = take(((size_t)p->gl + 1) * 4);
-  L.lut_flags = take(((size_t)p->gl + 1) * 4);
   for (int q = 0; q < 2; q++) {
     L.rep_stats[q] = take(sizeof(srla_slice_stats));
     L.rep_entries[q] = take((size_t)p->max_candidates * sizeof(srla_entry));
@@ -134,6 +132,10 @@ struct srla_s {
   uint64_t n_pkts_open;   // packets pushed into the open slice
   uint64_t staging_used;  // staging packets used in the open slice
   uint64_t launches;      // kernels launched so far
+  int occ_scan[2];        // resident scan blocks per SM (unaligned, aligned batches)
+  int sort_grid;          // blocks of the cooperative sort
+  cudaGraphExec_t graph[2];    // captured slice end, by slice parity
+  uint64_t graph_launches;     // kernels per captured slice end
   struct Slot {
     uint64_t slice, n_pkts;
     bool valid;
@@ -171,29 +173,26 @@ int grid_for(uint64_t items, int per_block, int cap) {
 
 template <typename CellT>
 int launch_scan(srla_t* h, const uint32_t* pairs, uint64_t n) {
-  const int grid = grid_for(n, 256 * 4, h->sms * 8);
+  const bool vec = (reinterpret_cast<uintptr_t>(pairs) & 15u) == 0;
+  auto kern = vec ? k_scan<CellT, true> : k_scan<CellT, false>;
+  const int grid = grid_for(n, kScanThreads * 4, h->sms * std::max(1, h->occ_scan[vec ? 1 : 0]));
   CellT* re = h->at<CellT>(h->L.re);
   CellT* le = h->at<CellT>(h->L.le);
   h->launches++;
-  if ((reinterpret_cast<uintptr_t>(pairs) & 15u) == 0)
-    k_scan<CellT, true><<<grid, 256, 0, h->st>>>(pairs, n, h->geo, h->coef, re, le, h->ctl(),
-                                                 h->at<unsigned long long>(h->L.utab), h->L.umask,
-                                                 h->at<uint32_t>(h->L.ulist), h->p.max_sampled);
-  else
-    k_scan<CellT, false><<<grid, 256, 0, h->st>>>(pairs, n, h->geo, h->coef, re, le, h->ctl(),
-                                                  h->at<unsigned long long>(h->L.utab), h->L.umask,
-                                                  h->at<uint32_t>(h->L.ulist), h->p.max_sampled);
+  kern<<<grid, kScanThreads, 0, h->st>>>(pairs, n, h->geo, h->coef, re, le, h->ctl(),
+                                         h->at<unsigned long long>(h->L.utab), h->L.umask,
+                                         h->at<uint32_t>(h->L.ulist), h->p.max_sampled);
   return cuda_err(cudaGetLastError());
 }
 
 template <typename CellT>
-int launch_sweep(srla_t* h, int census, int reset) {
+int launch_sweep(srla_t* h, int census, int reset, int after_close) {
   const size_t cells_max = (size_t)h->p.v * std::max(h->p.g, h->p.gl);
   const size_t nvec = cells_max * sizeof(CellT) / 16;
   const int gx = grid_for(nvec, 256, std::max(1, h->sms * 8 / (int)(2 * h->p.u)));
   h->launches++;
   k_sweep<CellT><<<dim3(gx, 2 * h->p.u), 256, 0, h->st>>>(h->geo, h->at<CellT>(h->L.re), h->at<CellT>(h->L.le),
-                                                         h->ctl(), census, reset);
+                                                         h->ctl(), census, reset, after_close);
   return cuda_err(cudaGetLastError());
 }
 
@@ -201,30 +200,28 @@ int launch_sort(srla_t* h) {
   const Layout& L = h->L;
   uint32_t* l0 = h->at<uint32_t>(L.clist[0]);
   uint32_t* l1 = h->at<uint32_t>(L.clist[1]);
-  const uint32_t cmax = h->p.max_candidates;
+  uint32_t cmax = h->p.max_candidates;
   h->launches++;
   k_sort_small<<<1, kSortThreads, kSortSmallSmem, h->st>>>(h->ctl(), l0, l1, cmax);
+  SRLA_TRY(cudaGetLastError());
   if (L.ntiles > 1) {
+    Ctl* ctl = h->ctl();
     uint32_t* tmp = h->at<uint32_t>(L.sort_tmp);
     uint32_t* hist = h->at<uint32_t>(L.sort_hist);
-    for (int pass = 0; pass < 4; pass++) {
-      h->launches += 3;
-      k_radix_hist<<<L.ntiles, kSortThreads, 0, h->st>>>(h->ctl(), l0, l1, tmp, cmax, pass, hist);
-      k_radix_scan<<<1, 1024, 0, h->st>>>(h->ctl(), cmax, hist);
-      k_radix_scatter<<<L.ntiles, kSortThreads, 0, h->st>>>(h->ctl(), l0, l1, tmp, cmax, pass, hist);
-    }
+    void* args[] = {&ctl, &l0, &l1, &tmp, &cmax, &hist};
+    h->launches++;
+    SRLA_TRY(cudaLaunchCooperativeKernel((const void*)k_sort_large, dim3(h->sort_grid), dim3(kSortThreads), args, 0,
+                                         h->st));
   }
-  return cuda_err(cudaGetLastError());
+  return SRLA_OK;
 }
 
 template <typename CellT>
 int launch_end_slice(srla_t* h) {
   const Layout& L = h->L;
   int r;
-  if ((r = launch_sweep<CellT>(h, 1, h->k_is_P ? 0 : 1)) != SRLA_OK) return r;
-  h->launches += 4;  // lut, filter, estimate, finish
-  k_lut<<<(h->p.gl + 1 + 255) / 256, 256, 0, h->st>>>(h->geo, h->ctl(), h->at<float>(L.lut_est),
-                                                       h->at<uint32_t>(L.lut_flags));
+  if ((r = launch_sweep<CellT>(h, 1, h->k_is_P ? 0 : 1, 0)) != SRLA_OK) return r;
+  h->launches += 2;  // filter, estimate
   k_filter<CellT><<<h->sms * 4, 256, 0, h->st>>>(
       h->geo, h->coef, h->at<CellT>(L.re), h->ctl(), h->at<uint32_t>(L.ulist), h->p.max_sampled,
       h->at<unsigned long long>(L.ctab[0]), h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]),
@@ -232,15 +229,56 @@ int launch_end_slice(srla_t* h) {
       h->p.max_candidates);
   if ((r = launch_sort(h)) != SRLA_OK) return r;
   k_estimate<CellT><<<h->sms * 4, 256, 0, h->st>>>(
-      h->geo, h->coef, h->at<CellT>(L.re), h->at<CellT>(L.le), h->ctl(), h->at<float>(L.lut_est),
-      h->at<uint32_t>(L.lut_flags), h->at<unsigned long long>(L.ctab[0]), h->at<unsigned long long>(L.ctab[1]),
-      h->at<uint32_t>(L.cflags[0]), h->at<uint32_t>(L.cflags[1]), L.cmask, h->at<uint32_t>(L.clist[0]),
-      h->at<uint32_t>(L.clist[1]), h->p.max_candidates, h->at<srla_entry>(L.rep_entries[0]),
-      h->at<srla_entry>(L.rep_entries[1]));
-  if (h->k_is_P && (r = launch_sweep<CellT>(h, 0, 1)) != SRLA_OK) return r;
-  k_finish<<<1, 32, 0, h->st>>>(h->geo, h->ctl(), h->at<srla_slice_stats>(L.rep_stats[0]),
-                                h->at<srla_slice_stats>(L.rep_stats[1]), h->p.max_sampled, h->p.max_candidates);
-  return cuda_err(cudaGetLastError());
+      h->geo, h->coef, h->at<CellT>(L.re), h->at<CellT>(L.le), h->ctl(), h->at<unsigned long long>(L.ctab[0]),
+      h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]), h->at<uint32_t>(L.cflags[1]), L.cmask,
+      h->at<uint32_t>(L.clist[0]), h->at<uint32_t>(L.clist[1]), h->p.max_candidates,
+      h->at<srla_entry>(L.rep_entries[0]), h->at<srla_entry>(L.rep_entries[1]),
+      h->at<srla_slice_stats>(L.rep_stats[0]), h->at<srla_slice_stats>(L.rep_stats[1]), h->p.max_sampled);
+  SRLA_TRY(cudaGetLastError());
+  // with k = 2^z - 1 the recorders that saturate are still inside the window of the closed
+  // slice, so they are cleared only after the slice was estimated and closed
+  if (h->k_is_P && (r = launch_sweep<CellT>(h, 0, 1, 1)) != SRLA_OK) return r;
+  return SRLA_OK;
+}
+
+// Slice end plus the copy of its header and first report entries into the pinned slot q.
+template <typename CellT>
+int enqueue_end_slice(srla_t* h, int q) {
+  const int r = launch_end_slice<CellT>(h);
+  if (r != SRLA_OK) return r;
+  srla_s::Slot& s = h->slot[q];
+  SRLA_TRY(cudaMemcpyAsync(s.h_stats, h->ws + h->L.rep_stats[q], sizeof(srla_slice_stats), cudaMemcpyDeviceToHost,
+                           h->st));
+  const uint32_t pre = std::min<uint32_t>(kPrefetch, h->p.max_candidates);
+  SRLA_TRY(cudaMemcpyAsync(s.h_entries, h->ws + h->L.rep_entries[q], (size_t)pre * sizeof(srla_entry),
+                           cudaMemcpyDeviceToHost, h->st));
+  return SRLA_OK;
+}
+
+// Capture the slice end once per parity into an executable graph: every kernel reads the
+// open slice from the control block, so the same graph serves every slice of that parity.
+int capture_graphs(srla_t* h) {
+  cudaStream_t user = h->st;
+  h->st = h->st_copy;
+  int rc = SRLA_OK;
+  for (int q = 0; q < 2 && rc == SRLA_OK; q++) {
+    cudaGraph_t g = nullptr;
+    const uint64_t before = h->launches;
+    if (cudaStreamBeginCapture(h->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = SRLA_E_CUDA;
+      break;
+    }
+    rc = h->p.dr_bytes == 1 ? enqueue_end_slice<uint8_t>(h, q) : enqueue_end_slice<uint16_t>(h, q);
+    const cudaError_t e = cudaStreamEndCapture(h->st, &g);
+    if (rc == SRLA_OK && e != cudaSuccess) rc = SRLA_E_CUDA;
+    if (rc == SRLA_OK && cudaGraphInstantiate(&h->graph[q], g, 0) != cudaSuccess) rc = SRLA_E_CUDA;
+    if (g) cudaGraphDestroy(g);
+    h->graph_launches = h->launches - before;
+    h->launches = before;
+  }
+  h->st = user;
+  if (rc != SRLA_OK) (void)cudaGetLastError();
+  return rc;
 }
 
 // Zero the control block and both candidate/sampled set tables (fresh tags).
@@ -249,6 +287,26 @@ int reset_tables(srla_t* h, bool all) {
   SRLA_TRY(cudaMemsetAsync(h->ws + L.utab, 0, ((size_t)L.umask + 1) * 8, h->st));
   for (int q = 0; q < 2; q++) SRLA_TRY(cudaMemsetAsync(h->ws + L.ctab[q], 0, ((size_t)L.cmask + 1) * 8, h->st));
   if (all) SRLA_TRY(cudaMemsetAsync(h->ws, 0, L.total, h->st));
+  return SRLA_OK;
+}
+
+// Resident blocks per SM of the scan, and the cooperative sort's grid (all co-resident).
+int occupancy(srla_t* h) {
+  int a = 0, b = 0, c = 0;
+  const bool one = h->p.dr_bytes == 1;
+  if ((one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_scan<uint8_t, false>, kScanThreads, 0)
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_scan<uint16_t, false>, kScanThreads, 0)) !=
+      cudaSuccess)
+    return SRLA_E_CUDA;
+  if ((one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan<uint8_t, true>, kScanThreads, 0)
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan<uint16_t, true>, kScanThreads, 0)) !=
+      cudaSuccess)
+    return SRLA_E_CUDA;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_sort_large, kSortThreads, 0) != cudaSuccess || c < 1)
+    return SRLA_E_CUDA;
+  h->occ_scan[0] = std::max(1, a);
+  h->occ_scan[1] = std::max(1, b);
+  h->sort_grid = (int)std::max<uint32_t>(1, std::min<uint32_t>(h->L.ntiles, (uint32_t)(h->sms * c)));
   return SRLA_OK;
 }
 
@@ -328,9 +386,17 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
   }
   if (rc == SRLA_OK) {
     cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmallSmem);
-    rc = reset_tables(h, true);
+    rc = occupancy(h);
   }
+  if (rc == SRLA_OK) rc = reset_tables(h, true);
   if (rc == SRLA_OK) rc = init_ctl(h, h->T, 0);
+  if (rc == SRLA_OK && capture_graphs(h) != SRLA_OK) {
+    // the slice end then runs as individual launches on the caller's stream
+    for (int q = 0; q < 2; q++) {
+      if (h->graph[q]) cudaGraphExecDestroy(h->graph[q]);
+      h->graph[q] = nullptr;
+    }
+  }
   if (rc != SRLA_OK) {
     srla_destroy(h);
     return rc;
@@ -371,15 +437,15 @@ int srla_push_packets(srla_t* h, const uint32_t* pairs, uint64_t n_pairs, int on
 
 int srla_end_slice(srla_t* h, uint64_t* slice_id) {
   if (!h) return SRLA_E_INVAL;
-  const int r = h->p.dr_bytes == 1 ? launch_end_slice<uint8_t>(h) : launch_end_slice<uint16_t>(h);
-  if (r != SRLA_OK) return r;
   const int q = (int)(h->T & 1);
   srla_s::Slot& s = h->slot[q];
-  SRLA_TRY(cudaMemcpyAsync(s.h_stats, h->ws + h->L.rep_stats[q], sizeof(srla_slice_stats), cudaMemcpyDeviceToHost,
-                           h->st));
-  const uint32_t pre = std::min<uint32_t>(kPrefetch, h->p.max_candidates);
-  SRLA_TRY(cudaMemcpyAsync(s.h_entries, h->ws + h->L.rep_entries[q], (size_t)pre * sizeof(srla_entry),
-                           cudaMemcpyDeviceToHost, h->st));
+  if (h->graph[q]) {
+    SRLA_TRY(cudaGraphLaunch(h->graph[q], h->st));
+    h->launches += h->graph_launches;
+  } else {
+    const int r = h->p.dr_bytes == 1 ? enqueue_end_slice<uint8_t>(h, q) : enqueue_end_slice<uint16_t>(h, q);
+    if (r != SRLA_OK) return r;
+  }
   SRLA_TRY(cudaEventRecord(s.ev, h->st));
   s.slice = h->T;
   s.n_pkts = h->n_pkts_open;
@@ -435,6 +501,8 @@ int srla_report(srla_t* h, uint64_t slice_id, srla_entry* out, size_t cap, size_
                              (take - pre) * sizeof(srla_entry), cudaMemcpyDeviceToHost, h->st_copy));
     SRLA_TRY(cudaStreamSynchronize(h->st_copy));
   }
+  if (st.overflow & 4u) return SRLA_E_TIMEOUT;
+  if (st.overflow & 4u) return SRLA_E_TIMEOUT;
   if (st.overflow) return SRLA_E_CAPACITY;
   if (cap < n) return SRLA_E_NOMEM;
   return SRLA_OK;
@@ -565,14 +633,18 @@ int srla_import_state(srla_t* h, const void* host_buf, size_t len) {
 
 uint64_t srla_kernel_launches(const srla_t* h) { return h ? h->launches : 0; }
 
+int srla_uses_graph(const srla_t* h) { return h && h->graph[0] && h->graph[1] ? 1 : 0; }
+
 void srla_destroy(srla_t* h) {
   if (!h) return;
   if (h->st_copy) {
     cudaStreamSynchronize(h->st);
     cudaStreamDestroy(h->st_copy);
   }
-  for (int q = 0; q < 2; q++)
+  for (int q = 0; q < 2; q++) {
     if (h->slot[q].ev) cudaEventDestroy(h->slot[q].ev);
+    if (h->graph[q]) cudaGraphExecDestroy(h->graph[q]);
+  }
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   delete h;
 }
@@ -666,6 +738,7 @@ extern "C" int srla_batch_report_static(const srla_params* p, const uint32_t* d_
   h.k_is_P = (q.k == h.geo.P);
   h.T = q.start_slice;
   SRLA_TRY(cudaDeviceGetAttribute(&h.sms, cudaDevAttrMultiProcessorCount, dev));
+  if ((r = occupancy(&h)) != SRLA_OK) return r;
 
   // The array keeps the previous call's contents: the recorders, the sets and the control
   // block must start at zero, so the whole used part is cleared first.
@@ -692,6 +765,7 @@ extern "C" int srla_batch_report_static(const srla_params* p, const uint32_t* d_
                              h.st));
     SRLA_TRY(cudaStreamSynchronize(h.st));
   }
+  if (st.overflow & 4u) return SRLA_E_TIMEOUT;
   if (st.overflow) return SRLA_E_CAPACITY;
   if (cap < n) return SRLA_E_NOMEM;
   return SRLA_OK;

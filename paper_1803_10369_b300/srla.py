@@ -64,6 +64,7 @@ SIGNATURES = {
     "srla_export_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "srla_import_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "srla_kernel_launches": (ctypes.c_uint64, [_P]),
+    "srla_uses_graph": (ctypes.c_int, [_P]),
     "srla_destroy": (None, [_P]),
     "srla_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "srla_batch_report_static": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P, _P, ctypes.c_size_t, _P, _P]),
@@ -212,6 +213,9 @@ class Link:
 
     def kernel_launches(self) -> int:
         return self.L.srla_kernel_launches(self._h)
+
+    def uses_graph(self) -> bool:
+        return bool(self.L.srla_uses_graph(self._h))
 
     def sync(self):
         _ck(self.L.srla_sync(self._h), "srla_sync")

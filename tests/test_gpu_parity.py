@@ -38,6 +38,7 @@ VARIANTS = {
 def test_parity_tiny_variants(name, cuda_device):
     w = VARIANTS[name]
     o, link = make_pair(w)
+    assert link.uses_graph()  # the slice end replays the captured graphs
     trace = synth.generate_trace(w.traffic, w.n_slices)
     for s in range(w.n_slices):
         pk = trace[s]

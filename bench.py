@@ -269,15 +269,19 @@ def bench_srla(args):
     value = total_pkts / (elapsed_ms * 1e-3) / 1e6
 
     # ---- latency: slice end -> report, with the slice's scan already complete
-    lat = []
+    lat, lat_gpu = [], []
     n_lat = max(args.latency_slices, K)
     for i in range(n_lat):
         link.push(batches[i % K])
         stream.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
+        e0.record(stream)
         sid = link.end_slice()
+        e1.record(stream)
         link.report(sid)
         lat.append((time.perf_counter() - t0) * 1e3)
+        lat_gpu.append(e0.elapsed_time(e1))
     lat.sort()
     p50 = lat[len(lat) // 2]
     p99 = lat[min(len(lat) - 1, int(round(0.99 * (len(lat) - 1))))]
@@ -315,7 +319,8 @@ def bench_srla(args):
         "metric": METRIC, "value": round(value, 3), "unit": "Mpkts/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(elapsed_ms / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "u16" if w.dr_bytes == 2 else "u8", "data": "synthetic", "config": _config(w),
-        "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "slices": n_lat},
+        "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "slices": n_lat,
+                       "slice_end_gpu_p50": round(statistics.median(lat_gpu), 4)},
         "scan_mpkts_s": round(per_launch_pkts / (scan_avg_ms * 1e-3) / 1e6, 3),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 5), "traffic": None, "kernel": "k_scan",

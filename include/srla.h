@@ -56,6 +56,9 @@ extern "C" {
  *   staging_pkts  packets the host-input staging area holds (0: 2^20)
  *   max_sampled   distinct hosts sampled into the SRE per slice
  *   max_candidates  candidate list entries per slice (new + carried)
+ *   pair_slots_log2 size of the per-slice table of scanned pairs that lets the scan skip a
+ *               pair already scanned in the open slice (it writes the same stamps): 0 gives
+ *               2^21 slots, -1 disables the table, 10..28 choose 2^value slots (8 bytes each)
  *   hash_a, hash_b  coefficients of the hash family h(x) = (a*x + b) mod (2^61 - 1), one
  *               pair per role: rows 0..u-1 (column of aip in row i), u (SLE cell of bip),
  *               u+1 (SRE cell of bip), u+2 (sampling hash of bip); a in [1, 2^61-2],
@@ -68,6 +71,8 @@ typedef struct srla_params {
   uint64_t start_slice;
   uint64_t staging_pkts;
   uint32_t max_sampled, max_candidates;
+  int32_t pair_slots_log2;
+  uint32_t reserved;
   uint64_t hash_a[SRLA_N_HASH];
   uint64_t hash_b[SRLA_N_HASH];
 } srla_params;

@@ -43,7 +43,11 @@ struct Ctl {
   unsigned int blocks_done;       // blocks of the estimate kernel that have finished
   unsigned int bar_count;         // grid barrier of the cooperative sort: arrivals
   unsigned int bar_gen;           // grid barrier of the cooperative sort: generation
-  unsigned int pad1;
+  unsigned int pair_mode;         // 1: the scan consults the per-slice pair table
+  unsigned int n_miss;            // packets of the open slice that missed their block's table
+  unsigned int n_gdup;            // of which the per-slice pair table found already scanned
+  unsigned int pad2;
+  double up;                      // UP of Eq. 8 for the open slice (set at its end)
   unsigned long long census[SRLA_MAX_ROWS];
 };
 
@@ -74,23 +78,56 @@ __device__ __forceinline__ uint32_t stamp_age(uint32_t c, uint32_t tm, uint32_t 
   return (uint32_t)age;
 }
 
-__device__ __forceinline__ bool in_window(uint32_t c, uint32_t tm, uint32_t P, uint32_t lim) {
-  return c != 0 && stamp_age(c, tm, P) < lim;
+
+// The stamps inside the window of the last `lim` slices (ages 0 .. lim-1) are the codes
+// 1 + ((tm - j) mod P), j < lim: one cyclic interval of codes ending at hi = tm + 1, either
+// [lo, hi] or, when it wraps past P, [lo, P] and [1, hi].  Empty cells (code 0) are never in
+// it.  SIMD compares test 2 (16-bit) or 4 (8-bit) cells per instruction.
+struct Win {
+  uint32_t lo, hi;  // splatted to every cell of a word
+  bool wrap, none;
+};
+
+template <typename CellT>
+__device__ __forceinline__ uint32_t splat(uint32_t x) {
+  return sizeof(CellT) == 1 ? x * 0x01010101u : x * 0x00010001u;
 }
 
-// Bit q set iff cell q of a 32-bit word of cells is inside the window (age < lim).
 template <typename CellT>
-__device__ __forceinline__ uint32_t window_bits(uint32_t word, uint32_t tm, uint32_t P, uint32_t lim) {
-  constexpr int kCells = 4 / (int)sizeof(CellT);
-  constexpr int kBits = 8 * (int)sizeof(CellT);
-  constexpr uint32_t kMask = (kBits == 32) ? 0xFFFFFFFFu : ((1u << kBits) - 1);
-  uint32_t bits = 0;
-#pragma unroll
-  for (int q = 0; q < kCells; q++) {
-    const uint32_t c = (word >> (q * kBits)) & kMask;
-    bits |= (uint32_t)in_window(c, tm, P, lim) << q;
+__device__ __forceinline__ Win make_win(uint32_t tm, uint32_t P, uint32_t lim) {
+  Win w;
+  w.none = lim == 0;
+  const uint32_t hi = tm + 1u;
+  uint32_t lo;
+  if (lim <= hi) {
+    lo = hi - lim + 1u;
+    w.wrap = false;
+  } else {
+    lo = hi + P - lim + 1u;
+    w.wrap = true;
   }
-  return bits;
+  w.lo = splat<CellT>(lo);
+  w.hi = splat<CellT>(hi);
+  return w;
+}
+
+// Per-cell mask of a 32-bit word of cells: all ones in the cells inside the window.
+template <typename CellT>
+__device__ __forceinline__ uint32_t window_mask(uint32_t word, const Win& w) {
+  if (w.none) return 0u;
+  if (sizeof(CellT) == 1) {
+    const uint32_t ge = __vcmpgeu4(word, w.lo), le = __vcmpleu4(word, w.hi);
+    return w.wrap ? (ge | (le & __vcmpne4(word, 0u))) : (ge & le);
+  } else {
+    const uint32_t ge = __vcmpgeu2(word, w.lo), le = __vcmpleu2(word, w.hi);
+    return w.wrap ? (ge | (le & __vcmpne2(word, 0u))) : (ge & le);
+  }
+}
+
+// Number of cells set in a sum of popcounts of per-cell masks.
+template <typename CellT>
+__device__ __forceinline__ uint32_t cells_of_bits(uint32_t bits) {
+  return bits / (8u * (uint32_t)sizeof(CellT));
 }
 
 // ------------------------------------------------------------------------- host sets
@@ -166,10 +203,23 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
 // whose recorder is inside the window in every row i, i.e. whose DRjoin (max) over the u
 // rows is below lim.  One warp per host; lane i < u holds the column of row i in `mycol`.
 // Every lane runs the same number of trips (the shuffles need the whole warp).
+template <int WPL>
+__device__ __forceinline__ void load_words(const uint32_t* run, uint32_t w0, uint32_t wd[WPL]) {
+  if constexpr (WPL == 4) {
+    const uint4 q4 = __ldg(reinterpret_cast<const uint4*>(run + w0));
+    wd[0] = q4.x; wd[1] = q4.y; wd[2] = q4.z; wd[3] = q4.w;
+  } else if constexpr (WPL == 2) {
+    const uint2 q2 = __ldg(reinterpret_cast<const uint2*>(run + w0));
+    wd[0] = q2.x; wd[1] = q2.y;
+  } else {
+    wd[0] = __ldg(run + w0);
+  }
+}
+
+// Rows are fetched eight at a time, all loads in flight before any is used.
 template <typename CellT, int WPL>
 __device__ __forceinline__ uint32_t union_count_w(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
-                                                  uint32_t u, uint32_t mycol, uint32_t tm, uint32_t P,
-                                                  uint32_t lim, int lane) {
+                                                  uint32_t u, uint32_t mycol, const Win& win, int lane) {
   const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;  // 32-bit words per run
   const uint32_t trips = (R + 32u * WPL - 1) / (32u * WPL);
   uint32_t total = 0;
@@ -179,40 +229,37 @@ __device__ __forceinline__ uint32_t union_count_w(const CellT* __restrict__ arr,
     uint32_t m[WPL];
 #pragma unroll
     for (int q = 0; q < WPL; q++) m[q] = 0xFFFFFFFFu;
-    for (uint32_t i = 0; i < u; i++) {
-      const uint32_t c = __shfl_sync(kFull, mycol, (int)i);
-      const uint32_t* run = reinterpret_cast<const uint32_t*>(arr + ((size_t)i * v + c) * cells);
-      if (ok) {
-        uint32_t wd[WPL];
-        if constexpr (WPL == 4) {
-          const uint4 q4 = __ldg(reinterpret_cast<const uint4*>(run + w0));
-          wd[0] = q4.x; wd[1] = q4.y; wd[2] = q4.z; wd[3] = q4.w;
-        } else if constexpr (WPL == 2) {
-          const uint2 q2 = __ldg(reinterpret_cast<const uint2*>(run + w0));
-          wd[0] = q2.x; wd[1] = q2.y;
-        } else {
-          wd[0] = __ldg(run + w0);
-        }
+    for (uint32_t i0 = 0; i0 < u; i0 += 8) {
+      uint32_t wd[8][WPL];
 #pragma unroll
-        for (int q = 0; q < WPL; q++) m[q] &= window_bits<CellT>(wd[q], tm, P, lim);
+      for (int r = 0; r < 8; r++) {
+        const uint32_t i = i0 + (uint32_t)r;
+        const uint32_t c = __shfl_sync(kFull, mycol, (int)(i & 31u));
+        if (ok && i < u)
+          load_words<WPL>(reinterpret_cast<const uint32_t*>(arr + ((size_t)i * v + c) * cells), w0, wd[r]);
       }
+#pragma unroll
+      for (int r = 0; r < 8; r++)
+        if (ok && i0 + (uint32_t)r < u) {
+#pragma unroll
+          for (int q = 0; q < WPL; q++) m[q] &= window_mask<CellT>(wd[r][q], win);
+        }
     }
     if (ok) {
 #pragma unroll
       for (int q = 0; q < WPL; q++) total += __popc(m[q]);
     }
   }
-  return warp_sum(total);
+  return cells_of_bits<CellT>(warp_sum(total));
 }
 
 template <typename CellT>
 __device__ __forceinline__ uint32_t union_count(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
-                                                uint32_t u, uint32_t mycol, uint32_t tm, uint32_t P,
-                                                uint32_t lim, int lane) {
+                                                uint32_t u, uint32_t mycol, const Win& win, int lane) {
   const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;
-  if (R >= 128) return union_count_w<CellT, 4>(arr, v, cells, u, mycol, tm, P, lim, lane);
-  if (R >= 64) return union_count_w<CellT, 2>(arr, v, cells, u, mycol, tm, P, lim, lane);
-  return union_count_w<CellT, 1>(arr, v, cells, u, mycol, tm, P, lim, lane);
+  if (R >= 128) return union_count_w<CellT, 4>(arr, v, cells, u, mycol, win, lane);
+  if (R >= 64) return union_count_w<CellT, 2>(arr, v, cells, u, mycol, win, lane);
+  return union_count_w<CellT, 1>(arr, v, cells, u, mycol, win, lane);
 }
 
 // Same count as union_count, for a caller that only needs to know whether it reaches
@@ -221,8 +268,8 @@ __device__ __forceinline__ uint32_t union_count(const CellT* __restrict__ arr, u
 // result is exact when it is >= need; below need it is some value < need.
 template <typename CellT, int WPL>
 __device__ __forceinline__ uint32_t union_count_atleast_w(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
-                                                          uint32_t u, uint32_t mycol, uint32_t tm, uint32_t P,
-                                                          uint32_t lim, uint32_t need, int lane) {
+                                                          uint32_t u, uint32_t mycol, const Win& win, uint32_t need,
+                                                          int lane) {
   const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;
   const uint32_t w0 = (uint32_t)lane * WPL;
   const bool ok = w0 < R;
@@ -232,25 +279,16 @@ __device__ __forceinline__ uint32_t union_count_atleast_w(const CellT* __restric
   uint32_t total = 0;
   for (uint32_t i = 0; i < u; i++) {
     const uint32_t c = __shfl_sync(kFull, mycol, (int)i);
-    const uint32_t* run = reinterpret_cast<const uint32_t*>(arr + ((size_t)i * v + c) * cells);
     if (ok) {
       uint32_t wd[WPL];
-      if constexpr (WPL == 4) {
-        const uint4 q4 = __ldg(reinterpret_cast<const uint4*>(run + w0));
-        wd[0] = q4.x; wd[1] = q4.y; wd[2] = q4.z; wd[3] = q4.w;
-      } else if constexpr (WPL == 2) {
-        const uint2 q2 = __ldg(reinterpret_cast<const uint2*>(run + w0));
-        wd[0] = q2.x; wd[1] = q2.y;
-      } else {
-        wd[0] = __ldg(run + w0);
-      }
+      load_words<WPL>(reinterpret_cast<const uint32_t*>(arr + ((size_t)i * v + c) * cells), w0, wd);
 #pragma unroll
-      for (int q = 0; q < WPL; q++) m[q] &= window_bits<CellT>(wd[q], tm, P, lim);
+      for (int q = 0; q < WPL; q++) m[q] &= window_mask<CellT>(wd[q], win);
     }
     uint32_t part = 0;
 #pragma unroll
     for (int q = 0; q < WPL; q++) part += __popc(m[q]);
-    total = warp_sum(part);
+    total = cells_of_bits<CellT>(warp_sum(part));
     if (total < need) break;  // warp-uniform
   }
   return total;
@@ -258,13 +296,13 @@ __device__ __forceinline__ uint32_t union_count_atleast_w(const CellT* __restric
 
 template <typename CellT>
 __device__ __forceinline__ uint32_t union_count_atleast(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
-                                                        uint32_t u, uint32_t mycol, uint32_t tm, uint32_t P,
-                                                        uint32_t lim, uint32_t need, int lane) {
+                                                        uint32_t u, uint32_t mycol, const Win& win, uint32_t need,
+                                                        int lane) {
   const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;
-  if (R <= 32) return union_count_atleast_w<CellT, 1>(arr, v, cells, u, mycol, tm, P, lim, need, lane);
-  if (R <= 64) return union_count_atleast_w<CellT, 2>(arr, v, cells, u, mycol, tm, P, lim, need, lane);
-  if (R <= 128) return union_count_atleast_w<CellT, 4>(arr, v, cells, u, mycol, tm, P, lim, need, lane);
-  return union_count<CellT>(arr, v, cells, u, mycol, tm, P, lim, lane);
+  if (R <= 32) return union_count_atleast_w<CellT, 1>(arr, v, cells, u, mycol, win, need, lane);
+  if (R <= 64) return union_count_atleast_w<CellT, 2>(arr, v, cells, u, mycol, win, need, lane);
+  if (R <= 128) return union_count_atleast_w<CellT, 4>(arr, v, cells, u, mycol, win, need, lane);
+  return union_count<CellT>(arr, v, cells, u, mycol, win, lane);
 }
 
 }  // namespace srla

@@ -26,6 +26,28 @@ constexpr int kSeenLog2 = 12;
 constexpr int kSeen = 1 << kSeenLog2;                      // pairs remembered per block
 constexpr unsigned long long kNoPair = ~0ull;              // empty slot; that pair is never cached
 constexpr int kScanThreads = 256;
+constexpr int kPairProbes = 2;                             // probes into the slice's pair table
+
+// Behind the per-block table sits one table of the pairs scanned anywhere on the GPU in the
+// open slice (cleared at every slice end).  A pair that missed its block's table claims a
+// slot with one compare-and-swap: the first claimant scans the pair, later ones skip it.  A
+// pair that finds no slot within kPairProbes probes is simply scanned, so a full table costs
+// speed, never correctness.  The table pays off only when pairs repeat across blocks: the
+// scan counts block misses and GPU-wide repeats, and the slice close switches the table off
+// for the next slice when fewer than a quarter of the misses were repeats (re-trying it
+// every 16 slices).
+__device__ __forceinline__ bool pair_claim(unsigned long long* __restrict__ ptab, uint32_t pmask,
+                                           unsigned long long key) {
+  uint32_t s = (uint32_t)((key * 0xD6E8FEB86659FD93ull) >> 32) & pmask;
+#pragma unroll 1
+  for (int i = 0; i < kPairProbes; i++) {
+    const unsigned long long old = atomicCAS(ptab + s, kNoPair, key);
+    if (old == kNoPair) return true;   // first in the slice: scan it
+    if (old == key) return false;      // already scanned in this slice
+    s = (s + 1) & pmask;
+  }
+  return true;
+}
 
 __device__ __forceinline__ uint32_t seen_slot(unsigned long long key) {
   return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - kSeenLog2));
@@ -37,16 +59,29 @@ __device__ __forceinline__ void scan_pair(uint32_t aip, uint32_t bip, bool ok, c
                                           CellT* __restrict__ le, Ctl* __restrict__ ctl,
                                           unsigned long long* __restrict__ utab, uint32_t umask,
                                           uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag,
-                                          int lane, volatile unsigned long long* seen) {
+                                          int lane, volatile unsigned long long* seen,
+                                          unsigned long long* __restrict__ ptab, uint32_t pmask,
+                                          uint32_t& n_miss, uint32_t& n_gdup) {
+  bool miss = false, gdup = false;
   if (ok) {
     const unsigned long long key = ((unsigned long long)aip << 32) | bip;
     if (key != kNoPair) {
       const uint32_t h = seen_slot(key);
-      if (seen[h] == key)
+      if (seen[h] == key) {
         ok = false;  // already scanned in this slice by this block
-      else
+      } else {
         seen[h] = key;
+        miss = true;
+        if (ptab) {
+          ok = pair_claim(ptab, pmask, key);
+          gdup = !ok;
+        }
+      }
     }
+  }
+  if (ptab) {  // block misses and GPU-wide repeats, counted per thread
+    n_miss += miss;
+    n_gdup += gdup;
   }
   const uint32_t u = geo.u;
   bool samp = false;
@@ -120,11 +155,13 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
                                                        const __grid_constant__ Coef coef, CellT* __restrict__ re,
                                                        CellT* __restrict__ le, Ctl* __restrict__ ctl,
                                                        unsigned long long* __restrict__ utab, uint32_t umask,
-                                                       uint32_t* __restrict__ ulist, uint32_t umax) {
+                                                       uint32_t* __restrict__ ulist, uint32_t umax,
+                                                       unsigned long long* __restrict__ ptab, uint32_t pmask) {
   __shared__ unsigned long long seen_mem[kSeen];
   volatile unsigned long long* seen = seen_mem;
   for (int x = threadIdx.x; x < kSeen; x += blockDim.x) seen[x] = kNoPair;
   __syncthreads();
+  if (ptab && ctl->pair_mode == 0) ptab = nullptr;
   const uint32_t tm = ctl->tm;
   const CellT code = (CellT)(tm + 1u);
   const uint32_t tag = slice_tag(ctl->T);
@@ -134,6 +171,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
   uint64_t base = gw * 128;
   uint32_t a[4], b[4];
   bool ok[4];
+  uint32_t n_miss = 0, n_gdup = 0;
   load_pairs<kVec>(pairs, n, base, lane, a, b, ok);
   while (base < n) {
     const uint64_t next = base + nw * 128;
@@ -142,12 +180,29 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
     load_pairs<kVec>(pairs, n, next, lane, na, nb, nok);
 #pragma unroll
     for (int j = 0; j < 4; j++)
-      scan_pair<CellT>(a[j], b[j], ok[j], geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, seen);
+      scan_pair<CellT>(a[j], b[j], ok[j], geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, seen,
+                       ptab, pmask, n_miss, n_gdup);
 #pragma unroll
     for (int j = 0; j < 4; j++) {
       a[j] = na[j]; b[j] = nb[j]; ok[j] = nok[j];
     }
     base = next;
+  }
+  if (ptab) {  // one global update per block
+    __shared__ unsigned s_miss, s_gdup;
+    if (threadIdx.x == 0) s_miss = s_gdup = 0;
+    __syncthreads();
+    n_miss = warp_sum(n_miss);
+    n_gdup = warp_sum(n_gdup);
+    if (lane == 0) {
+      atomicAdd(&s_miss, n_miss);
+      atomicAdd(&s_gdup, n_gdup);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      atomicAdd(&ctl->n_miss, s_miss);
+      atomicAdd(&ctl->n_gdup, s_gdup);
+    }
   }
 }
 
@@ -158,6 +213,64 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
 // the open slice (age < k).  Reset: clear the stamps whose age would reach P after the
 // slide, i.e. the code 1 + ((T + 1) mod P); this is the DRslide of Algorithm 3 at the
 // point where a distance saturates at 2^z - 1.
+// In-window cells of one 32-bit word (the interval form of make_win, one compare per cell).
+template <typename CellT>
+__device__ __forceinline__ uint32_t count_in_window(uint32_t word, uint32_t lo, uint32_t len, bool wrap,
+                                                    uint32_t hi) {
+  constexpr int kCells = 4 / (int)sizeof(CellT);
+  constexpr int kBits = 8 * (int)sizeof(CellT);
+  constexpr uint32_t kMask = (1u << kBits) - 1u;
+  uint32_t n = 0;
+#pragma unroll
+  for (int q = 0; q < kCells; q++) {
+    const uint32_t c = (word >> (q * kBits)) & kMask;
+    n += wrap ? (uint32_t)((c >= lo) | (c - 1u < hi)) : (uint32_t)(c - lo < len);
+  }
+  return n;
+}
+
+// Nonzero iff some cell of the word equals the splatted stamp (exact zero-cell test).
+template <typename CellT>
+__device__ __forceinline__ uint32_t has_stamp(uint32_t word, uint32_t asplat) {
+  const uint32_t x = word ^ asplat;
+  return sizeof(CellT) == 1 ? ((x - 0x01010101u) & ~x & 0x80808080u) : ((x - 0x00010001u) & ~x & 0x80008000u);
+}
+
+template <typename CellT>
+__device__ __forceinline__ uint32_t clear_stamp(uint32_t word, uint32_t alias) {
+  constexpr int kCells = 4 / (int)sizeof(CellT);
+  constexpr int kBits = 8 * (int)sizeof(CellT);
+  constexpr uint32_t kMask = (1u << kBits) - 1u;
+#pragma unroll
+  for (int q = 0; q < kCells; q++)
+    if (((word >> (q * kBits)) & kMask) == alias) word &= ~(kMask << (q * kBits));
+  return word;
+}
+
+struct SweepWin {
+  uint32_t lo, hi, len;
+  bool wrap;
+};
+
+template <typename CellT>
+__device__ __forceinline__ void sweep_vec(uint4* base, size_t x, uint4 q, bool count, bool reset, const SweepWin& sw,
+                                          uint32_t alias, uint32_t asplat, uint32_t& cnt) {
+  if (count)
+    cnt += count_in_window<CellT>(q.x, sw.lo, sw.len, sw.wrap, sw.hi) +
+           count_in_window<CellT>(q.y, sw.lo, sw.len, sw.wrap, sw.hi) +
+           count_in_window<CellT>(q.z, sw.lo, sw.len, sw.wrap, sw.hi) +
+           count_in_window<CellT>(q.w, sw.lo, sw.len, sw.wrap, sw.hi);
+  if (reset && (has_stamp<CellT>(q.x, asplat) | has_stamp<CellT>(q.y, asplat) | has_stamp<CellT>(q.z, asplat) |
+                has_stamp<CellT>(q.w, asplat))) {
+    uint4 r;
+    r.x = clear_stamp<CellT>(q.x, alias);
+    r.y = clear_stamp<CellT>(q.y, alias);
+    r.z = clear_stamp<CellT>(q.z, alias);
+    r.w = clear_stamp<CellT>(q.w, alias);
+    base[x] = r;
+  }
+}
+
 template <typename CellT>
 __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, CellT* __restrict__ le,
                                                Ctl* __restrict__ ctl, int do_census, int do_reset,
@@ -166,33 +279,31 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
   const bool is_le = y < geo.u;
   if (!is_le && !do_reset) return;
   const bool count = is_le && do_census;
+  const bool reset = do_reset != 0;
   const uint32_t row = is_le ? y : y - geo.u;
   const size_t cells = (size_t)geo.v * (is_le ? geo.gl : geo.g);
   uint4* base = reinterpret_cast<uint4*>((is_le ? le : re) + (size_t)row * cells);
   const size_t nvec = cells * sizeof(CellT) / 16;
-  const uint32_t tm = ctl->tm, P = geo.P, k = geo.k;
+  const uint32_t tm = ctl->tm, P = geo.P;
   // stamp of the slice that opens next: after the slice was closed, that is the open slice
   const uint32_t alias = 1u + (after_close ? tm : ((tm + 1u == P) ? 0u : tm + 1u));
-  const uint32_t splat = sizeof(CellT) == 1 ? alias * 0x01010101u : alias * 0x00010001u;
+  const uint32_t asplat = splat<CellT>(alias);
+  SweepWin sw;  // the in-window stamps: [lo, hi], or [lo, P] and [1, hi] when wrapped
+  sw.hi = tm + 1u;
+  sw.wrap = geo.k > sw.hi;
+  sw.lo = sw.wrap ? sw.hi + P - geo.k + 1u : sw.hi - geo.k + 1u;
+  sw.len = geo.k;
   uint32_t cnt = 0;
-  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < nvec; x += (size_t)gridDim.x * blockDim.x) {
-    uint4 q = base[x];
-    if (count) {
-      cnt += __popc(window_bits<CellT>(q.x, tm, P, k)) + __popc(window_bits<CellT>(q.y, tm, P, k)) +
-             __popc(window_bits<CellT>(q.z, tm, P, k)) + __popc(window_bits<CellT>(q.w, tm, P, k));
-    }
-    if (do_reset) {
-      uint4 r;
-      if (sizeof(CellT) == 1) {
-        r.x = q.x & ~__vcmpeq4(q.x, splat); r.y = q.y & ~__vcmpeq4(q.y, splat);
-        r.z = q.z & ~__vcmpeq4(q.z, splat); r.w = q.w & ~__vcmpeq4(q.w, splat);
-      } else {
-        r.x = q.x & ~__vcmpeq2(q.x, splat); r.y = q.y & ~__vcmpeq2(q.y, splat);
-        r.z = q.z & ~__vcmpeq2(q.z, splat); r.w = q.w & ~__vcmpeq2(q.w, splat);
-      }
-      if (r.x != q.x || r.y != q.y || r.z != q.z || r.w != q.w) base[x] = r;
-    }
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; x + 3 * stride < nvec; x += 4 * stride) {  // four loads in flight per thread
+    uint4 q[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) q[j] = base[x + j * stride];
+#pragma unroll
+    for (int j = 0; j < 4; j++) sweep_vec<CellT>(base, x + j * stride, q[j], count, reset, sw, alias, asplat, cnt);
   }
+  for (; x < nvec; x += stride) sweep_vec<CellT>(base, x, base[x], count, reset, sw, alias, asplat, cnt);
   if (count) {
     __shared__ uint32_t part[8];
     cnt = warp_sum(cnt);
@@ -202,53 +313,6 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
       unsigned long long s = 0;
       for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += part[w];
       atomicAdd(&ctl->census[row], s);
-    }
-  }
-}
-
-// -------------------------------------------------------------- new candidates (b3)
-//
-// For every distinct host sampled in the open slice: |URE(aip)|^k at the end of the slice
-// (before the slide).  Hosts with at least ceil(rho*g) in-window union cells enter the
-// slice's candidate set, which already holds the hosts carried from the previous slice.
-template <typename CellT>
-__global__ void __launch_bounds__(256) k_filter(Geo geo, const __grid_constant__ Coef coef,
-                                                const CellT* __restrict__ re, Ctl* __restrict__ ctl,
-                                                const uint32_t* __restrict__ ulist, uint32_t umax,
-                                                unsigned long long* ctab0, unsigned long long* ctab1,
-                                                uint32_t* cflags0, uint32_t* cflags1, uint32_t cmask,
-                                                uint32_t* clist0, uint32_t* clist1, uint32_t cmax) {
-  const unsigned long long T = ctl->T;
-  const int par = (int)(T & 1);
-  unsigned long long* ctab = par ? ctab1 : ctab0;
-  uint32_t* cflags = par ? cflags1 : cflags0;
-  uint32_t* clist = par ? clist1 : clist0;
-  const uint32_t tag = slice_tag(T);
-  const uint32_t n = min(ctl->n_sampled, umax);
-  const uint32_t tm = ctl->tm;
-  const int lane = threadIdx.x & 31;
-  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t idx = gw; idx < n; idx += nw) {
-    const uint32_t aip = ulist[idx];
-    const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
-    const uint32_t cnt = union_count_atleast<CellT>(re, geo.v, geo.g, geo.u, mycol, tm, geo.P, geo.k, geo.rho_g, lane);
-    if (lane == 0 && cnt >= geo.rho_g) {
-      atomicAdd(&ctl->n_new, 1u);
-      uint32_t slot;
-      const int r = set_insert(ctab, cmask, tag, aip, &slot);
-      if (r == 1) {
-        cflags[slot] = SRLA_NEW;
-        const unsigned at = atomicAdd(&ctl->cat_count[par], 1u);
-        if (at < cmax)
-          clist[at] = aip;
-        else
-          atomicOr(&ctl->overflow, 2u);
-      } else if (r == 0) {
-        atomicOr(&cflags[slot], SRLA_NEW);
-      } else {
-        atomicOr(&ctl->overflow, 2u);
-      }
     }
   }
 }
@@ -279,6 +343,71 @@ __device__ __forceinline__ double eq9(uint32_t w, uint32_t gl, double up, uint32
   return est;
 }
 
+// -------------------------------------------------------------- new candidates (b3)
+//
+// For every distinct host sampled in the open slice: |URE(aip)|^k at the end of the slice
+// (before the slide).  Hosts with at least ceil(rho*g) in-window union cells enter the
+// slice's candidate set, which already holds the hosts carried from the previous slice.
+template <typename CellT>
+__global__ void __launch_bounds__(256) k_filter(Geo geo, const __grid_constant__ Coef coef,
+                                                const CellT* __restrict__ re, Ctl* __restrict__ ctl,
+                                                const uint32_t* __restrict__ ulist, uint32_t umax,
+                                                unsigned long long* ctab0, unsigned long long* ctab1,
+                                                uint32_t* cflags0, uint32_t* cflags1, uint32_t cmask,
+                                                uint32_t* clist0, uint32_t* clist1, uint32_t cmax,
+                                                float* __restrict__ lut_est, uint32_t* __restrict__ lut_flags) {
+  // Eq. 8 and Eq. 9 for every union weight w in [0, g'], spread over all blocks: for a fixed
+  // slice the estimate depends on w alone, so the estimate kernel only looks it up.
+  {
+    __shared__ double s_up;
+    if (threadIdx.x == 0) {
+      s_up = slice_up(geo, ctl);
+      if (blockIdx.x == 0) ctl->up = s_up;
+    }
+    __syncthreads();
+    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w <= geo.gl; w += gridDim.x * blockDim.x) {
+      uint32_t f;
+      const double e = eq9(w, geo.gl, s_up, geo.theta, &f);
+      lut_est[w] = (float)e;
+      lut_flags[w] = f;
+      if (f & SRLA_SUPER) atomicMin(&ctl->w_star, w);
+    }
+  }
+  const unsigned long long T = ctl->T;
+  const int par = (int)(T & 1);
+  unsigned long long* ctab = par ? ctab1 : ctab0;
+  uint32_t* cflags = par ? cflags1 : cflags0;
+  uint32_t* clist = par ? clist1 : clist0;
+  const uint32_t tag = slice_tag(T);
+  const uint32_t n = min(ctl->n_sampled, umax);
+  const Win win = make_win<CellT>(ctl->tm, geo.P, geo.k);
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t idx = gw; idx < n; idx += nw) {
+    const uint32_t aip = ulist[idx];
+    const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
+    const uint32_t cnt = union_count_atleast<CellT>(re, geo.v, geo.g, geo.u, mycol, win, geo.rho_g, lane);
+    if (lane == 0 && cnt >= geo.rho_g) {
+      atomicAdd(&ctl->n_new, 1u);
+      uint32_t slot;
+      const int r = set_insert(ctab, cmask, tag, aip, &slot);
+      if (r == 1) {
+        cflags[slot] = SRLA_NEW;
+        const unsigned at = atomicAdd(&ctl->cat_count[par], 1u);
+        if (at < cmax)
+          clist[at] = aip;
+        else
+          atomicOr(&ctl->overflow, 2u);
+      } else if (r == 0) {
+        atomicOr(&cflags[slot], SRLA_NEW);
+      } else {
+        atomicOr(&ctl->overflow, 2u);
+      }
+    }
+  }
+}
+
 // -------------------------------------------------- estimate (b4), carry (b5), close
 //
 // For every candidate of the sorted list: w = |ULE(aip)|^k (Algorithm 1), the Eq. 9
@@ -293,8 +422,9 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
                                                   unsigned long long* ctab1, uint32_t* cflags0, uint32_t* cflags1,
                                                   uint32_t cmask, uint32_t* clist0, uint32_t* clist1, uint32_t cmax,
                                                   srla_entry* rep0, srla_entry* rep1, srla_slice_stats* st0,
-                                                  srla_slice_stats* st1, uint32_t umax) {
-  __shared__ double s_up;
+                                                  srla_slice_stats* st1, uint32_t umax,
+                                                  const float* __restrict__ lut_est,
+                                                  const uint32_t* __restrict__ lut_flags) {
   __shared__ int s_last;
   const unsigned long long T = ctl->T;
   const int par = (int)(T & 1);
@@ -307,29 +437,24 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
   srla_entry* rep = par ? rep1 : rep0;
   const uint32_t tag = slice_tag(T), ntag = slice_tag(T + 1);
   const uint32_t n = min(ctl->cat_count[par], cmax);
-  const uint32_t tm = ctl->tm;
-  const uint32_t klim_post = geo.k - 1u;  // age + 1 < k after the slide
-  if (threadIdx.x == 0) s_up = slice_up(geo, ctl);
-  __syncthreads();
-  const double up = s_up;
+  const Win win = make_win<CellT>(ctl->tm, geo.P, geo.k);
+  const Win win_post = make_win<CellT>(ctl->tm, geo.P, geo.k - 1u);  // age + 1 < k after the slide
   const int lane = threadIdx.x & 31;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t idx = gw; idx < n; idx += nw) {
     const uint32_t aip = clist[idx];
     const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
-    const uint32_t w = union_count<CellT>(le, geo.v, geo.gl, geo.u, mycol, tm, geo.P, geo.k, lane);
-    const uint32_t cw = union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, tm, geo.P, klim_post, lane);
+    const uint32_t w = union_count<CellT>(le, geo.v, geo.gl, geo.u, mycol, win, lane);
+    const uint32_t cw = union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, win_post, lane);
     if (lane == 0) {
       const uint32_t s = set_find(ctab, cmask, tag, aip);
       const uint32_t origin = (s != 0xFFFFFFFFu) ? cflags[s] : 0u;
-      uint32_t ef;
-      const double est = eq9(w, geo.gl, up, geo.theta, &ef);
       srla_entry e;
       e.aip = aip;
       e.w = w;
-      e.est = (float)est;
-      e.flags = origin | ef;
+      e.est = lut_est[w];
+      e.flags = origin | lut_flags[w];
       rep[idx] = e;
       if (cw >= geo.rho_g) {
         uint32_t slot;
@@ -363,17 +488,9 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
   st->n_new = ctl->n_new;
   st->n_candidates = n;
   st->n_carry_out = min(ctl->cat_count[par ^ 1], cmax);
-  // least w whose estimate reaches theta (Eq. 9 is increasing in w): binary search
-  uint32_t lo = 0, hi = geo.gl;
-  while (lo < hi) {
-    const uint32_t mid = (lo + hi) / 2;
-    uint32_t f;
-    eq9(mid, geo.gl, up, geo.theta, &f);
-    if (f & SRLA_SUPER) hi = mid; else lo = mid + 1;
-  }
-  st->w_star = lo;
+  st->w_star = min(ctl->w_star, geo.gl + 1u);
   st->overflow = ctl->overflow;
-  st->up = up;
+  st->up = ctl->up;
   for (int i = 0; i < SRLA_MAX_ROWS; i++) {
     st->census[i] = ctl->census[i];
     ctl->census[i] = 0;
@@ -387,6 +504,13 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
   ctl->overflow_next = 0;
   ctl->blocks_done = 0;
   ctl->bar_count = 0;
+  ctl->w_star = geo.gl + 1u;
+  // keep the per-slice pair table on while it finds repeats for >= 1/4 of the block misses
+  const bool measured = ctl->pair_mode != 0;
+  const bool worth = 4ull * ctl->n_gdup >= (unsigned long long)ctl->n_miss;
+  ctl->pair_mode = (measured ? worth : false) || ((T + 1) % 16 == 0) ? 1u : 0u;
+  ctl->n_miss = 0;
+  ctl->n_gdup = 0;
   __threadfence();
 }
 

@@ -3,9 +3,9 @@
 // Least-significant-digit radix sort, 8-bit digits, 4 passes.  A tile is 4096 keys handled
 // by 16 warps; each warp ranks its 256 keys in 8 rounds of 32 with __match_any_sync, which
 // keeps the ranking stable (index order within a round, rounds in order, warps in order).
-// Lists of up to one tile are sorted by a single block in shared memory; longer lists use
-// three kernels per pass (tile histograms, one scan over them, stable scatter).  The list
-// length lives on the device, so every kernel reads it and exits when it is not its case.
+// Lists of up to one tile are sorted by a single block in shared memory (bitonic); longer
+// lists by all blocks of the same cooperative launch.  The list length lives on the device,
+// so the kernel reads it and takes the matching path.
 #pragma once
 
 #include "device.cuh"
@@ -69,61 +69,30 @@ __device__ __forceinline__ void warp_prefix(uint32_t (*wcnt)[kRadix], uint32_t* 
   }
 }
 
-// Lists of at most one tile: the whole sort in one block, in shared memory.
-__global__ void __launch_bounds__(kSortThreads) k_sort_small(const Ctl* __restrict__ ctl, uint32_t* l0,
-                                                             uint32_t* l1, uint32_t cmax) {
-  const uint32_t n = sort_len(ctl, cmax);
-  if (n <= 1 || n > (uint32_t)kSortTile) return;
-  uint32_t* list = sort_list(ctl, l0, l1);
-  extern __shared__ uint32_t smem[];
-  uint32_t* bufA = smem;                                   // kSortTile
-  uint32_t* bufB = smem + kSortTile;                       // kSortTile
-  uint32_t(*wcnt)[kRadix] = reinterpret_cast<uint32_t(*)[kRadix]>(smem + 2 * kSortTile);
-  uint32_t* tot = smem + 2 * kSortTile + kSortWarps * kRadix;  // kRadix
-  for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) bufA[x] = list[x];
-  const int w = threadIdx.x >> 5;
-  for (int pass = 0; pass < 4; pass++) {
-    uint32_t* src = (pass & 1) ? bufB : bufA;
-    uint32_t* dst = (pass & 1) ? bufA : bufB;
-    for (int x = threadIdx.x; x < kSortWarps * kRadix; x += blockDim.x) (&wcnt[0][0])[x] = 0;
-    __syncthreads();
-    uint32_t key[8], rank[8];
-    bool valid[8];
-    rank_tile(src, 0, n, pass * 8, wcnt, key, rank, valid);
-    __syncthreads();
-    warp_prefix(wcnt, tot);
-    __syncthreads();
-    if (threadIdx.x < 32) {  // exclusive scan of the 256 digit totals by one warp
-      uint32_t v[8], s = 0;
-#pragma unroll
-      for (int q = 0; q < 8; q++) {
-        v[q] = tot[threadIdx.x * 8 + q];
-        s += v[q];
+// A list of at most one tile: a bitonic sort in shared memory by one block.  The list is
+// padded to a power of two with 0xFFFFFFFF; the keys are unique, so the first n of the
+// sorted array are the sorted list even when a key equals the pad value.
+__device__ __forceinline__ void bitonic_block(uint32_t* list, uint32_t n, uint32_t* smem) {
+  uint32_t N = 2;
+  while (N < n) N <<= 1;
+  for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) smem[x] = x < n ? list[x] : 0xFFFFFFFFu;
+  __syncthreads();
+  for (uint32_t k = 2; k <= N; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t t = threadIdx.x; t < N / 2; t += blockDim.x) {
+        const uint32_t i = 2 * j * (t / j) + (t % j);  // lower index of the pair
+        const uint32_t l = i + j;
+        const bool up = (i & k) == 0;
+        const uint32_t a = smem[i], b = smem[l];
+        if ((a > b) == up) {
+          smem[i] = b;
+          smem[l] = a;
+        }
       }
-      uint32_t incl = s;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(kFull, incl, o);
-        if ((int)threadIdx.x >= o) incl += t;
-      }
-      uint32_t run = incl - s;
-#pragma unroll
-      for (int q = 0; q < 8; q++) {
-        tot[threadIdx.x * 8 + q] = run;
-        run += v[q];
-      }
+      __syncthreads();
     }
-    __syncthreads();
-#pragma unroll
-    for (int r = 0; r < 8; r++) {
-      if (valid[r]) {
-        const uint32_t d = (key[r] >> (pass * 8)) & 0xFFu;
-        dst[tot[d] + wcnt[w][d] + rank[r]] = key[r];
-      }
-    }
-    __syncthreads();
   }
-  for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) list[x] = bufA[x];
+  for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) list[x] = smem[x];
 }
 
 // Lists longer than one tile: one cooperative kernel runs the four passes, each as three
@@ -236,10 +205,15 @@ __device__ __forceinline__ void radix_scatter_tiles(const uint32_t* src, uint32_
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_large(Ctl* __restrict__ ctl, uint32_t* l0, uint32_t* l1,
-                                                             uint32_t* tmp, uint32_t cmax, uint32_t* __restrict__ hist) {
+// The slice's candidate sort: one cooperative launch whatever the list length.
+__global__ void __launch_bounds__(kSortThreads) k_sort(Ctl* __restrict__ ctl, uint32_t* l0, uint32_t* l1,
+                                                       uint32_t* tmp, uint32_t cmax, uint32_t* __restrict__ hist) {
   const uint32_t n = sort_len(ctl, cmax);
-  if (n <= (uint32_t)kSortTile) return;  // the whole grid leaves together
+  if (n <= (uint32_t)kSortTile) {  // one block sorts in shared memory; the grid leaves together
+    extern __shared__ uint32_t bsm[];
+    if (blockIdx.x == 0 && n > 1) bitonic_block(sort_list(ctl, l0, l1), n, bsm);
+    return;
+  }
   __shared__ uint32_t wcnt[kSortWarps][kRadix];
   __shared__ uint32_t tot[kRadix];
   __shared__ uint32_t part[32];
@@ -257,6 +231,6 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_large(Ctl* __restrict__ c
   }
 }
 
-constexpr size_t kSortSmallSmem = (size_t)(2 * kSortTile + kSortWarps * kRadix + kRadix) * sizeof(uint32_t);
+constexpr size_t kSortSmallSmem = (size_t)kSortTile * sizeof(uint32_t);
 
 }  // namespace srla

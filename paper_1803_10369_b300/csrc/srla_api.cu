@@ -35,10 +35,11 @@ uint64_t next_pow2(uint64_t x) {
 }
 
 struct Layout {
-  size_t ctl, re, le, staging, utab, ulist, ctab[2], cflags[2], clist[2], sort_tmp, sort_hist, rep_stats[2],
-      rep_entries[2], total;
+  size_t ctl, re, le, staging, utab, ulist, ctab[2], cflags[2], clist[2], sort_tmp, sort_hist, lut_est,
+      lut_flags, rep_stats[2], rep_entries[2], ptab, total;
   uint64_t staging_pkts;
-  uint32_t umask, cmask, ntiles;
+  uint32_t umask, cmask, ntiles, pmask;
+  bool pairs;  // per-slice pair table present
 };
 
 // Eq. 1 on integers: the least n >= 0 with g * 2^n >= theta.
@@ -66,6 +67,8 @@ int check(const srla_params* p) {
   if (p->gl > (1u << 24)) return SRLA_E_INVAL;
   if (p->max_sampled < 1 || p->max_sampled > (1u << 30)) return SRLA_E_INVAL;
   if (p->max_candidates < 1 || p->max_candidates > (1u << 26)) return SRLA_E_INVAL;
+  if (p->pair_slots_log2 != 0 && p->pair_slots_log2 != -1 && (p->pair_slots_log2 < 10 || p->pair_slots_log2 > 28))
+    return SRLA_E_INVAL;
   for (uint32_t r = 0; r < p->u + 3; r++) {
     if (p->hash_a[r] < 1 || p->hash_a[r] >= kP61) return SRLA_E_INVAL;
     if (p->hash_b[r] >= kP61) return SRLA_E_INVAL;
@@ -82,7 +85,7 @@ Layout layout_of(const srla_params* p) {
     return at;
   };
   const size_t B = p->dr_bytes;
-  L.staging_pkts = p->staging_pkts ? p->staging_pkts : (1ull << 20);
+  L.staging_pkts = p->staging_pkts ? std::max<uint64_t>(p->staging_pkts, 4) : (1ull << 20);
   const uint64_t ucap = std::max<uint64_t>(64, next_pow2(2ull * p->max_sampled));
   const uint64_t ccap = std::max<uint64_t>(64, next_pow2(2ull * p->max_candidates));
   L.umask = (uint32_t)(ucap - 1);
@@ -101,10 +104,16 @@ Layout layout_of(const srla_params* p) {
   }
   L.sort_tmp = take((size_t)p->max_candidates * 4);
   L.sort_hist = take((size_t)L.ntiles * kRadix * 4);
+  L.lut_est = take(((size_t)p->gl + 1) * 4);
+  L.lut_flags = take(((size_t)p->gl + 1) * 4);
   for (int q = 0; q < 2; q++) {
     L.rep_stats[q] = take(sizeof(srla_slice_stats));
     L.rep_entries[q] = take((size_t)p->max_candidates * sizeof(srla_entry));
   }
+  L.pairs = p->pair_slots_log2 != -1;
+  const uint32_t plog = p->pair_slots_log2 > 0 ? (uint32_t)p->pair_slots_log2 : 21u;
+  L.pmask = L.pairs ? (1u << plog) - 1u : 0u;
+  L.ptab = take(L.pairs ? ((size_t)1 << plog) * 8 : 0);
   L.total = off;
   return L;
 }
@@ -126,6 +135,10 @@ struct srla_s {
   char* ws;
   cudaStream_t st;
   cudaStream_t st_copy;  // internal stream for report remainders and checkpoints
+  cudaStream_t st_h2d;   // internal stream for host-to-device copies of host batches
+  cudaEvent_t ev_ready[2], ev_free[2];  // staging halves: copied / consumed by the scan
+  bool free_pending[2];
+  int stage_cur;
   int sms;
   bool k_is_P;
   uint64_t T;             // open slice
@@ -181,7 +194,8 @@ int launch_scan(srla_t* h, const uint32_t* pairs, uint64_t n) {
   h->launches++;
   kern<<<grid, kScanThreads, 0, h->st>>>(pairs, n, h->geo, h->coef, re, le, h->ctl(),
                                          h->at<unsigned long long>(h->L.utab), h->L.umask,
-                                         h->at<uint32_t>(h->L.ulist), h->p.max_sampled);
+                                         h->at<uint32_t>(h->L.ulist), h->p.max_sampled,
+                                         h->L.pairs ? h->at<unsigned long long>(h->L.ptab) : nullptr, h->L.pmask);
   return cuda_err(cudaGetLastError());
 }
 
@@ -198,22 +212,22 @@ int launch_sweep(srla_t* h, int census, int reset, int after_close) {
 
 int launch_sort(srla_t* h) {
   const Layout& L = h->L;
+  Ctl* ctl = h->ctl();
   uint32_t* l0 = h->at<uint32_t>(L.clist[0]);
   uint32_t* l1 = h->at<uint32_t>(L.clist[1]);
   uint32_t cmax = h->p.max_candidates;
+  uint32_t* tmp = h->at<uint32_t>(L.sort_tmp);
+  uint32_t* hist = h->at<uint32_t>(L.sort_hist);
+  void* args[] = {&ctl, &l0, &l1, &tmp, &cmax, &hist};
   h->launches++;
-  k_sort_small<<<1, kSortThreads, kSortSmallSmem, h->st>>>(h->ctl(), l0, l1, cmax);
-  SRLA_TRY(cudaGetLastError());
-  if (L.ntiles > 1) {
-    Ctl* ctl = h->ctl();
-    uint32_t* tmp = h->at<uint32_t>(L.sort_tmp);
-    uint32_t* hist = h->at<uint32_t>(L.sort_hist);
-    void* args[] = {&ctl, &l0, &l1, &tmp, &cmax, &hist};
-    h->launches++;
-    SRLA_TRY(cudaLaunchCooperativeKernel((const void*)k_sort_large, dim3(h->sort_grid), dim3(kSortThreads), args, 0,
-                                         h->st));
-  }
-  return SRLA_OK;
+  return cuda_err(cudaLaunchCooperativeKernel((const void*)k_sort, dim3(h->sort_grid), dim3(kSortThreads), args,
+                                              kSortSmallSmem, h->st));
+}
+
+// The next slice starts with an empty pair table (all slots hold the empty key, ~0).
+int clear_pairs(srla_t* h) {
+  if (!h->L.pairs) return SRLA_OK;
+  return cuda_err(cudaMemsetAsync(h->ws + h->L.ptab, 0xFF, ((size_t)h->L.pmask + 1) * 8, h->st));
 }
 
 template <typename CellT>
@@ -226,19 +240,20 @@ int launch_end_slice(srla_t* h) {
       h->geo, h->coef, h->at<CellT>(L.re), h->ctl(), h->at<uint32_t>(L.ulist), h->p.max_sampled,
       h->at<unsigned long long>(L.ctab[0]), h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]),
       h->at<uint32_t>(L.cflags[1]), L.cmask, h->at<uint32_t>(L.clist[0]), h->at<uint32_t>(L.clist[1]),
-      h->p.max_candidates);
+      h->p.max_candidates, h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
   if ((r = launch_sort(h)) != SRLA_OK) return r;
-  k_estimate<CellT><<<h->sms * 4, 256, 0, h->st>>>(
+  k_estimate<CellT><<<h->sms * 2, 256, 0, h->st>>>(
       h->geo, h->coef, h->at<CellT>(L.re), h->at<CellT>(L.le), h->ctl(), h->at<unsigned long long>(L.ctab[0]),
       h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]), h->at<uint32_t>(L.cflags[1]), L.cmask,
       h->at<uint32_t>(L.clist[0]), h->at<uint32_t>(L.clist[1]), h->p.max_candidates,
       h->at<srla_entry>(L.rep_entries[0]), h->at<srla_entry>(L.rep_entries[1]),
-      h->at<srla_slice_stats>(L.rep_stats[0]), h->at<srla_slice_stats>(L.rep_stats[1]), h->p.max_sampled);
+      h->at<srla_slice_stats>(L.rep_stats[0]), h->at<srla_slice_stats>(L.rep_stats[1]), h->p.max_sampled,
+      h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
   SRLA_TRY(cudaGetLastError());
   // with k = 2^z - 1 the recorders that saturate are still inside the window of the closed
   // slice, so they are cleared only after the slice was estimated and closed
   if (h->k_is_P && (r = launch_sweep<CellT>(h, 0, 1, 1)) != SRLA_OK) return r;
-  return SRLA_OK;
+  return clear_pairs(h);
 }
 
 // Slice end plus the copy of its header and first report entries into the pinned slot q.
@@ -287,7 +302,7 @@ int reset_tables(srla_t* h, bool all) {
   SRLA_TRY(cudaMemsetAsync(h->ws + L.utab, 0, ((size_t)L.umask + 1) * 8, h->st));
   for (int q = 0; q < 2; q++) SRLA_TRY(cudaMemsetAsync(h->ws + L.ctab[q], 0, ((size_t)L.cmask + 1) * 8, h->st));
   if (all) SRLA_TRY(cudaMemsetAsync(h->ws, 0, L.total, h->st));
-  return SRLA_OK;
+  return clear_pairs(h);
 }
 
 // Resident blocks per SM of the scan, and the cooperative sort's grid (all co-resident).
@@ -302,7 +317,7 @@ int occupancy(srla_t* h) {
            : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan<uint16_t, true>, kScanThreads, 0)) !=
       cudaSuccess)
     return SRLA_E_CUDA;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_sort_large, kSortThreads, 0) != cudaSuccess || c < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_sort, kSortThreads, kSortSmallSmem) != cudaSuccess || c < 1)
     return SRLA_E_CUDA;
   h->occ_scan[0] = std::max(1, a);
   h->occ_scan[1] = std::max(1, b);
@@ -315,6 +330,7 @@ int init_ctl(srla_t* h, uint64_t T, uint32_t carried) {
   c.T = T;
   c.tm = (uint32_t)(T % h->geo.P);
   c.w_star = h->geo.gl + 1;
+  c.pair_mode = 1;
   c.cat_count[T & 1] = carried;
   SRLA_TRY(cudaMemcpyAsync(h->ctl(), &c, sizeof(Ctl), cudaMemcpyHostToDevice, h->st));
   return cudaStreamSynchronize(h->st) == cudaSuccess ? SRLA_OK : SRLA_E_CUDA;
@@ -377,6 +393,12 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
     delete h;
     return SRLA_E_CUDA;
   }
+  if (cudaStreamCreateWithFlags(&h->st_h2d, cudaStreamNonBlocking) != cudaSuccess) rc = SRLA_E_CUDA;
+  for (int q = 0; q < 2 && rc == SRLA_OK; q++) {
+    if (cudaEventCreateWithFlags(&h->ev_ready[q], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_free[q], cudaEventDisableTiming) != cudaSuccess)
+      rc = SRLA_E_CUDA;
+  }
   for (int q = 0; q < 2; q++) {
     h->slot[q].valid = false;
     h->slot[q].h_stats = reinterpret_cast<srla_slice_stats*>(static_cast<char*>(h->h_pinned) + q * per_slot);
@@ -385,7 +407,7 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
     if (cudaEventCreateWithFlags(&h->slot[q].ev, cudaEventDisableTiming) != cudaSuccess) rc = SRLA_E_CUDA;
   }
   if (rc == SRLA_OK) {
-    cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmallSmem);
+    cudaFuncSetAttribute(k_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmallSmem);
     rc = occupancy(h);
   }
   if (rc == SRLA_OK) rc = reset_tables(h, true);
@@ -416,18 +438,23 @@ int srla_push_packets(srla_t* h, const uint32_t* pairs, uint64_t n_pairs, int on
     if (r == SRLA_OK) h->n_pkts_open += n_pairs;
     return r;
   }
+  // Double-buffered staging: the copy of one half (on the internal copy stream) overlaps
+  // with the scan of the other half (on the caller's stream); events order the reuse.
   uint32_t* staging = h->at<uint32_t>(h->L.staging);
+  const uint64_t half = std::max<uint64_t>(2, (h->L.staging_pkts / 2) & ~1ull);
   while (n_pairs) {
-    if (h->staging_used == h->L.staging_pkts) {
-      SRLA_TRY(cudaStreamSynchronize(h->st));
-      h->staging_used = 0;
-    }
-    const uint64_t m = std::min<uint64_t>(n_pairs, h->L.staging_pkts - h->staging_used);
-    uint32_t* dst = staging + 2 * h->staging_used;
-    SRLA_TRY(cudaMemcpyAsync(dst, pairs, m * 8, cudaMemcpyHostToDevice, h->st));
+    const int x = h->stage_cur;
+    h->stage_cur ^= 1;
+    const uint64_t m = std::min<uint64_t>(n_pairs, half);
+    uint32_t* dst = staging + 2 * half * (uint64_t)x;
+    if (h->free_pending[x]) SRLA_TRY(cudaStreamWaitEvent(h->st_h2d, h->ev_free[x], 0));
+    SRLA_TRY(cudaMemcpyAsync(dst, pairs, m * 8, cudaMemcpyHostToDevice, h->st_h2d));
+    SRLA_TRY(cudaEventRecord(h->ev_ready[x], h->st_h2d));
+    SRLA_TRY(cudaStreamWaitEvent(h->st, h->ev_ready[x], 0));
     const int r = scan(dst, m);
     if (r != SRLA_OK) return r;
-    h->staging_used += m;
+    SRLA_TRY(cudaEventRecord(h->ev_free[x], h->st));
+    h->free_pending[x] = true;
     h->n_pkts_open += m;
     pairs += 2 * m;
     n_pairs -= m;
@@ -641,9 +668,12 @@ void srla_destroy(srla_t* h) {
     cudaStreamSynchronize(h->st);
     cudaStreamDestroy(h->st_copy);
   }
+  if (h->st_h2d) cudaStreamDestroy(h->st_h2d);
   for (int q = 0; q < 2; q++) {
     if (h->slot[q].ev) cudaEventDestroy(h->slot[q].ev);
     if (h->graph[q]) cudaGraphExecDestroy(h->graph[q]);
+    if (h->ev_ready[q]) cudaEventDestroy(h->ev_ready[q]);
+    if (h->ev_free[q]) cudaEventDestroy(h->ev_free[q]);
   }
   if (h->h_pinned) cudaFreeHost(h->h_pinned);
   delete h;
@@ -690,7 +720,7 @@ int static_scratch_setup(int dev, void** out) {
   if (!g_static_addr[dev]) {
     void* addr = nullptr;
     if (cudaGetSymbolAddress(&addr, g_static_scratch) != cudaSuccess || !addr) return cuda_err(cudaErrorUnknown);
-    if (cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmallSmem) !=
+    if (cudaFuncSetAttribute(k_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmallSmem) !=
         cudaSuccess)
       return cuda_err(cudaErrorUnknown);
     g_static_addr[dev] = addr;
@@ -743,10 +773,12 @@ extern "C" int srla_batch_report_static(const srla_params* p, const uint32_t* d_
   // The array keeps the previous call's contents: the recorders, the sets and the control
   // block must start at zero, so the whole used part is cleared first.
   SRLA_TRY(cudaMemsetAsync(h.ws, 0, L.total, h.st));
+  if ((r = clear_pairs(&h)) != SRLA_OK) return r;
   Ctl c{};
   c.T = h.T;
   c.tm = (uint32_t)(h.T % h.geo.P);
   c.w_star = h.geo.gl + 1;
+  c.pair_mode = 1;
   SRLA_TRY(cudaMemcpyAsync(h.ctl(), &c, sizeof(Ctl), cudaMemcpyHostToDevice, h.st));
   r = q.dr_bytes == 1 ? static_batch<uint8_t>(&h, d_pairs, n_pairs) : static_batch<uint16_t>(&h, d_pairs, n_pairs);
   if (r != SRLA_OK) return r;

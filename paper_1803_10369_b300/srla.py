@@ -26,6 +26,7 @@ class srla_params(ctypes.Structure):
         ("dr_bytes", ctypes.c_uint32), ("z", ctypes.c_uint32), ("k", ctypes.c_uint32), ("theta", ctypes.c_uint32),
         ("start_slice", ctypes.c_uint64), ("staging_pkts", ctypes.c_uint64),
         ("max_sampled", ctypes.c_uint32), ("max_candidates", ctypes.c_uint32),
+        ("pair_slots_log2", ctypes.c_int32), ("reserved", ctypes.c_uint32),
         ("hash_a", ctypes.c_uint64 * N_HASH), ("hash_b", ctypes.c_uint64 * N_HASH),
     ]
 
@@ -105,8 +106,9 @@ def _ck(code: int, what: str):
 
 
 def make_params(u, v, g, gl, dr_bytes, z, k, theta, hash_a, hash_b, start_slice=0, staging_pkts=0,
-                max_sampled=1 << 16, max_candidates=1 << 14) -> srla_params:
+                max_sampled=1 << 16, max_candidates=1 << 14, pair_slots_log2=0) -> srla_params:
     p = srla_params()
+    p.pair_slots_log2 = pair_slots_log2
     p.u, p.v, p.g, p.gl = u, v, g, gl
     p.dr_bytes, p.z, p.k, p.theta = dr_bytes, z, k, theta
     p.start_slice, p.staging_pkts = start_slice, staging_pkts
@@ -163,6 +165,7 @@ class Link:
                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), "srla_create")
         self._h = h
         self._last = None
+        self._out = np.empty(params.max_candidates, dtype=ENTRY_DTYPE)  # reused report buffer
 
     # -- packets ---------------------------------------------------------------
     def push(self, pairs):
@@ -197,7 +200,9 @@ class Link:
             slice_id = self._last
         if cap is None:
             cap = self.params.max_candidates
-        out = np.zeros(cap, dtype=ENTRY_DTYPE)
+            out = self._out
+        else:
+            out = np.empty(cap, dtype=ENTRY_DTYPE)
         n = ctypes.c_size_t()
         st = srla_slice_stats()
         rc = self.L.srla_report(self._h, slice_id, ctypes.c_void_p(out.ctypes.data), cap, ctypes.byref(n),

@@ -56,6 +56,7 @@ def _params(**kw):
 def test_param_validation():
     assert srla.check_params(_params()) == 0
     bad = [dict(u=0), dict(u=17), dict(v=1000), dict(g=48), dict(gl=0), dict(dr_bytes=3), dict(z=9),
+           dict(pair_slots_log2=9), dict(pair_slots_log2=29), dict(pair_slots_log2=-2),
            dict(dr_bytes=2, z=17), dict(k=0), dict(k=256), dict(z=3, k=8), dict(theta=0),
            dict(g=2, dr_bytes=1), dict(v=1, g=4, gl=4)]
     for kw in bad:

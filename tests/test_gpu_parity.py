@@ -188,3 +188,18 @@ def test_import_oracle_state_then_continue(cuda_device):
         link.push(trace[s].to(cuda_device))
         compare_reports(o.end_slice(), link.report(link.end_slice()), f"slice {s}")
         compare_state(o, link, f"slice {s}")
+
+
+@pytest.mark.parametrize("pair_log2", [-1, 10])
+def test_pair_table_disabled_or_overfull(pair_log2, cuda_device):
+    """The per-slice table of scanned pairs only skips repeated work: without it, or with a
+    table far too small for the slice (probes give up and the pair is scanned), results are
+    the same.  The traffic repeats pairs heavily (small per-source destination pools)."""
+    w = TINY.replace(dst_model="pool", pool_max=8, n_slices=6)
+    o, link = make_pair(w, pair_slots_log2=pair_log2)
+    for s in range(w.n_slices):
+        pk = synth.generate_slice(w.traffic, s)
+        o.push(synth.pairs_to_numpy(pk))
+        link.push(pk.to(cuda_device))
+        compare_reports(o.end_slice(), link.report(link.end_slice()), f"pairs {pair_log2} slice {s}")
+        compare_state(o, link, f"pairs {pair_log2} slice {s}")

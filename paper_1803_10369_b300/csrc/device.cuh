@@ -178,6 +178,31 @@ __device__ __forceinline__ int set_insert(unsigned long long* tab, uint32_t mask
   return -1;
 }
 
+// set_insert continued from a first probe already loaded: slot s holds cur.
+__device__ __forceinline__ int set_insert_from(unsigned long long* tab, uint32_t mask, uint32_t tag, uint32_t key,
+                                               uint32_t s, unsigned long long cur, uint32_t* slot_out) {
+  const unsigned long long want = ((unsigned long long)tag << 32) | key;
+  const uint32_t limit = 2u * mask + 4u;
+  for (uint32_t it = 0; it < limit; it++) {
+    if ((uint32_t)(cur >> 32) == tag) {
+      if ((uint32_t)cur == key) {
+        *slot_out = s;
+        return 0;
+      }
+      s = (s + 1) & mask;
+      cur = tab[s];
+      continue;
+    }
+    const unsigned long long old = atomicCAS(tab + s, cur, want);
+    if (old == cur) {
+      *slot_out = s;
+      return 1;
+    }
+    cur = old;
+  }
+  return -1;
+}
+
 // Find key with tag; returns the slot or 0xFFFFFFFF.
 __device__ __forceinline__ uint32_t set_find(const unsigned long long* tab, uint32_t mask, uint32_t tag,
                                              uint32_t key) {
@@ -216,7 +241,7 @@ __device__ __forceinline__ void load_words(const uint32_t* run, uint32_t w0, uin
   }
 }
 
-// Rows are fetched eight at a time, all loads in flight before any is used.
+// Rows are fetched four at a time, all loads in flight before any is used.
 template <typename CellT, int WPL>
 __device__ __forceinline__ uint32_t union_count_w(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
                                                   uint32_t u, uint32_t mycol, const Win& win, int lane) {
@@ -229,17 +254,17 @@ __device__ __forceinline__ uint32_t union_count_w(const CellT* __restrict__ arr,
     uint32_t m[WPL];
 #pragma unroll
     for (int q = 0; q < WPL; q++) m[q] = 0xFFFFFFFFu;
-    for (uint32_t i0 = 0; i0 < u; i0 += 8) {
-      uint32_t wd[8][WPL];
+    for (uint32_t i0 = 0; i0 < u; i0 += 4) {
+      uint32_t wd[4][WPL];
 #pragma unroll
-      for (int r = 0; r < 8; r++) {
+      for (int r = 0; r < 4; r++) {
         const uint32_t i = i0 + (uint32_t)r;
         const uint32_t c = __shfl_sync(kFull, mycol, (int)(i & 31u));
         if (ok && i < u)
           load_words<WPL>(reinterpret_cast<const uint32_t*>(arr + ((size_t)i * v + c) * cells), w0, wd[r]);
       }
 #pragma unroll
-      for (int r = 0; r < 8; r++)
+      for (int r = 0; r < 4; r++)
         if (ok && i0 + (uint32_t)r < u) {
 #pragma unroll
           for (int q = 0; q < WPL; q++) m[q] &= window_mask<CellT>(wd[r][q], win);
@@ -266,43 +291,56 @@ __device__ __forceinline__ uint32_t union_count(const CellT* __restrict__ arr, u
 // `need`: rows are joined one at a time and the join stops as soon as fewer than `need`
 // cells remain inside the window in every row so far (the union can only shrink).  The
 // result is exact when it is >= need; below need it is some value < need.
+// |URE|^k of two hosts at once (their row loads overlap), for a caller that only needs to
+// know whether each reaches `need`: rows are joined one at a time, and a host stops as soon
+// as fewer than `need` cells remain inside the window in every row so far (the union can
+// only shrink).  A count is exact when it is >= need; below need it is some value < need.
 template <typename CellT, int WPL>
-__device__ __forceinline__ uint32_t union_count_atleast_w(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
-                                                          uint32_t u, uint32_t mycol, const Win& win, uint32_t need,
-                                                          int lane) {
+__device__ __forceinline__ void union_count_atleast2_w(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
+                                                       uint32_t u, uint32_t col0, uint32_t col1, const Win& win,
+                                                       uint32_t need, int lane, uint32_t& out0, uint32_t& out1) {
   const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;
   const uint32_t w0 = (uint32_t)lane * WPL;
   const bool ok = w0 < R;
-  uint32_t m[WPL];
+  uint32_t m0[WPL], m1[WPL];
 #pragma unroll
-  for (int q = 0; q < WPL; q++) m[q] = ok ? 0xFFFFFFFFu : 0u;
-  uint32_t total = 0;
-  for (uint32_t i = 0; i < u; i++) {
-    const uint32_t c = __shfl_sync(kFull, mycol, (int)i);
-    if (ok) {
-      uint32_t wd[WPL];
-      load_words<WPL>(reinterpret_cast<const uint32_t*>(arr + ((size_t)i * v + c) * cells), w0, wd);
+  for (int q = 0; q < WPL; q++) m0[q] = m1[q] = ok ? 0xFFFFFFFFu : 0u;
+  bool live0 = true, live1 = true;
+  out0 = out1 = 0;
+  for (uint32_t i = 0; i < u && (live0 || live1); i++) {
+    const uint32_t c0 = __shfl_sync(kFull, col0, (int)i), c1 = __shfl_sync(kFull, col1, (int)i);
+    uint32_t wd0[WPL], wd1[WPL];
+    if (ok && live0) load_words<WPL>(reinterpret_cast<const uint32_t*>(arr + ((size_t)i * v + c0) * cells), w0, wd0);
+    if (ok && live1) load_words<WPL>(reinterpret_cast<const uint32_t*>(arr + ((size_t)i * v + c1) * cells), w0, wd1);
+    uint32_t p0 = 0, p1 = 0;
 #pragma unroll
-      for (int q = 0; q < WPL; q++) m[q] &= window_mask<CellT>(wd[q], win);
+    for (int q = 0; q < WPL; q++) {
+      if (ok && live0) m0[q] &= window_mask<CellT>(wd0[q], win);
+      if (ok && live1) m1[q] &= window_mask<CellT>(wd1[q], win);
+      p0 += __popc(m0[q]);
+      p1 += __popc(m1[q]);
     }
-    uint32_t part = 0;
-#pragma unroll
-    for (int q = 0; q < WPL; q++) part += __popc(m[q]);
-    total = cells_of_bits<CellT>(warp_sum(part));
-    if (total < need) break;  // warp-uniform
+    if (live0) {
+      out0 = cells_of_bits<CellT>(warp_sum(p0));
+      live0 = out0 >= need;
+    }
+    if (live1) {
+      out1 = cells_of_bits<CellT>(warp_sum(p1));
+      live1 = out1 >= need;
+    }
   }
-  return total;
 }
 
 template <typename CellT>
-__device__ __forceinline__ uint32_t union_count_atleast(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
-                                                        uint32_t u, uint32_t mycol, const Win& win, uint32_t need,
-                                                        int lane) {
+__device__ __forceinline__ void union_count_atleast2(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
+                                                     uint32_t u, uint32_t col0, uint32_t col1, const Win& win,
+                                                     uint32_t need, int lane, uint32_t& out0, uint32_t& out1) {
   const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;
-  if (R <= 32) return union_count_atleast_w<CellT, 1>(arr, v, cells, u, mycol, win, need, lane);
-  if (R <= 64) return union_count_atleast_w<CellT, 2>(arr, v, cells, u, mycol, win, need, lane);
-  if (R <= 128) return union_count_atleast_w<CellT, 4>(arr, v, cells, u, mycol, win, need, lane);
-  return union_count<CellT>(arr, v, cells, u, mycol, win, lane);
+  if (R <= 32) return union_count_atleast2_w<CellT, 1>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
+  if (R <= 64) return union_count_atleast2_w<CellT, 2>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
+  if (R <= 128) return union_count_atleast2_w<CellT, 4>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
+  out0 = union_count<CellT>(arr, v, cells, u, col0, win, lane);
+  out1 = union_count<CellT>(arr, v, cells, u, col1, win, lane);
 }
 
 }  // namespace srla

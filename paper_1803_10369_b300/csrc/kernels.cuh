@@ -36,11 +36,15 @@ constexpr int kPairProbes = 2;                             // probes into the sl
 // scan counts block misses and GPU-wide repeats, and the slice close switches the table off
 // for the next slice when fewer than a quarter of the misses were repeats (re-trying it
 // every 16 slices).
-__device__ __forceinline__ bool pair_claim(unsigned long long* __restrict__ ptab, uint32_t pmask,
-                                           unsigned long long key) {
-  uint32_t s = (uint32_t)((key * 0xD6E8FEB86659FD93ull) >> 32) & pmask;
+__device__ __forceinline__ uint32_t pair_home(unsigned long long key, uint32_t pmask) {
+  return (uint32_t)((key * 0xD6E8FEB86659FD93ull) >> 32) & pmask;
+}
+
+// Probes after the first: true if the pair is to be scanned (claimed, or no slot found).
+__device__ __forceinline__ bool pair_claim_from(unsigned long long* __restrict__ ptab, uint32_t pmask,
+                                                unsigned long long key, uint32_t s) {
 #pragma unroll 1
-  for (int i = 0; i < kPairProbes; i++) {
+  for (int i = 1; i < kPairProbes; i++) {
     const unsigned long long old = atomicCAS(ptab + s, kNoPair, key);
     if (old == kNoPair) return true;   // first in the slice: scan it
     if (old == key) return false;      // already scanned in this slice
@@ -53,36 +57,15 @@ __device__ __forceinline__ uint32_t seen_slot(unsigned long long key) {
   return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - kSeenLog2));
 }
 
+// Full scan of one pair per lane (a dense batch): Algorithm 2's DRsets, and the sampled host
+// into the slice's set (one probe per distinct host of the warp, one append counter update
+// per warp).  All 32 lanes call it; `ok` marks the lanes that hold a pair.
 template <typename CellT>
-__device__ __forceinline__ void scan_pair(uint32_t aip, uint32_t bip, bool ok, const Geo& geo,
-                                          const Coef& coef, CellT code, CellT* __restrict__ re,
-                                          CellT* __restrict__ le, Ctl* __restrict__ ctl,
-                                          unsigned long long* __restrict__ utab, uint32_t umask,
-                                          uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag,
-                                          int lane, volatile unsigned long long* seen,
-                                          unsigned long long* __restrict__ ptab, uint32_t pmask,
-                                          uint32_t& n_miss, uint32_t& n_gdup) {
-  bool miss = false, gdup = false;
-  if (ok) {
-    const unsigned long long key = ((unsigned long long)aip << 32) | bip;
-    if (key != kNoPair) {
-      const uint32_t h = seen_slot(key);
-      if (seen[h] == key) {
-        ok = false;  // already scanned in this slice by this block
-      } else {
-        seen[h] = key;
-        miss = true;
-        if (ptab) {
-          ok = pair_claim(ptab, pmask, key);
-          gdup = !ok;
-        }
-      }
-    }
-  }
-  if (ptab) {  // block misses and GPU-wide repeats, counted per thread
-    n_miss += miss;
-    n_gdup += gdup;
-  }
+__device__ __forceinline__ void scan_dense(uint32_t aip, uint32_t bip, bool ok, const Geo& geo, const Coef& coef,
+                                           CellT code, CellT* __restrict__ re, CellT* __restrict__ le,
+                                           Ctl* __restrict__ ctl, unsigned long long* __restrict__ utab,
+                                           uint32_t umask, uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag,
+                                           int lane) {
   const uint32_t u = geo.u;
   bool samp = false;
   if (ok) {
@@ -98,8 +81,6 @@ __device__ __forceinline__ void scan_pair(uint32_t aip, uint32_t bip, bool ok, c
       if (samp) re[se * geo.g + jr] = code;
     }
   }
-  // Add aip to the slice's sampled-host set: one probe per distinct host of the warp, one
-  // append counter update per warp.
   const unsigned sm = __ballot_sync(kFull, samp);
   int r = -2;
   if (samp) {
@@ -124,6 +105,75 @@ __device__ __forceinline__ void scan_pair(uint32_t aip, uint32_t bip, bool ok, c
         atomicOr(&ctl->overflow, 1u);
     }
   }
+}
+
+// Per-warp work queues in shared memory.  Pairs that miss the block's table go to queue 1;
+// 32 at a time they claim their slot in the slice's pair table with every lane busy, and
+// the pairs still to be scanned go to queue 2, scanned 32 at a time.  Divergent lanes would
+// otherwise pay for the whole scan path whenever any lane of the warp needs it.
+constexpr int kQueue = 64;
+
+struct ScanQueues {
+  volatile unsigned long long* q1;
+  volatile unsigned long long* q2;
+  uint32_t n1, n2;  // warp-uniform fill levels, both < 32 between drains
+};
+
+__device__ __forceinline__ void queue_push(volatile unsigned long long* q, uint32_t& n, bool pred,
+                                           unsigned long long key, int lane) {
+  const unsigned m = __ballot_sync(kFull, pred);
+  if (pred) q[n + (uint32_t)__popc(m & ((1u << lane) - 1u))] = key;
+  n += (uint32_t)__popc(m);
+  __syncwarp();
+}
+
+// Take the first min(n, 32) entries, one per lane; move the rest to the front.
+__device__ __forceinline__ bool queue_take(volatile unsigned long long* q, uint32_t& n, int lane,
+                                           unsigned long long& key) {
+  const bool ok = (uint32_t)lane < n;
+  key = ok ? q[lane] : 0ull;
+  const uint32_t rest = n > 32u ? n - 32u : 0u;
+  const unsigned long long mv = (uint32_t)lane < rest ? q[32 + lane] : 0ull;
+  __syncwarp();
+  if ((uint32_t)lane < rest) q[lane] = mv;
+  __syncwarp();
+  n = rest;
+  return ok;
+}
+
+template <typename CellT>
+__device__ __forceinline__ void drain_scan(ScanQueues& Q, const Geo& geo, const Coef& coef, CellT code,
+                                           CellT* __restrict__ re, CellT* __restrict__ le, Ctl* __restrict__ ctl,
+                                           unsigned long long* __restrict__ utab, uint32_t umask,
+                                           uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag, int lane) {
+  unsigned long long key;
+  const bool ok = queue_take(Q.q2, Q.n2, lane, key);
+  scan_dense<CellT>((uint32_t)(key >> 32), (uint32_t)key, ok, geo, coef, code, re, le, ctl, utab, umask, ulist, umax,
+                    tag, lane);
+}
+
+template <typename CellT>
+__device__ __forceinline__ void drain_claim(ScanQueues& Q, unsigned long long* __restrict__ ptab, uint32_t pmask,
+                                            uint32_t& n_miss, uint32_t& n_gdup, const Geo& geo, const Coef& coef,
+                                            CellT code, CellT* __restrict__ re, CellT* __restrict__ le,
+                                            Ctl* __restrict__ ctl, unsigned long long* __restrict__ utab,
+                                            uint32_t umask, uint32_t* __restrict__ ulist, uint32_t umax,
+                                            uint32_t tag, int lane) {
+  unsigned long long key;
+  const bool ok = queue_take(Q.q1, Q.n1, lane, key);
+  bool scan = false;
+  if (ok) {
+    const uint32_t home = pair_home(key, pmask);
+    const unsigned long long old = atomicCAS(ptab + home, kNoPair, key);
+    bool dup = old == key;
+    if (old != kNoPair && !dup) dup = !pair_claim_from(ptab, pmask, key, (home + 1) & pmask);
+    scan = !dup;
+    n_miss += 1;
+    n_gdup += dup;
+  }
+  queue_push(Q.q2, Q.n2, scan, key, lane);
+  if (Q.n2 >= 32)
+    drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
 }
 
 template <bool kVec>
@@ -151,13 +201,14 @@ __device__ __forceinline__ void load_pairs(const uint32_t* __restrict__ pairs, u
 // Each warp iteration covers 128 packets: lane l holds packets 2l, 2l+1, 64+2l, 65+2l; the
 // next iteration's packets are loaded before the current ones are scanned.
 template <typename CellT, bool kVec>
-__global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restrict__ pairs, uint64_t n, Geo geo,
-                                                       const __grid_constant__ Coef coef, CellT* __restrict__ re,
-                                                       CellT* __restrict__ le, Ctl* __restrict__ ctl,
-                                                       unsigned long long* __restrict__ utab, uint32_t umask,
-                                                       uint32_t* __restrict__ ulist, uint32_t umax,
-                                                       unsigned long long* __restrict__ ptab, uint32_t pmask) {
+__global__ void __launch_bounds__(kScanThreads, 4) k_scan(const uint32_t* __restrict__ pairs, uint64_t n, Geo geo,
+                                                          const __grid_constant__ Coef coef, CellT* __restrict__ re,
+                                                          CellT* __restrict__ le, Ctl* __restrict__ ctl,
+                                                          unsigned long long* __restrict__ utab, uint32_t umask,
+                                                          uint32_t* __restrict__ ulist, uint32_t umax,
+                                                          unsigned long long* __restrict__ ptab, uint32_t pmask) {
   __shared__ unsigned long long seen_mem[kSeen];
+  __shared__ unsigned long long queue_mem[kScanThreads / 32][2][kQueue];
   volatile unsigned long long* seen = seen_mem;
   for (int x = threadIdx.x; x < kSeen; x += blockDim.x) seen[x] = kNoPair;
   __syncthreads();
@@ -166,6 +217,8 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
   const CellT code = (CellT)(tm + 1u);
   const uint32_t tag = slice_tag(ctl->T);
   const int lane = threadIdx.x & 31;
+  const int warp = threadIdx.x >> 5;
+  ScanQueues Q{queue_mem[warp][0], queue_mem[warp][1], 0u, 0u};
   const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
   uint64_t base = gw * 128;
@@ -179,15 +232,40 @@ __global__ void __launch_bounds__(kScanThreads) k_scan(const uint32_t* __restric
     bool nok[4];
     load_pairs<kVec>(pairs, n, next, lane, na, nb, nok);
 #pragma unroll
-    for (int j = 0; j < 4; j++)
-      scan_pair<CellT>(a[j], b[j], ok[j], geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, seen,
-                       ptab, pmask, n_miss, n_gdup);
+    for (int j = 0; j < 4; j++) {
+      const unsigned long long key = ((unsigned long long)a[j] << 32) | b[j];
+      bool miss = false;
+      if (ok[j]) {  // this block's table of recently scanned pairs
+        const uint32_t h = seen_slot(key);
+        if (key == kNoPair || seen[h] != key) {
+          miss = true;
+          if (key != kNoPair) seen[h] = key;
+        }
+      }
+      if (ptab) {
+        // the pair that marks empty slots cannot be claimed: it is always scanned
+        queue_push(Q.q1, Q.n1, miss && key != kNoPair, key, lane);
+        queue_push(Q.q2, Q.n2, miss && key == kNoPair, key, lane);
+        if (Q.n2 >= 32) drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+        if (Q.n1 >= 32)
+          drain_claim<CellT>(Q, ptab, pmask, n_miss, n_gdup, geo, coef, code, re, le, ctl, utab, umask, ulist, umax,
+                             tag, lane);
+      } else {
+        queue_push(Q.q2, Q.n2, miss, key, lane);
+        if (Q.n2 >= 32) drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+      }
+    }
 #pragma unroll
     for (int j = 0; j < 4; j++) {
       a[j] = na[j]; b[j] = nb[j]; ok[j] = nok[j];
     }
     base = next;
   }
+  // what is left in the queues
+  if (ptab && Q.n1)
+    drain_claim<CellT>(Q, ptab, pmask, n_miss, n_gdup, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag,
+                       lane);
+  while (Q.n2) drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
   if (ptab) {  // one global update per block
     __shared__ unsigned s_miss, s_gdup;
     if (threadIdx.x == 0) s_miss = s_gdup = 0;
@@ -343,36 +421,60 @@ __device__ __forceinline__ double eq9(uint32_t w, uint32_t gl, double up, uint32
   return est;
 }
 
+// A host that passes the union SRE test enters the open slice's candidate set (or, if it
+// was carried in, gains the NEW flag).
+__device__ __forceinline__ void filter_admit(Ctl* ctl, unsigned long long* ctab, uint32_t* cflags, uint32_t cmask,
+                                             uint32_t* clist, uint32_t cmax, int par, uint32_t tag, uint32_t aip,
+                                             bool pass) {
+  if (!pass) return;
+  atomicAdd(&ctl->n_new, 1u);
+  uint32_t slot;
+  const int r = set_insert(ctab, cmask, tag, aip, &slot);
+  if (r == 1) {
+    cflags[slot] = SRLA_NEW;
+    const unsigned at = atomicAdd(&ctl->cat_count[par], 1u);
+    if (at < cmax)
+      clist[at] = aip;
+    else
+      atomicOr(&ctl->overflow, 2u);
+  } else if (r == 0) {
+    atomicOr(&cflags[slot], SRLA_NEW);
+  } else {
+    atomicOr(&ctl->overflow, 2u);
+  }
+}
+
+// Eq. 8 (UP from the row census) and Eq. 9 for every union weight w in [0, g'], in FP64,
+// rounded once to FP32: for a fixed slice the estimate depends on w alone, so the estimate
+// kernel only looks it up.  Runs concurrently with the candidate filter and sort.
+__global__ void k_lut(Geo geo, Ctl* __restrict__ ctl, float* __restrict__ lut_est, uint32_t* __restrict__ lut_flags) {
+  __shared__ double s_up;
+  if (threadIdx.x == 0) {
+    s_up = slice_up(geo, ctl);
+    if (blockIdx.x == 0) ctl->up = s_up;
+  }
+  __syncthreads();
+  for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w <= geo.gl; w += gridDim.x * blockDim.x) {
+    uint32_t f;
+    const double e = eq9(w, geo.gl, s_up, geo.theta, &f);
+    lut_est[w] = (float)e;
+    lut_flags[w] = f;
+    if (f & SRLA_SUPER) atomicMin(&ctl->w_star, w);
+  }
+}
+
 // -------------------------------------------------------------- new candidates (b3)
 //
 // For every distinct host sampled in the open slice: |URE(aip)|^k at the end of the slice
 // (before the slide).  Hosts with at least ceil(rho*g) in-window union cells enter the
 // slice's candidate set, which already holds the hosts carried from the previous slice.
 template <typename CellT>
-__global__ void __launch_bounds__(256) k_filter(Geo geo, const __grid_constant__ Coef coef,
+__global__ void __launch_bounds__(256, 4) k_filter(Geo geo, const __grid_constant__ Coef coef,
                                                 const CellT* __restrict__ re, Ctl* __restrict__ ctl,
                                                 const uint32_t* __restrict__ ulist, uint32_t umax,
                                                 unsigned long long* ctab0, unsigned long long* ctab1,
                                                 uint32_t* cflags0, uint32_t* cflags1, uint32_t cmask,
-                                                uint32_t* clist0, uint32_t* clist1, uint32_t cmax,
-                                                float* __restrict__ lut_est, uint32_t* __restrict__ lut_flags) {
-  // Eq. 8 and Eq. 9 for every union weight w in [0, g'], spread over all blocks: for a fixed
-  // slice the estimate depends on w alone, so the estimate kernel only looks it up.
-  {
-    __shared__ double s_up;
-    if (threadIdx.x == 0) {
-      s_up = slice_up(geo, ctl);
-      if (blockIdx.x == 0) ctl->up = s_up;
-    }
-    __syncthreads();
-    for (uint32_t w = blockIdx.x * blockDim.x + threadIdx.x; w <= geo.gl; w += gridDim.x * blockDim.x) {
-      uint32_t f;
-      const double e = eq9(w, geo.gl, s_up, geo.theta, &f);
-      lut_est[w] = (float)e;
-      lut_flags[w] = f;
-      if (f & SRLA_SUPER) atomicMin(&ctl->w_star, w);
-    }
-  }
+                                                uint32_t* clist0, uint32_t* clist1, uint32_t cmax) {
   const unsigned long long T = ctl->T;
   const int par = (int)(T & 1);
   unsigned long long* ctab = par ? ctab1 : ctab0;
@@ -384,26 +486,19 @@ __global__ void __launch_bounds__(256) k_filter(Geo geo, const __grid_constant__
   const int lane = threadIdx.x & 31;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t idx = gw; idx < n; idx += nw) {
-    const uint32_t aip = ulist[idx];
-    const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
-    const uint32_t cnt = union_count_atleast<CellT>(re, geo.v, geo.g, geo.u, mycol, win, geo.rho_g, lane);
-    if (lane == 0 && cnt >= geo.rho_g) {
-      atomicAdd(&ctl->n_new, 1u);
-      uint32_t slot;
-      const int r = set_insert(ctab, cmask, tag, aip, &slot);
-      if (r == 1) {
-        cflags[slot] = SRLA_NEW;
-        const unsigned at = atomicAdd(&ctl->cat_count[par], 1u);
-        if (at < cmax)
-          clist[at] = aip;
-        else
-          atomicOr(&ctl->overflow, 2u);
-      } else if (r == 0) {
-        atomicOr(&cflags[slot], SRLA_NEW);
-      } else {
-        atomicOr(&ctl->overflow, 2u);
-      }
+  // two hosts per warp and iteration, so that their gathers overlap
+  for (uint32_t idx = 2 * gw; idx < n; idx += 2 * nw) {
+    const bool two = idx + 1 < n;
+    const uint32_t aip0 = ulist[idx];
+    const uint32_t aip1 = two ? ulist[idx + 1] : aip0;
+    const bool mine = (uint32_t)lane < geo.u;
+    const uint32_t col0 = mine ? hash61(coef.a[lane], coef.b[lane], aip0) & geo.vmask : 0u;
+    const uint32_t col1 = mine ? hash61(coef.a[lane], coef.b[lane], aip1) & geo.vmask : 0u;
+    uint32_t cnt0, cnt1;
+    union_count_atleast2<CellT>(re, geo.v, geo.g, geo.u, col0, col1, win, geo.rho_g, lane, cnt0, cnt1);
+    if (lane == 0) {
+      filter_admit(ctl, ctab, cflags, cmask, clist, cmax, par, tag, aip0, cnt0 >= geo.rho_g);
+      if (two) filter_admit(ctl, ctab, cflags, cmask, clist, cmax, par, tag, aip1, cnt1 >= geo.rho_g);
     }
   }
 }

@@ -136,6 +136,8 @@ struct srla_s {
   cudaStream_t st;
   cudaStream_t st_copy;  // internal stream for report remainders and checkpoints
   cudaStream_t st_h2d;   // internal stream for host-to-device copies of host batches
+  cudaStream_t st_side;  // internal stream: the estimator table beside filter and sort
+  cudaEvent_t ev_fork, ev_join;
   cudaEvent_t ev_ready[2], ev_free[2];  // staging halves: copied / consumed by the scan
   bool free_pending[2];
   int stage_cur;
@@ -235,13 +237,24 @@ int launch_end_slice(srla_t* h) {
   const Layout& L = h->L;
   int r;
   if ((r = launch_sweep<CellT>(h, 1, h->k_is_P ? 0 : 1, 0)) != SRLA_OK) return r;
-  h->launches += 2;  // filter, estimate
+  // Eq. 8/9 table: needs the census; runs beside the filter and sort when a side stream exists
+  const int lut_grid = (int)std::min<uint32_t>((h->p.gl + 1 + 255) / 256, (uint32_t)h->sms * 4);
+  h->launches += 3;  // lut, filter, estimate
+  if (h->st_side) {
+    SRLA_TRY(cudaEventRecord(h->ev_fork, h->st));
+    SRLA_TRY(cudaStreamWaitEvent(h->st_side, h->ev_fork, 0));
+    k_lut<<<lut_grid, 256, 0, h->st_side>>>(h->geo, h->ctl(), h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
+    SRLA_TRY(cudaEventRecord(h->ev_join, h->st_side));
+  } else {
+    k_lut<<<lut_grid, 256, 0, h->st>>>(h->geo, h->ctl(), h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
+  }
   k_filter<CellT><<<h->sms * 4, 256, 0, h->st>>>(
       h->geo, h->coef, h->at<CellT>(L.re), h->ctl(), h->at<uint32_t>(L.ulist), h->p.max_sampled,
       h->at<unsigned long long>(L.ctab[0]), h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]),
       h->at<uint32_t>(L.cflags[1]), L.cmask, h->at<uint32_t>(L.clist[0]), h->at<uint32_t>(L.clist[1]),
-      h->p.max_candidates, h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
+      h->p.max_candidates);
   if ((r = launch_sort(h)) != SRLA_OK) return r;
+  if (h->st_side) SRLA_TRY(cudaStreamWaitEvent(h->st, h->ev_join, 0));
   k_estimate<CellT><<<h->sms * 2, 256, 0, h->st>>>(
       h->geo, h->coef, h->at<CellT>(L.re), h->at<CellT>(L.le), h->ctl(), h->at<unsigned long long>(L.ctab[0]),
       h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]), h->at<uint32_t>(L.cflags[1]), L.cmask,
@@ -394,6 +407,10 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
     return SRLA_E_CUDA;
   }
   if (cudaStreamCreateWithFlags(&h->st_h2d, cudaStreamNonBlocking) != cudaSuccess) rc = SRLA_E_CUDA;
+  if (rc == SRLA_OK && (cudaStreamCreateWithFlags(&h->st_side, cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess))
+    rc = SRLA_E_CUDA;
   for (int q = 0; q < 2 && rc == SRLA_OK; q++) {
     if (cudaEventCreateWithFlags(&h->ev_ready[q], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_free[q], cudaEventDisableTiming) != cudaSuccess)
@@ -669,6 +686,9 @@ void srla_destroy(srla_t* h) {
     cudaStreamDestroy(h->st_copy);
   }
   if (h->st_h2d) cudaStreamDestroy(h->st_h2d);
+  if (h->st_side) cudaStreamDestroy(h->st_side);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (int q = 0; q < 2; q++) {
     if (h->slot[q].ev) cudaEventDestroy(h->slot[q].ev);
     if (h->graph[q]) cudaGraphExecDestroy(h->graph[q]);

@@ -55,6 +55,28 @@ def _algorithmic_bytes_per_pkt(w, tau):
     return 8.0 + w.u * w.dr_bytes + s * w.u * w.dr_bytes + s * 4.0
 
 
+# DRAM traffic of one k_scan launch (5M packets of the paper-scale workload) from one ncu
+# capture (profiles/k_scan_paper_scale.md), valid only for the kernel sources it was taken on.
+SCAN_TRAFFIC = {"bytes_per_launch": 103.865344e6 + 56.594688e6, "pkts": 5_000_000, "sources": "f0e31af2f691c56f"}
+
+
+def _kernel_sources_hash():
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1803_10369_b300", "csrc", "*.cu*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _scan_traffic(pkts_per_launch):
+    if _kernel_sources_hash() != SCAN_TRAFFIC["sources"] or pkts_per_launch != SCAN_TRAFFIC["pkts"]:
+        return None
+    return SCAN_TRAFFIC["bytes_per_launch"]
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -323,8 +345,8 @@ def bench_srla(args):
                        "slice_end_gpu_p50": round(statistics.median(lat_gpu), 4)},
         "scan_mpkts_s": round(per_launch_pkts / (scan_avg_ms * 1e-3) / 1e6, 3),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 5), "traffic": None, "kernel": "k_scan",
-                     "bytes_per_pkt": bpp, "peak_kind": peak_kind},
+                     "frac": round(achieved / peak, 5), "traffic": _scan_traffic(int(per_launch_pkts)),
+                     "kernel": "k_scan", "bytes_per_pkt": bpp, "peak_kind": peak_kind},
         "e2e": {"value": round(e2e, 3), "unit": "Mpkts/s", "h2d_bytes_per_step": int(8 * per_launch_pkts),
                 "d2h_bytes_per_step": int(statistics.mean(d2h))},
         "gpu_launches": int(launches),

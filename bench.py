@@ -48,6 +48,18 @@ def _dist():
     return rank, world, local
 
 
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """Max of a per-rank figure over all ranks (the job's wall time is its slowest rank's)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def _algorithmic_bytes_per_pkt(w, tau):
     """Bytes the scan must move per packet: the 8-byte pair, u SLE recorders, u SRE recorders
     for the 2^-tau sampled share, and a 4-byte sampled-host record for that share."""
@@ -281,12 +293,8 @@ def bench_srla(args):
         torch.cuda.synchronize(dev)
     launches = link.kernel_launches() - launches0
     barrier()
-    elapsed_ms = ev[0].elapsed_time(ev[1])
+    elapsed_ms = max_over_ranks(ev[0].elapsed_time(ev[1]), world, dev)
     scan_ms = [a.elapsed_time(b) for a, b in scan_ev]
-    if world > 1:
-        t = torch.tensor([elapsed_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
     total_pkts = pkts * world
     value = total_pkts / (elapsed_ms * 1e-3) / 1e6
 
@@ -325,11 +333,7 @@ def bench_srla(args):
     r = link.report(pending)
     d2h.append(64 + 16 * len(r["aip"]))
     torch.cuda.synchronize(dev)
-    e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
     e2e = total_pkts / e2e_s / 1e6
 
     peak, peak_kind = _peaks()

@@ -203,6 +203,68 @@ int srla_batch_report_static(const srla_params *p, const uint32_t *d_pairs, uint
                              srla_slice_stats *stats);
 const char *srla_strerror(int code);
 
+
+/* ======================================================================================
+ * Groups: many monitored links advanced together (one CUDA graph launch per slice).
+ *
+ * Each link is an independent estimator array (one per edge router, Section 3.1) with its
+ * own parameters, window and slice index.  A group owns one caller-provided workspace: a
+ * fixed part (link table, task table, report buffer, staging) and an arena from which link
+ * regions are carved when links attach.  Between two slice ends the caller pushes packets of
+ * any attached link; srla_group_end_slice then scans all of them and closes the slice of
+ * every attached link with one graph launch (kernels over all links, not one launch per
+ * link).  Attach and detach are allowed at slice boundaries (no packets pushed yet), which
+ * is how a serving loop admits and retires links while others keep running.
+ * ====================================================================================== */
+typedef struct srla_group_s srla_group_t;
+
+/* Fixed workspace part of a group (0 on invalid arguments).  The arena for links is the
+ * rest of the workspace given to srla_group_create.
+ *   max_links        link slots
+ *   max_pkts         packets per slice over all links (device and host batches)
+ *   max_host_pkts    packets per slice pushed from host memory (staged, double-buffered)
+ *   max_report       report entries per slice over all links                                */
+size_t srla_group_fixed_bytes(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_pkts,
+                              uint32_t max_report);
+
+/* Arena bytes one link with parameters p occupies (0 if p is invalid); for admission.    */
+size_t srla_group_link_bytes(const srla_params *p);
+
+int srla_group_create(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_pkts,
+                      uint32_t max_report, void *dev_workspace, size_t ws_bytes, void *stream,
+                      srla_group_t **out);
+
+/* Attach a link (fresh, empty recorders, slice index p->start_slice); *link receives its
+ * slot.  SRLA_E_NOMEM when the arena has no room, SRLA_E_CAPACITY when all slots are used,
+ * SRLA_E_ORDER when packets were already pushed in the open slice.                        */
+int srla_group_attach(srla_group_t *g, const srla_params *p, uint32_t *link);
+/* Detach a link; its arena region is reused by later attaches.  Reports of its past slices
+ * are no longer available.  SRLA_E_ORDER when packets were already pushed in the slice.  */
+int srla_group_detach(srla_group_t *g, uint32_t link);
+
+/* Packets of one link for the open slice (as srla_push_packets).  Device batches must stay
+ * unchanged until the slice end's work completes (srla_group_report / srla_group_sync).  */
+int srla_group_push(srla_group_t *g, uint32_t link, const uint32_t *pairs, uint64_t n_pairs,
+                    int on_device);
+
+/* Scan and close the open slice of every attached link; *group_slice receives the group
+ * slice counter (0, 1, 2, ...).                                                          */
+int srla_group_end_slice(srla_group_t *g, uint64_t *group_slice);
+
+/* All reports of a group slice (one of the two most recent ones): the entries of every link
+ * that was attached at that slice, concatenated in slot order, each link's sorted by aip.
+ * offsets[l] .. offsets[l+1] are link l's entries (max_links + 1 values); stats[l] its
+ * statistics (zeroed for free slots); either may be NULL.  Returns like srla_report.     */
+int srla_group_report_all(srla_group_t *g, uint64_t group_slice, srla_entry *out, size_t cap,
+                          size_t *n_out, uint32_t *offsets, srla_slice_stats *stats);
+/* One link's report of a group slice.                                                   */
+int srla_group_report(srla_group_t *g, uint32_t link, uint64_t group_slice, srla_entry *out,
+                      size_t cap, size_t *n_out, srla_slice_stats *stats);
+
+int srla_group_sync(srla_group_t *g);
+uint64_t srla_group_kernel_launches(const srla_group_t *g);
+void srla_group_destroy(srla_group_t *g);
+
 #ifdef __cplusplus
 }
 #endif

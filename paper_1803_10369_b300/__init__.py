@@ -2,6 +2,7 @@
 from .srla import (  # noqa: F401
     CARRIED,
     ENTRY_DTYPE,
+    Group,
     NEW,
     SATURATED,
     SUPER,

@@ -12,6 +12,14 @@ namespace srla {
 constexpr uint64_t kP61 = (1ull << 61) - 1;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
+// Candidate sort geometry: a tile of 4096 keys ranked by 16 warps, 8-bit radix digits.
+constexpr int kSortThreads = 512;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kKeysPerWarp = 256;
+constexpr int kSortTile = kSortWarps * kKeysPerWarp;  // 4096
+constexpr int kRadix = 256;
+constexpr size_t kSortSmallSmem = (size_t)kSortTile * sizeof(uint32_t);  // bitonic buffer
+
 // Hash coefficients, one (a, b) per role: rows 0..u-1, SLE cell, SRE cell, sampling.
 struct Coef {
   uint64_t a[SRLA_N_HASH];

@@ -1,0 +1,492 @@
+// Kernels of the multi-link group: the same scan and slice end as one link (scan_parts.cuh),
+// run for every attached link in one launch each.  Links are independent estimator arrays
+// (one per monitored edge router, Section 3.1); the kernels find their links, packet batches
+// and sweep work in device-resident tables, so one captured graph serves any membership.
+#pragma once
+
+#include "scan_parts.cuh"
+#include "sort_parts.cuh"
+
+namespace srla {
+
+// Everything a kernel needs to know about one attached link.
+struct LinkDesc {
+  Geo geo;
+  Coef coef;
+  uint32_t active;      // 0: free slot
+  uint32_t cell_bytes;  // 1 or 2
+  uint32_t k_is_P;
+  uint32_t umask, umax, cmask, cmax, ntiles, pmask;
+  uint32_t pad;
+  Ctl* ctl;
+  void* re;
+  void* le;
+  unsigned long long* utab;
+  uint32_t* ulist;
+  unsigned long long* ctab[2];
+  uint32_t* cflags[2];
+  uint32_t* clist[2];
+  uint32_t* sort_tmp;
+  uint32_t* sort_hist;
+  float* lut_est;
+  uint32_t* lut_flags;
+  srla_slice_stats* st[2];
+  unsigned long long* ptab;  // per-slice pair table, or null
+};
+
+// One packet batch of one link for the group scan (at most kTaskPkts packets).
+struct ScanTask {
+  unsigned long long ptr;  // device address of interleaved (aip, bip) uint32 pairs
+  uint32_t n;
+  uint32_t link;
+};
+constexpr uint32_t kTaskPkts = 1u << 16;
+
+// A streaming piece of per-slice sweep work.
+struct SweepChunk {
+  uint32_t link;
+  uint32_t kind;   // 0: SLE row (census, ageing), 1: SRE row (ageing), 2: pair table (clear)
+  uint32_t row;
+  uint32_t pad;
+  unsigned long long begin, count;  // 16-byte vectors
+};
+
+// Group control block (device).
+struct GroupCtl {
+  const SweepChunk* chunks;  // sweep work list (rebuilt when links attach or detach)
+  const SweepChunk* post;    // post-close ageing work list
+  unsigned int next_task;  // scan work counter
+  unsigned int blocks_done;
+  unsigned int bar_count, bar_gen;  // cooperative sort barrier
+  unsigned int n_links;    // slots (active or not)
+  unsigned int n_chunks;   // sweep chunks
+  unsigned int n_post;     // post-close ageing chunks (links with k = 2^z - 1)
+  unsigned int overflow;   // bit 2: a bounded wait gave up
+  unsigned int rep_cap;    // entries of the group report buffer
+  unsigned int pad[3];
+};
+
+// The per-slice task table: a 16-byte header (task count) followed by the tasks.
+struct TaskHeader {
+  unsigned int n_tasks;
+  unsigned int pad[3];
+};
+
+// ------------------------------------------------------------------------ scan
+
+template <typename CellT, bool kVec>
+__device__ __forceinline__ void group_scan_task(const ScanTask& t, const LinkDesc& D, Ctl* ctl,
+                                                volatile unsigned long long* seen, ScanQueues& Q, int lane, int warp,
+                                                int nwarps, uint32_t& n_miss, uint32_t& n_gdup) {
+  const uint32_t* pairs = reinterpret_cast<const uint32_t*>(t.ptr);
+  const uint64_t n = t.n;
+  CellT* re = static_cast<CellT*>(D.re);
+  CellT* le = static_cast<CellT*>(D.le);
+  unsigned long long* ptab = (D.ptab && ctl->pair_mode) ? D.ptab : nullptr;
+  const uint32_t tm = ctl->tm;
+  const CellT code = (CellT)(tm + 1u);
+  const uint32_t tag = slice_tag(ctl->T);
+  const Geo& geo = D.geo;
+  const Coef& coef = D.coef;
+  for (uint64_t base = (uint64_t)warp * 128; base < n; base += (uint64_t)nwarps * 128) {
+    uint32_t a[4], b[4];
+    bool ok[4];
+    load_pairs<kVec>(pairs, n, base, lane, a, b, ok);
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const unsigned long long key = ((unsigned long long)a[j] << 32) | b[j];
+      bool miss = false;
+      if (ok[j]) {
+        const uint32_t h = seen_slot(key);
+        if (key == kNoPair || seen[h] != key) {
+          miss = true;
+          if (key != kNoPair) seen[h] = key;
+        }
+      }
+      if (ptab) {
+        queue_push(Q.q1, Q.n1, miss && key != kNoPair, key, lane);
+        queue_push(Q.q2, Q.n2, miss && key == kNoPair, key, lane);
+        if (Q.n2 >= 32)
+          drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag, lane);
+        if (Q.n1 >= 32)
+          drain_claim<CellT>(Q, ptab, D.pmask, n_miss, n_gdup, geo, coef, code, re, le, ctl, D.utab, D.umask,
+                             D.ulist, D.umax, tag, lane);
+      } else {
+        queue_push(Q.q2, Q.n2, miss, key, lane);
+        if (Q.n2 >= 32)
+          drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag, lane);
+      }
+    }
+  }
+  if (ptab && Q.n1)
+    drain_claim<CellT>(Q, ptab, D.pmask, n_miss, n_gdup, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist,
+                       D.umax, tag, lane);
+  while (Q.n2) drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag, lane);
+}
+
+// Persistent blocks take scan tasks one at a time; a task is one link's batch, so the block's
+// pair table and the link's parameters (in shared memory) serve the whole task.
+template <int kThreads>
+__global__ void __launch_bounds__(kThreads) kg_scan(const LinkDesc* __restrict__ descs,
+                                                    const TaskHeader* __restrict__ thdr, GroupCtl* __restrict__ gctl) {
+  const ScanTask* tasks = reinterpret_cast<const ScanTask*>(thdr + 1);
+  __shared__ unsigned long long seen_mem[kSeen];
+  __shared__ unsigned long long queue_mem[kThreads / 32][2][kQueue];
+  __shared__ LinkDesc sdesc;
+  __shared__ ScanTask stask;
+  __shared__ unsigned s_task, s_miss, s_gdup;
+  volatile unsigned long long* seen = seen_mem;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const unsigned n_tasks = thdr->n_tasks;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      s_task = atomicAdd(&gctl->next_task, 1u);
+      s_miss = s_gdup = 0;
+    }
+    __syncthreads();
+    const unsigned ti = s_task;
+    if (ti >= n_tasks) break;
+    if (threadIdx.x == 0) stask = tasks[ti];
+    __syncthreads();
+    {  // the task's link parameters into shared memory
+      const uint32_t* src = reinterpret_cast<const uint32_t*>(descs + stask.link);
+      uint32_t* dst = reinterpret_cast<uint32_t*>(&sdesc);
+      for (int x = threadIdx.x; x < (int)(sizeof(LinkDesc) / 4); x += kThreads) dst[x] = src[x];
+    }
+    for (int x = threadIdx.x; x < kSeen; x += kThreads) seen[x] = kNoPair;
+    __syncthreads();
+    ScanQueues Q{queue_mem[warp][0], queue_mem[warp][1], 0u, 0u};
+    uint32_t n_miss = 0, n_gdup = 0;
+    const bool vec = (stask.ptr & 15ull) == 0;
+    Ctl* ctl = sdesc.ctl;
+    if (sdesc.cell_bytes == 1) {
+      if (vec) group_scan_task<uint8_t, true>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, n_miss, n_gdup);
+      else group_scan_task<uint8_t, false>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, n_miss, n_gdup);
+    } else {
+      if (vec) group_scan_task<uint16_t, true>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, n_miss, n_gdup);
+      else group_scan_task<uint16_t, false>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, n_miss, n_gdup);
+    }
+    n_miss = warp_sum(n_miss);
+    n_gdup = warp_sum(n_gdup);
+    if (lane == 0 && (n_miss | n_gdup)) {
+      atomicAdd(&s_miss, n_miss);
+      atomicAdd(&s_gdup, n_gdup);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && (s_miss | s_gdup)) {
+      atomicAdd(&ctl->n_miss, s_miss);
+      atomicAdd(&ctl->n_gdup, s_gdup);
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------- sweep
+
+template <typename CellT>
+__device__ __forceinline__ void group_sweep_chunk(const SweepChunk& c, const LinkDesc& D, int after_close) {
+  Ctl* ctl = D.ctl;
+  const bool is_le = c.kind == 0;
+  const size_t cells = (size_t)D.geo.v * (is_le ? D.geo.gl : D.geo.g);
+  uint4* base = reinterpret_cast<uint4*>(static_cast<CellT*>(is_le ? D.le : D.re) + (size_t)c.row * cells) + c.begin;
+  const uint32_t tm = ctl->tm, P = D.geo.P;
+  const uint32_t alias = 1u + (after_close ? tm : ((tm + 1u == P) ? 0u : tm + 1u));
+  const uint32_t asplat = splat<CellT>(alias);
+  const bool count = is_le && !after_close;
+  const bool reset = after_close ? true : !D.k_is_P;
+  SweepWin sw;
+  sw.hi = tm + 1u;
+  sw.wrap = D.geo.k > sw.hi;
+  sw.lo = sw.wrap ? sw.hi + P - D.geo.k + 1u : sw.hi - D.geo.k + 1u;
+  sw.len = D.geo.k;
+  uint32_t cnt = 0;
+  const size_t nvec = c.count;
+  size_t x = threadIdx.x;
+  for (; x + 3 * blockDim.x < nvec; x += 4 * blockDim.x) {
+    uint4 q[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) q[j] = base[x + j * blockDim.x];
+#pragma unroll
+    for (int j = 0; j < 4; j++) sweep_vec<CellT>(base, x + j * blockDim.x, q[j], count, reset, sw, alias, asplat, cnt);
+  }
+  for (; x < nvec; x += blockDim.x) sweep_vec<CellT>(base, x, base[x], count, reset, sw, alias, asplat, cnt);
+  if (count) {
+    __shared__ uint32_t part[32];
+    cnt = warp_sum(cnt);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = cnt;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      unsigned long long s = 0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += part[w];
+      atomicAdd(&ctl->census[c.row], s);
+    }
+    __syncthreads();
+  }
+}
+
+// Census and ageing of every link's recorders, and clearing of the pair tables.  The
+// post-close variant ages the links with k = 2^z - 1 after their slice was closed.
+__global__ void __launch_bounds__(256) kg_sweep(const LinkDesc* __restrict__ descs, const GroupCtl* __restrict__ gctl,
+                                                int post) {
+  const unsigned n = post ? gctl->n_post : gctl->n_chunks;
+  const SweepChunk* __restrict__ chunks = post ? gctl->post : gctl->chunks;
+  for (unsigned ci = blockIdx.x; ci < n; ci += gridDim.x) {
+    const SweepChunk c = chunks[ci];
+    const LinkDesc& D = descs[c.link];
+    if (c.kind == 2) {
+      uint4* p = reinterpret_cast<uint4*>(D.ptab) + c.begin;
+      const uint4 ones = make_uint4(~0u, ~0u, ~0u, ~0u);
+      for (size_t x = threadIdx.x; x < c.count; x += blockDim.x) p[x] = ones;
+      continue;
+    }
+    if (D.cell_bytes == 1)
+      group_sweep_chunk<uint8_t>(c, D, post);
+    else
+      group_sweep_chunk<uint16_t>(c, D, post);
+  }
+}
+
+// ------------------------------------------------------------------ Eq. 8, Eq. 9
+
+__global__ void kg_lut(const LinkDesc* __restrict__ descs, const GroupCtl* __restrict__ gctl) {
+  __shared__ double s_up;
+  for (unsigned l = blockIdx.x; l < gctl->n_links; l += gridDim.x) {
+    const LinkDesc& D = descs[l];
+    if (!D.active) continue;
+    if (threadIdx.x == 0) {
+      s_up = slice_up(D.geo, D.ctl);
+      D.ctl->up = s_up;
+    }
+    __syncthreads();
+    for (uint32_t w = threadIdx.x; w <= D.geo.gl; w += blockDim.x) {
+      uint32_t f;
+      const double e = eq9(w, D.geo.gl, s_up, D.geo.theta, &f);
+      D.lut_est[w] = (float)e;
+      D.lut_flags[w] = f;
+      if (f & SRLA_SUPER) atomicMin(&D.ctl->w_star, w);
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------- new candidates
+
+template <typename CellT>
+__device__ __forceinline__ void group_filter_link(const LinkDesc& D, uint32_t gw, uint32_t nw, int lane) {
+  Ctl* ctl = D.ctl;
+  const unsigned long long T = ctl->T;
+  const int par = (int)(T & 1);
+  const uint32_t tag = slice_tag(T);
+  const uint32_t n = min(ctl->n_sampled, D.umax);
+  const Win win = make_win<CellT>(ctl->tm, D.geo.P, D.geo.k);
+  const CellT* re = static_cast<const CellT*>(D.re);
+  for (uint32_t idx = 2 * gw; idx < n; idx += 2 * nw) {
+    const bool two = idx + 1 < n;
+    const uint32_t aip0 = D.ulist[idx];
+    const uint32_t aip1 = two ? D.ulist[idx + 1] : aip0;
+    const bool mine = (uint32_t)lane < D.geo.u;
+    const uint32_t col0 = mine ? hash61(D.coef.a[lane], D.coef.b[lane], aip0) & D.geo.vmask : 0u;
+    const uint32_t col1 = mine ? hash61(D.coef.a[lane], D.coef.b[lane], aip1) & D.geo.vmask : 0u;
+    uint32_t cnt0, cnt1;
+    union_count_atleast2<CellT>(re, D.geo.v, D.geo.g, D.geo.u, col0, col1, win, D.geo.rho_g, lane, cnt0, cnt1);
+    if (lane == 0) {
+      filter_admit(ctl, D.ctab[par], D.cflags[par], D.cmask, D.clist[par], D.cmax, par, tag, aip0,
+                   cnt0 >= D.geo.rho_g);
+      if (two)
+        filter_admit(ctl, D.ctab[par], D.cflags[par], D.cmask, D.clist[par], D.cmax, par, tag, aip1,
+                     cnt1 >= D.geo.rho_g);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256, 2) kg_filter(const LinkDesc* __restrict__ descs,
+                                                    const GroupCtl* __restrict__ gctl) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (unsigned l = 0; l < gctl->n_links; l++) {
+    const LinkDesc& D = descs[l];
+    if (!D.active) continue;
+    if (D.cell_bytes == 1)
+      group_filter_link<uint8_t>(D, gw, nw, lane);
+    else
+      group_filter_link<uint16_t>(D, gw, nw, lane);
+  }
+}
+
+// ------------------------------------------------------------------------- sort
+//
+// Candidate lists of up to one tile: one block each (bitonic in shared memory).  Longer
+// lists: all blocks together, one link after another (radix passes between grid barriers).
+
+__device__ __forceinline__ bool group_barrier(GroupCtl* g, unsigned nblocks) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = &g->bar_gen;
+    const unsigned gg = *gen;
+    __threadfence();
+    int ok = 1;
+    if (atomicAdd(&g->bar_count, 1u) == nblocks - 1u) {
+      g->bar_count = 0;
+      __threadfence();
+      atomicAdd(&g->bar_gen, 1u);
+    } else {
+      unsigned it = 0;
+      while (*gen == gg) {
+        if (++it > kBarrierSpinLimit) {
+          atomicOr(&g->overflow, 4u);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+    }
+    __threadfence();
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+__global__ void __launch_bounds__(kSortThreads) kg_sort(const LinkDesc* __restrict__ descs, GroupCtl* __restrict__ gctl,
+                                                        uint32_t* __restrict__ rep_off) {
+  extern __shared__ uint32_t bsm[];
+  __shared__ uint32_t wcnt[kSortWarps][kRadix];
+  __shared__ uint32_t tot[kRadix];
+  __shared__ uint32_t part[32];
+  const unsigned nl = gctl->n_links;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // where each link's entries go in the group report
+    uint32_t run = 0;
+    for (unsigned l = 0; l < nl; l++) {
+      rep_off[l] = run;
+      const LinkDesc& D = descs[l];
+      if (D.active) run += min(D.ctl->cat_count[D.ctl->T & 1], D.cmax);
+    }
+    rep_off[nl] = run;
+  }
+  for (unsigned l = blockIdx.x; l < nl; l += gridDim.x) {
+    const LinkDesc& D = descs[l];
+    if (!D.active) continue;
+    const unsigned long long T = D.ctl->T;
+    const uint32_t n = min(D.ctl->cat_count[T & 1], D.cmax);
+    if (n > 1 && n <= (uint32_t)kSortTile) bitonic_block(D.clist[T & 1], n, bsm);
+    __syncthreads();
+  }
+  for (unsigned l = 0; l < nl; l++) {
+    const LinkDesc& D = descs[l];
+    if (!D.active) continue;
+    const unsigned long long T = D.ctl->T;
+    const uint32_t n = min(D.ctl->cat_count[T & 1], D.cmax);
+    if (n <= (uint32_t)kSortTile) continue;
+    uint32_t* list = D.clist[T & 1];
+    const uint32_t ntiles = (n + kSortTile - 1) / kSortTile;
+    for (int pass = 0; pass < 4; pass++) {
+      const uint32_t* src = (pass & 1) ? D.sort_tmp : list;
+      uint32_t* dst = (pass & 1) ? list : D.sort_tmp;
+      radix_hist_tiles(src, n, ntiles, pass * 8, D.sort_hist, tot);
+      if (!group_barrier(gctl, gridDim.x)) return;
+      if (blockIdx.x == 0) radix_scan_block(D.sort_hist, ntiles * kRadix, part);
+      if (!group_barrier(gctl, gridDim.x)) return;
+      radix_scatter_tiles(src, dst, n, ntiles, pass * 8, D.sort_hist, wcnt, tot);
+      if (!group_barrier(gctl, gridDim.x)) return;
+    }
+  }
+}
+
+// ------------------------------------------------------ estimate, carry, close
+
+__device__ __forceinline__ bool grep_off_ok(uint32_t idx, uint32_t cap) { return idx < cap; }
+
+template <typename CellT>
+__device__ __forceinline__ void group_estimate_link(const LinkDesc& D, uint32_t gw, uint32_t nw, int lane,
+                                                    srla_entry* grep, uint32_t rep_cap, GroupCtl* gctl) {
+  Ctl* ctl = D.ctl;
+  const unsigned long long T = ctl->T;
+  const int par = (int)(T & 1);
+  const uint32_t tag = slice_tag(T), ntag = slice_tag(T + 1);
+  const uint32_t n = min(ctl->cat_count[par], D.cmax);
+  const Win win = make_win<CellT>(ctl->tm, D.geo.P, D.geo.k);
+  const Win win_post = make_win<CellT>(ctl->tm, D.geo.P, D.geo.k - 1u);
+  const CellT* re = static_cast<const CellT*>(D.re);
+  const CellT* le = static_cast<const CellT*>(D.le);
+  const uint32_t* clist = D.clist[par];
+  for (uint32_t idx = gw; idx < n; idx += nw) {
+    const uint32_t aip = clist[idx];
+    const uint32_t mycol = (uint32_t)lane < D.geo.u ? hash61(D.coef.a[lane], D.coef.b[lane], aip) & D.geo.vmask : 0u;
+    const uint32_t w = union_count<CellT>(le, D.geo.v, D.geo.gl, D.geo.u, mycol, win, lane);
+    const uint32_t cw = union_count<CellT>(re, D.geo.v, D.geo.g, D.geo.u, mycol, win_post, lane);
+    if (lane == 0) {
+      const uint32_t s = set_find(D.ctab[par], D.cmask, tag, aip);
+      const uint32_t origin = (s != 0xFFFFFFFFu) ? D.cflags[par][s] : 0u;
+      srla_entry e;
+      e.aip = aip;
+      e.w = w;
+      e.est = D.lut_est[w];
+      e.flags = origin | D.lut_flags[w];
+      if (grep_off_ok(idx, rep_cap)) grep[idx] = e; else atomicOr(&gctl->overflow, 2u);
+      if (cw >= D.geo.rho_g) {
+        uint32_t slot;
+        const int r = set_insert(D.ctab[par ^ 1], D.cmask, ntag, aip, &slot);
+        if (r == 1) {
+          D.cflags[par ^ 1][slot] = SRLA_CARRIED;
+          const unsigned at = atomicAdd(&ctl->cat_count[par ^ 1], 1u);
+          if (at < D.cmax)
+            D.clist[par ^ 1][at] = aip;
+          else
+            atomicOr(&ctl->overflow_next, 2u);
+        } else if (r < 0) {
+          atomicOr(&ctl->overflow_next, 2u);
+        }
+      }
+    }
+  }
+}
+
+// The last block closes every link's slice and gathers the links' statistics into one
+// array (copied to the host with a single transfer), then resets the group counters.
+__global__ void __launch_bounds__(256) kg_estimate(const LinkDesc* __restrict__ descs, GroupCtl* __restrict__ gctl,
+                                                   srla_slice_stats* __restrict__ gstats,
+                                                   const uint32_t* __restrict__ rep_off, srla_entry* __restrict__ grep) {
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31;
+  const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  const unsigned nl = gctl->n_links;
+  for (unsigned l = 0; l < nl; l++) {
+    const LinkDesc& D = descs[l];
+    if (!D.active) continue;
+    const uint32_t off = rep_off[l];
+    const uint32_t cap = gctl->rep_cap > off ? gctl->rep_cap - off : 0u;
+    if (D.cell_bytes == 1)
+      group_estimate_link<uint8_t>(D, gw, nw, lane, grep + off, cap, gctl);
+    else
+      group_estimate_link<uint16_t>(D, gw, nw, lane, grep + off, cap, gctl);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&gctl->blocks_done, 1u) == gridDim.x - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (unsigned l = threadIdx.x; l < nl; l += blockDim.x) {
+    const LinkDesc& D = descs[l];
+    if (!D.active) continue;
+    const int par = (int)(D.ctl->T & 1);
+    close_slice(D.geo, D.ctl, D.st[par], D.umax, D.cmax);
+    gstats[l] = *D.st[par];
+    gstats[l].overflow |= gctl->overflow & 6u;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    gctl->blocks_done = 0;
+    gctl->next_task = 0;
+    gctl->bar_count = 0;
+    gctl->overflow = 0;
+    __threadfence();
+  }
+}
+
+}  // namespace srla

@@ -1,0 +1,114 @@
+// Host-side helpers shared by the single-link and the multi-link C ABI: parameter checks,
+// the workspace layout of one link, and the constants of Eq. 1 and Section 3.2.
+#pragma once
+
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+
+#include "device.cuh"
+
+namespace srla {
+namespace host {
+
+inline constexpr size_t kAlign = 256;
+inline constexpr uint32_t kPrefetch = 2048;  // report entries copied with the slice's header
+inline constexpr uint32_t kStateMagic = 0x53524C41u;  // "SRLA"
+inline constexpr uint32_t kStateVersion = 1;
+
+inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+inline bool pow2(uint64_t x) { return x && !(x & (x - 1)); }
+
+inline uint64_t next_pow2(uint64_t x) {
+  uint64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
+
+struct Layout {
+  size_t ctl, re, le, staging, utab, ulist, ctab[2], cflags[2], clist[2], sort_tmp, sort_hist, lut_est,
+      lut_flags, rep_stats[2], rep_entries[2], ptab, total;
+  uint64_t staging_pkts;
+  uint32_t umask, cmask, ntiles, pmask;
+  bool pairs;  // per-slice pair table present
+};
+
+// Eq. 1 on integers: the least n >= 0 with g * 2^n >= theta.
+inline uint32_t tau_of(uint32_t theta, uint32_t g) {
+  uint32_t n = 0;
+  while ((uint64_t)g << n < (uint64_t)theta) n++;
+  return n;
+}
+
+// ceil(rho * g) with rho = 0.99 (1 - e^{-1/3}) (Section 3.2), evaluated in FP64.
+inline uint32_t rho_g_of(uint32_t g) { return (uint32_t)std::ceil(0.99 * (1.0 - std::exp(-1.0 / 3.0)) * (double)g); }
+
+inline int check(const srla_params* p) {
+  if (!p) return SRLA_E_INVAL;
+  if (p->u < 1 || p->u > SRLA_MAX_ROWS) return SRLA_E_INVAL;
+  if (!pow2(p->v) || !pow2(p->g) || !pow2(p->gl)) return SRLA_E_INVAL;
+  if (p->dr_bytes != 1 && p->dr_bytes != 2) return SRLA_E_INVAL;
+  if (p->z < 1 || p->z > 8 * p->dr_bytes) return SRLA_E_INVAL;
+  const uint32_t P = (1u << p->z) - 1u;
+  if (p->k < 1 || p->k > P) return SRLA_E_INVAL;
+  if (p->theta < 1) return SRLA_E_INVAL;
+  if ((uint64_t)p->g * p->dr_bytes < 4 || (uint64_t)p->gl * p->dr_bytes < 4) return SRLA_E_INVAL;
+  if ((uint64_t)p->v * p->g * p->dr_bytes < 16 || (uint64_t)p->v * p->gl * p->dr_bytes < 16) return SRLA_E_INVAL;
+  if ((uint64_t)p->v * p->gl > (1ull << 40) || (uint64_t)p->v * p->g > (1ull << 40)) return SRLA_E_INVAL;
+  if (p->gl > (1u << 24)) return SRLA_E_INVAL;
+  if (p->max_sampled < 1 || p->max_sampled > (1u << 30)) return SRLA_E_INVAL;
+  if (p->max_candidates < 1 || p->max_candidates > (1u << 26)) return SRLA_E_INVAL;
+  if (p->pair_slots_log2 != 0 && p->pair_slots_log2 != -1 && (p->pair_slots_log2 < 10 || p->pair_slots_log2 > 28))
+    return SRLA_E_INVAL;
+  for (uint32_t r = 0; r < p->u + 3; r++) {
+    if (p->hash_a[r] < 1 || p->hash_a[r] >= kP61) return SRLA_E_INVAL;
+    if (p->hash_b[r] >= kP61) return SRLA_E_INVAL;
+  }
+  return SRLA_OK;
+}
+
+inline Layout layout_of(const srla_params* p) {
+  Layout L{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  const size_t B = p->dr_bytes;
+  L.staging_pkts = p->staging_pkts ? std::max<uint64_t>(p->staging_pkts, 4) : (1ull << 20);
+  const uint64_t ucap = std::max<uint64_t>(64, next_pow2(2ull * p->max_sampled));
+  const uint64_t ccap = std::max<uint64_t>(64, next_pow2(2ull * p->max_candidates));
+  L.umask = (uint32_t)(ucap - 1);
+  L.cmask = (uint32_t)(ccap - 1);
+  L.ntiles = (p->max_candidates + kSortTile - 1) / kSortTile;
+  L.ctl = take(sizeof(Ctl));
+  L.re = take((size_t)p->u * p->v * p->g * B);
+  L.le = take((size_t)p->u * p->v * p->gl * B);
+  L.staging = take(L.staging_pkts * 8);
+  L.utab = take(ucap * 8);
+  L.ulist = take((size_t)p->max_sampled * 4);
+  for (int q = 0; q < 2; q++) {
+    L.ctab[q] = take(ccap * 8);
+    L.cflags[q] = take(ccap * 4);
+    L.clist[q] = take((size_t)p->max_candidates * 4);
+  }
+  L.sort_tmp = take((size_t)p->max_candidates * 4);
+  L.sort_hist = take((size_t)L.ntiles * kRadix * 4);
+  L.lut_est = take(((size_t)p->gl + 1) * 4);
+  L.lut_flags = take(((size_t)p->gl + 1) * 4);
+  for (int q = 0; q < 2; q++) {
+    L.rep_stats[q] = take(sizeof(srla_slice_stats));
+    L.rep_entries[q] = take((size_t)p->max_candidates * sizeof(srla_entry));
+  }
+  L.pairs = p->pair_slots_log2 != -1;
+  const uint32_t plog = p->pair_slots_log2 > 0 ? (uint32_t)p->pair_slots_log2 : 21u;
+  L.pmask = L.pairs ? (1u << plog) - 1u : 0u;
+  L.ptab = take(L.pairs ? ((size_t)1 << plog) * 8 : 0);
+  L.total = off;
+  return L;
+}
+
+}  // namespace host
+}  // namespace srla

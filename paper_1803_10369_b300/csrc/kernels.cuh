@@ -1,201 +1,10 @@
-// The kernels of the SRLA hot path: the per-packet scan (Algorithm 2) and the end-of-slice
-// pass (Section 4.2: row census, Eq. 8, Eq. 9; Algorithm 3: slide and carry).
+// The kernels of the SRLA hot path for one link: the per-packet scan (Algorithm 2) and the
+// end-of-slice pass (Section 4.2: row census, Eq. 8, Eq. 9; Algorithm 3: slide and carry).
 #pragma once
 
-#include <math.h>
-
-#include "device.cuh"
+#include "scan_parts.cuh"
 
 namespace srla {
-
-// ------------------------------------------------------------------------------ scan
-//
-// Algorithm 2 for one pair, under the order-free candidate rule: DRset the SLE recorder
-// selected by bip in each of the u estimators of aip; if LSB(H_S(bip)) >= tau, DRset the
-// SRE recorder selected by bip in the same estimators and add aip to the slice's set of
-// sampled hosts.  All writers of a slice write the same stamp, so plain stores are
-// race-free (Section 4.3 makes the same observation for its bits and recorders).
-//
-// A pair seen again in the same slice writes exactly the same stamps into exactly the same
-// recorders and samples the same host, so it can be skipped.  Each block keeps the pairs it
-// scanned last in a small direct-mapped table in shared memory; hot pairs (heavy sources
-// talk to few peers) then cost one shared-memory probe instead of u + u/2^tau scattered
-// stores that would all land on the same L2 sectors.
-
-constexpr int kSeenLog2 = 12;
-constexpr int kSeen = 1 << kSeenLog2;                      // pairs remembered per block
-constexpr unsigned long long kNoPair = ~0ull;              // empty slot; that pair is never cached
-constexpr int kScanThreads = 256;
-constexpr int kPairProbes = 2;                             // probes into the slice's pair table
-
-// Behind the per-block table sits one table of the pairs scanned anywhere on the GPU in the
-// open slice (cleared at every slice end).  A pair that missed its block's table claims a
-// slot with one compare-and-swap: the first claimant scans the pair, later ones skip it.  A
-// pair that finds no slot within kPairProbes probes is simply scanned, so a full table costs
-// speed, never correctness.  The table pays off only when pairs repeat across blocks: the
-// scan counts block misses and GPU-wide repeats, and the slice close switches the table off
-// for the next slice when fewer than a quarter of the misses were repeats (re-trying it
-// every 16 slices).
-__device__ __forceinline__ uint32_t pair_home(unsigned long long key, uint32_t pmask) {
-  return (uint32_t)((key * 0xD6E8FEB86659FD93ull) >> 32) & pmask;
-}
-
-// Probes after the first: true if the pair is to be scanned (claimed, or no slot found).
-__device__ __forceinline__ bool pair_claim_from(unsigned long long* __restrict__ ptab, uint32_t pmask,
-                                                unsigned long long key, uint32_t s) {
-#pragma unroll 1
-  for (int i = 1; i < kPairProbes; i++) {
-    const unsigned long long old = atomicCAS(ptab + s, kNoPair, key);
-    if (old == kNoPair) return true;   // first in the slice: scan it
-    if (old == key) return false;      // already scanned in this slice
-    s = (s + 1) & pmask;
-  }
-  return true;
-}
-
-__device__ __forceinline__ uint32_t seen_slot(unsigned long long key) {
-  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - kSeenLog2));
-}
-
-// Full scan of one pair per lane (a dense batch): Algorithm 2's DRsets, and the sampled host
-// into the slice's set (one probe per distinct host of the warp, one append counter update
-// per warp).  All 32 lanes call it; `ok` marks the lanes that hold a pair.
-template <typename CellT>
-__device__ __forceinline__ void scan_dense(uint32_t aip, uint32_t bip, bool ok, const Geo& geo, const Coef& coef,
-                                           CellT code, CellT* __restrict__ re, CellT* __restrict__ le,
-                                           Ctl* __restrict__ ctl, unsigned long long* __restrict__ utab,
-                                           uint32_t umask, uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag,
-                                           int lane) {
-  const uint32_t u = geo.u;
-  bool samp = false;
-  if (ok) {
-    const uint32_t jl = hash61(coef.a[u], coef.b[u], bip) & geo.glmask;
-    const uint32_t jr = hash61(coef.a[u + 1], coef.b[u + 1], bip) & geo.gmask;
-    const uint32_t hs = hash61(coef.a[u + 2], coef.b[u + 2], bip);
-    samp = (hs & geo.samp_mask) == 0;
-#pragma unroll 4
-    for (uint32_t i = 0; i < u; i++) {
-      const uint32_t c = hash61(coef.a[i], coef.b[i], aip) & geo.vmask;
-      const size_t se = (size_t)i * geo.v + c;
-      le[se * geo.gl + jl] = code;
-      if (samp) re[se * geo.g + jr] = code;
-    }
-  }
-  const unsigned sm = __ballot_sync(kFull, samp);
-  int r = -2;
-  if (samp) {
-    const unsigned peers = __match_any_sync(sm, aip);
-    if ((peers & ((1u << lane) - 1u)) == 0) {
-      uint32_t slot;
-      r = set_insert(utab, umask, tag, aip, &slot);
-      if (r < 0) atomicOr(&ctl->overflow, 1u);
-    }
-  }
-  const unsigned ins = __ballot_sync(kFull, r == 1);
-  if (ins) {
-    const int first = __ffs(ins) - 1;
-    unsigned base = 0;
-    if (lane == first) base = atomicAdd(&ctl->n_sampled, (unsigned)__popc(ins));
-    base = __shfl_sync(kFull, base, first);
-    if (r == 1) {
-      const unsigned idx = base + (unsigned)__popc(ins & ((1u << lane) - 1u));
-      if (idx < umax)
-        ulist[idx] = aip;
-      else
-        atomicOr(&ctl->overflow, 1u);
-    }
-  }
-}
-
-// Per-warp work queues in shared memory.  Pairs that miss the block's table go to queue 1;
-// 32 at a time they claim their slot in the slice's pair table with every lane busy, and
-// the pairs still to be scanned go to queue 2, scanned 32 at a time.  Divergent lanes would
-// otherwise pay for the whole scan path whenever any lane of the warp needs it.
-constexpr int kQueue = 64;
-
-struct ScanQueues {
-  volatile unsigned long long* q1;
-  volatile unsigned long long* q2;
-  uint32_t n1, n2;  // warp-uniform fill levels, both < 32 between drains
-};
-
-__device__ __forceinline__ void queue_push(volatile unsigned long long* q, uint32_t& n, bool pred,
-                                           unsigned long long key, int lane) {
-  const unsigned m = __ballot_sync(kFull, pred);
-  if (pred) q[n + (uint32_t)__popc(m & ((1u << lane) - 1u))] = key;
-  n += (uint32_t)__popc(m);
-  __syncwarp();
-}
-
-// Take the first min(n, 32) entries, one per lane; move the rest to the front.
-__device__ __forceinline__ bool queue_take(volatile unsigned long long* q, uint32_t& n, int lane,
-                                           unsigned long long& key) {
-  const bool ok = (uint32_t)lane < n;
-  key = ok ? q[lane] : 0ull;
-  const uint32_t rest = n > 32u ? n - 32u : 0u;
-  const unsigned long long mv = (uint32_t)lane < rest ? q[32 + lane] : 0ull;
-  __syncwarp();
-  if ((uint32_t)lane < rest) q[lane] = mv;
-  __syncwarp();
-  n = rest;
-  return ok;
-}
-
-template <typename CellT>
-__device__ __forceinline__ void drain_scan(ScanQueues& Q, const Geo& geo, const Coef& coef, CellT code,
-                                           CellT* __restrict__ re, CellT* __restrict__ le, Ctl* __restrict__ ctl,
-                                           unsigned long long* __restrict__ utab, uint32_t umask,
-                                           uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag, int lane) {
-  unsigned long long key;
-  const bool ok = queue_take(Q.q2, Q.n2, lane, key);
-  scan_dense<CellT>((uint32_t)(key >> 32), (uint32_t)key, ok, geo, coef, code, re, le, ctl, utab, umask, ulist, umax,
-                    tag, lane);
-}
-
-template <typename CellT>
-__device__ __forceinline__ void drain_claim(ScanQueues& Q, unsigned long long* __restrict__ ptab, uint32_t pmask,
-                                            uint32_t& n_miss, uint32_t& n_gdup, const Geo& geo, const Coef& coef,
-                                            CellT code, CellT* __restrict__ re, CellT* __restrict__ le,
-                                            Ctl* __restrict__ ctl, unsigned long long* __restrict__ utab,
-                                            uint32_t umask, uint32_t* __restrict__ ulist, uint32_t umax,
-                                            uint32_t tag, int lane) {
-  unsigned long long key;
-  const bool ok = queue_take(Q.q1, Q.n1, lane, key);
-  bool scan = false;
-  if (ok) {
-    const uint32_t home = pair_home(key, pmask);
-    const unsigned long long old = atomicCAS(ptab + home, kNoPair, key);
-    bool dup = old == key;
-    if (old != kNoPair && !dup) dup = !pair_claim_from(ptab, pmask, key, (home + 1) & pmask);
-    scan = !dup;
-    n_miss += 1;
-    n_gdup += dup;
-  }
-  queue_push(Q.q2, Q.n2, scan, key, lane);
-  if (Q.n2 >= 32)
-    drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
-}
-
-template <bool kVec>
-__device__ __forceinline__ void load_pairs(const uint32_t* __restrict__ pairs, uint64_t n, uint64_t base, int lane,
-                                           uint32_t a[4], uint32_t b[4], bool ok[4]) {
-#pragma unroll
-  for (int h = 0; h < 2; h++) {
-    const uint64_t p = base + (uint64_t)h * 64 + (uint64_t)lane * 2;
-    if (kVec && p + 1 < n) {
-      const uint4 q = __ldcs(reinterpret_cast<const uint4*>(pairs) + (p >> 1));
-      a[2 * h] = q.x; b[2 * h] = q.y; a[2 * h + 1] = q.z; b[2 * h + 1] = q.w;
-      ok[2 * h] = true; ok[2 * h + 1] = true;
-    } else {
-      ok[2 * h] = p < n;
-      ok[2 * h + 1] = p + 1 < n;
-      a[2 * h] = ok[2 * h] ? pairs[2 * p] : 0u;
-      b[2 * h] = ok[2 * h] ? pairs[2 * p + 1] : 0u;
-      a[2 * h + 1] = ok[2 * h + 1] ? pairs[2 * p + 2] : 0u;
-      b[2 * h + 1] = ok[2 * h + 1] ? pairs[2 * p + 3] : 0u;
-    }
-  }
-}
 
 // Packets are read as 16-byte vectors (two pairs) when the batch is 16-byte aligned.
 // Each warp iteration covers 128 packets: lane l holds packets 2l, 2l+1, 64+2l, 65+2l; the
@@ -284,71 +93,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan(const uint32_t* __rest
   }
 }
 
-// ------------------------------------------------------------- sweep and row census
-//
 // One streaming pass over a row of recorders (blockIdx.y < u: SLE row y; >= u: SRE row
-// y - u).  Census (Section 4.2): count the SLE recorders of the row inside the window at
-// the open slice (age < k).  Reset: clear the stamps whose age would reach P after the
-// slide, i.e. the code 1 + ((T + 1) mod P); this is the DRslide of Algorithm 3 at the
-// point where a distance saturates at 2^z - 1.
-// In-window cells of one 32-bit word (the interval form of make_win, one compare per cell).
-template <typename CellT>
-__device__ __forceinline__ uint32_t count_in_window(uint32_t word, uint32_t lo, uint32_t len, bool wrap,
-                                                    uint32_t hi) {
-  constexpr int kCells = 4 / (int)sizeof(CellT);
-  constexpr int kBits = 8 * (int)sizeof(CellT);
-  constexpr uint32_t kMask = (1u << kBits) - 1u;
-  uint32_t n = 0;
-#pragma unroll
-  for (int q = 0; q < kCells; q++) {
-    const uint32_t c = (word >> (q * kBits)) & kMask;
-    n += wrap ? (uint32_t)((c >= lo) | (c - 1u < hi)) : (uint32_t)(c - lo < len);
-  }
-  return n;
-}
-
-// Nonzero iff some cell of the word equals the splatted stamp (exact zero-cell test).
-template <typename CellT>
-__device__ __forceinline__ uint32_t has_stamp(uint32_t word, uint32_t asplat) {
-  const uint32_t x = word ^ asplat;
-  return sizeof(CellT) == 1 ? ((x - 0x01010101u) & ~x & 0x80808080u) : ((x - 0x00010001u) & ~x & 0x80008000u);
-}
-
-template <typename CellT>
-__device__ __forceinline__ uint32_t clear_stamp(uint32_t word, uint32_t alias) {
-  constexpr int kCells = 4 / (int)sizeof(CellT);
-  constexpr int kBits = 8 * (int)sizeof(CellT);
-  constexpr uint32_t kMask = (1u << kBits) - 1u;
-#pragma unroll
-  for (int q = 0; q < kCells; q++)
-    if (((word >> (q * kBits)) & kMask) == alias) word &= ~(kMask << (q * kBits));
-  return word;
-}
-
-struct SweepWin {
-  uint32_t lo, hi, len;
-  bool wrap;
-};
-
-template <typename CellT>
-__device__ __forceinline__ void sweep_vec(uint4* base, size_t x, uint4 q, bool count, bool reset, const SweepWin& sw,
-                                          uint32_t alias, uint32_t asplat, uint32_t& cnt) {
-  if (count)
-    cnt += count_in_window<CellT>(q.x, sw.lo, sw.len, sw.wrap, sw.hi) +
-           count_in_window<CellT>(q.y, sw.lo, sw.len, sw.wrap, sw.hi) +
-           count_in_window<CellT>(q.z, sw.lo, sw.len, sw.wrap, sw.hi) +
-           count_in_window<CellT>(q.w, sw.lo, sw.len, sw.wrap, sw.hi);
-  if (reset && (has_stamp<CellT>(q.x, asplat) | has_stamp<CellT>(q.y, asplat) | has_stamp<CellT>(q.z, asplat) |
-                has_stamp<CellT>(q.w, asplat))) {
-    uint4 r;
-    r.x = clear_stamp<CellT>(q.x, alias);
-    r.y = clear_stamp<CellT>(q.y, alias);
-    r.z = clear_stamp<CellT>(q.z, alias);
-    r.w = clear_stamp<CellT>(q.w, alias);
-    base[x] = r;
-  }
-}
-
+// y - u): census and stamp ageing.
 template <typename CellT>
 __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, CellT* __restrict__ le,
                                                Ctl* __restrict__ ctl, int do_census, int do_reset,
@@ -392,55 +138,6 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
       for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += part[w];
       atomicAdd(&ctl->census[row], s);
     }
-  }
-}
-
-// ------------------------------------------------------------- Eq. 8 and Eq. 9 (b2)
-//
-// UP = prod_i |LDR(i)|^k / (g' v) from the row census, and Eq. 9 for a union weight w, both
-// in FP64; the estimate is rounded once to FP32 when reported.  Edges: w <= g' UP gives 0;
-// w = g' or UP = 1 gives +inf (saturated).  The super point decision (estimate >= theta,
-// Definition 2) is taken in FP64.
-__device__ __forceinline__ double slice_up(const Geo& geo, const Ctl* ctl) {
-  const double cells = (double)geo.gl * (double)geo.v;
-  double up = 1.0;
-  for (uint32_t i = 0; i < geo.u; i++) up *= (double)ctl->census[i] / cells;
-  return up;
-}
-
-__device__ __forceinline__ double eq9(uint32_t w, uint32_t gl, double up, uint32_t theta, uint32_t* flags) {
-  const double g = (double)gl;
-  if (w == gl || up >= 1.0) {
-    *flags = SRLA_SATURATED | SRLA_SUPER;
-    return INFINITY;
-  }
-  *flags = 0;
-  if ((double)w <= g * up) return 0.0;
-  const double est = -g * log(1.0 - ((double)w - g * up) / (g * (1.0 - up)));
-  if (est >= (double)theta) *flags = SRLA_SUPER;
-  return est;
-}
-
-// A host that passes the union SRE test enters the open slice's candidate set (or, if it
-// was carried in, gains the NEW flag).
-__device__ __forceinline__ void filter_admit(Ctl* ctl, unsigned long long* ctab, uint32_t* cflags, uint32_t cmask,
-                                             uint32_t* clist, uint32_t cmax, int par, uint32_t tag, uint32_t aip,
-                                             bool pass) {
-  if (!pass) return;
-  atomicAdd(&ctl->n_new, 1u);
-  uint32_t slot;
-  const int r = set_insert(ctab, cmask, tag, aip, &slot);
-  if (r == 1) {
-    cflags[slot] = SRLA_NEW;
-    const unsigned at = atomicAdd(&ctl->cat_count[par], 1u);
-    if (at < cmax)
-      clist[at] = aip;
-    else
-      atomicOr(&ctl->overflow, 2u);
-  } else if (r == 0) {
-    atomicOr(&cflags[slot], SRLA_NEW);
-  } else {
-    atomicOr(&ctl->overflow, 2u);
   }
 }
 
@@ -576,40 +273,8 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
   __syncthreads();
   if (!s_last || threadIdx.x != 0) return;
   __threadfence();
-  srla_slice_stats* st = par ? st1 : st0;
-  st->slice = T;
-  st->n_pkts = 0;
-  st->n_sampled = min(ctl->n_sampled, umax);
-  st->n_new = ctl->n_new;
-  st->n_candidates = n;
-  st->n_carry_out = min(ctl->cat_count[par ^ 1], cmax);
-  st->w_star = min(ctl->w_star, geo.gl + 1u);
-  st->overflow = ctl->overflow;
-  st->up = ctl->up;
-  for (int i = 0; i < SRLA_MAX_ROWS; i++) {
-    st->census[i] = ctl->census[i];
-    ctl->census[i] = 0;
-  }
-  ctl->T = T + 1;
-  ctl->tm = (ctl->tm + 1u == geo.P) ? 0u : ctl->tm + 1u;
-  ctl->n_sampled = 0;
-  ctl->n_new = 0;
-  ctl->cat_count[par] = 0;
-  ctl->overflow = ctl->overflow_next;
-  ctl->overflow_next = 0;
-  ctl->blocks_done = 0;
-  ctl->bar_count = 0;
-  ctl->w_star = geo.gl + 1u;
-  // keep the per-slice pair table on while it finds repeats for >= 1/4 of the block misses
-  const bool measured = ctl->pair_mode != 0;
-  const bool worth = 4ull * ctl->n_gdup >= (unsigned long long)ctl->n_miss;
-  ctl->pair_mode = (measured ? worth : false) || ((T + 1) % 16 == 0) ? 1u : 0u;
-  ctl->n_miss = 0;
-  ctl->n_gdup = 0;
-  __threadfence();
+  close_slice(geo, ctl, par ? st1 : st0, umax, cmax);
 }
-
-// ------------------------------------------------------------------- checkpointing
 
 // Recorder stamps -> the paper's distances (2^z - 1 = empty), at the open slice.
 template <typename CellT>

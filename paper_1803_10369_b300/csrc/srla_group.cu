@@ -1,0 +1,598 @@
+// libsrla groups: many links advanced together, one CUDA graph launch per slice
+// (declared in include/srla.h).  Host code lays out the caller's workspace, carves link
+// regions out of its arena, keeps the device link table and work lists current, builds the
+// per-slice task table, and replays one captured graph per slice parity.
+#include <algorithm>
+#include <cstddef>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "group.cuh"
+#include "host_layout.h"
+
+using namespace srla;
+using namespace srla::host;
+
+namespace {
+
+constexpr uint64_t kChunkVecs = 1ull << 14;  // 256 KB of recorders per sweep chunk
+constexpr int kGroupScanThreads = 256;
+
+int gerr(cudaError_t e) {
+  if (e == cudaSuccess) return SRLA_OK;
+  (void)cudaGetLastError();
+  return SRLA_E_CUDA;
+}
+
+#define G_TRY(x)                   \
+  do {                             \
+    const int _r = gerr(x);        \
+    if (_r != SRLA_OK) return _r;  \
+  } while (0)
+
+uint64_t max_tasks_for(uint32_t max_links, uint64_t max_pkts) {
+  // every push may leave one partial task behind
+  return max_pkts / kTaskPkts + 8ull * max_links + 64;
+}
+
+struct Fixed {
+  size_t gctl, descs, tasks, gstats[2], rep_off[2], grep[2], stage[2], total;
+  uint64_t max_tasks;
+};
+
+Fixed fixed_layout(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_pkts, uint32_t max_report) {
+  Fixed F{};
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  F.max_tasks = max_tasks_for(max_links, max_pkts);
+  F.gctl = take(sizeof(GroupCtl));
+  F.descs = take(sizeof(LinkDesc) * max_links);
+  F.tasks = take(sizeof(TaskHeader) + sizeof(ScanTask) * F.max_tasks);
+  for (int q = 0; q < 2; q++) {
+    F.gstats[q] = take(sizeof(srla_slice_stats) * max_links);
+    F.rep_off[q] = take(sizeof(uint32_t) * (max_links + 1));
+    F.grep[q] = take(sizeof(srla_entry) * (size_t)max_report);
+    F.stage[q] = take(8 * (size_t)max_host_pkts);
+  }
+  F.total = off;
+  return F;
+}
+
+srla_params link_params(const srla_params& p) {
+  srla_params q = p;
+  q.staging_pkts = 4;  // host batches of a group go through the group's staging area
+  return q;
+}
+
+struct Slot {
+  bool active = false;
+  srla_params p{};
+  Layout L{};
+  size_t off = 0, bytes = 0;  // arena region
+  uint64_t T = 0;             // open slice of the link
+  uint64_t pkts_open = 0;
+  uint64_t attached_at = 0;   // first group slice of the link
+  uint64_t pkts_slice[2] = {0, 0};
+};
+
+struct Region {
+  size_t off, bytes;
+};
+
+}  // namespace
+
+struct srla_group_s {
+  uint32_t max_links = 0;
+  uint64_t max_pkts = 0, max_host_pkts = 0;
+  uint32_t max_report = 0;
+  Fixed F{};
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t st = nullptr, st_copy = nullptr, st_side = nullptr;
+  cudaEvent_t ev[2] = {nullptr, nullptr}, ev_fork = nullptr, ev_join = nullptr;
+  int sms = 0, scan_grid = 0, sort_grid = 0;
+  void* h_pinned = nullptr;
+  TaskHeader* h_tasks[2] = {nullptr, nullptr};
+  srla_slice_stats* h_stats[2] = {nullptr, nullptr};
+  uint32_t* h_off[2] = {nullptr, nullptr};
+  std::vector<Slot> slots;
+  std::vector<Region> free_list;
+  size_t chunk_off = 0, chunk_bytes = 0;  // arena region of the sweep work lists
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  uint64_t G = 0;
+  bool valid[2] = {false, false};
+  uint64_t G_of[2] = {0, 0};
+  std::vector<ScanTask> pending;
+  uint64_t stage_used = 0;
+  bool stage_waited = false;
+  uint64_t launches = 0, graph_launches = 0;
+
+  GroupCtl* gctl() const { return reinterpret_cast<GroupCtl*>(ws + F.gctl); }
+  LinkDesc* descs() const { return reinterpret_cast<LinkDesc*>(ws + F.descs); }
+};
+
+namespace {
+
+// ------------------------------------------------------------------ arena allocator
+
+bool arena_alloc(srla_group_t* g, size_t bytes, size_t* off) {
+  bytes = align_up(bytes);
+  for (size_t i = 0; i < g->free_list.size(); i++) {
+    Region& r = g->free_list[i];
+    if (r.bytes >= bytes) {
+      *off = r.off;
+      r.off += bytes;
+      r.bytes -= bytes;
+      if (r.bytes == 0) g->free_list.erase(g->free_list.begin() + (long)i);
+      return true;
+    }
+  }
+  return false;
+}
+
+void arena_free(srla_group_t* g, size_t off, size_t bytes) {
+  bytes = align_up(bytes);
+  if (!bytes) return;
+  auto it = std::lower_bound(g->free_list.begin(), g->free_list.end(), off,
+                             [](const Region& r, size_t o) { return r.off < o; });
+  it = g->free_list.insert(it, Region{off, bytes});
+  // coalesce with the neighbours
+  if (it + 1 != g->free_list.end() && it->off + it->bytes == (it + 1)->off) {
+    it->bytes += (it + 1)->bytes;
+    g->free_list.erase(it + 1);
+  }
+  if (it != g->free_list.begin() && (it - 1)->off + (it - 1)->bytes == it->off) {
+    (it - 1)->bytes += it->bytes;
+    g->free_list.erase(it);
+  }
+}
+
+// -------------------------------------------------------------- device link table
+
+LinkDesc make_desc(srla_group_t* g, const Slot& s) {
+  LinkDesc D{};
+  const srla_params& p = s.p;
+  const Layout& L = s.L;
+  char* base = g->ws + s.off;
+  const uint32_t tau = tau_of(p.theta, p.g);
+  D.geo = Geo{p.u, p.v, p.g, p.gl, p.v - 1, p.g - 1, p.gl - 1, p.k, (1u << p.z) - 1u,
+              tau >= 32 ? 0xFFFFFFFFu : ((1u << tau) - 1u), rho_g_of(p.g), p.theta};
+  for (int r = 0; r < SRLA_N_HASH; r++) {
+    D.coef.a[r] = p.hash_a[r];
+    D.coef.b[r] = p.hash_b[r];
+  }
+  D.active = 1;
+  D.cell_bytes = p.dr_bytes;
+  D.k_is_P = p.k == D.geo.P;
+  D.umask = L.umask;
+  D.umax = p.max_sampled;
+  D.cmask = L.cmask;
+  D.cmax = p.max_candidates;
+  D.ntiles = L.ntiles;
+  D.pmask = L.pmask;
+  D.ctl = reinterpret_cast<Ctl*>(base + L.ctl);
+  D.re = base + L.re;
+  D.le = base + L.le;
+  D.utab = reinterpret_cast<unsigned long long*>(base + L.utab);
+  D.ulist = reinterpret_cast<uint32_t*>(base + L.ulist);
+  for (int q = 0; q < 2; q++) {
+    D.ctab[q] = reinterpret_cast<unsigned long long*>(base + L.ctab[q]);
+    D.cflags[q] = reinterpret_cast<uint32_t*>(base + L.cflags[q]);
+    D.clist[q] = reinterpret_cast<uint32_t*>(base + L.clist[q]);
+    D.st[q] = reinterpret_cast<srla_slice_stats*>(base + L.rep_stats[q]);
+  }
+  D.sort_tmp = reinterpret_cast<uint32_t*>(base + L.sort_tmp);
+  D.sort_hist = reinterpret_cast<uint32_t*>(base + L.sort_hist);
+  D.lut_est = reinterpret_cast<float*>(base + L.lut_est);
+  D.lut_flags = reinterpret_cast<uint32_t*>(base + L.lut_flags);
+  D.ptab = L.pairs ? reinterpret_cast<unsigned long long*>(base + L.ptab) : nullptr;
+  return D;
+}
+
+void add_rows(std::vector<SweepChunk>& out, uint32_t link, uint32_t kind, uint32_t rows, uint64_t vecs_per_row) {
+  for (uint32_t r = 0; r < rows; r++)
+    for (uint64_t b = 0; b < vecs_per_row; b += kChunkVecs)
+      out.push_back(SweepChunk{link, kind, r, 0, b, std::min(kChunkVecs, vecs_per_row - b)});
+}
+
+// Rebuild the sweep work lists and the group counters (n_links, n_chunks, n_post) after a
+// membership change.  The lists live in the arena; the copies are ordered on the stream
+// after every slice end already enqueued, so no running graph sees a half-written list.
+int rebuild_work(srla_group_t* g) {
+  std::vector<SweepChunk> chunks, post;
+  uint32_t n_links = 0;
+  for (uint32_t l = 0; l < g->max_links; l++) {
+    const Slot& s = g->slots[l];
+    if (!s.active) continue;
+    n_links = l + 1;
+    const srla_params& p = s.p;
+    const uint64_t le_vecs = (uint64_t)p.v * p.gl * p.dr_bytes / 16, re_vecs = (uint64_t)p.v * p.g * p.dr_bytes / 16;
+    const bool kP = p.k == (1u << p.z) - 1u;
+    add_rows(chunks, l, 0, p.u, le_vecs);
+    if (!kP) add_rows(chunks, l, 1, p.u, re_vecs);
+    if (s.L.pairs) add_rows(chunks, l, 2, 1, ((uint64_t)s.L.pmask + 1) * 8 / 16);
+    if (kP) {
+      add_rows(post, l, 0, p.u, le_vecs);
+      add_rows(post, l, 1, p.u, re_vecs);
+    }
+  }
+  const size_t need = (chunks.size() + post.size()) * sizeof(SweepChunk);
+  if (g->chunk_bytes) arena_free(g, g->chunk_off, g->chunk_bytes);
+  g->chunk_bytes = 0;
+  size_t off = 0;
+  if (need && !arena_alloc(g, need, &off)) return SRLA_E_NOMEM;
+  g->chunk_off = off;
+  g->chunk_bytes = need;
+  SweepChunk* dchunks = reinterpret_cast<SweepChunk*>(g->ws + off);
+  if (!chunks.empty())
+    G_TRY(cudaMemcpyAsync(dchunks, chunks.data(), chunks.size() * sizeof(SweepChunk), cudaMemcpyHostToDevice, g->st));
+  if (!post.empty())
+    G_TRY(cudaMemcpyAsync(dchunks + chunks.size(), post.data(), post.size() * sizeof(SweepChunk),
+                          cudaMemcpyHostToDevice, g->st));
+  struct {
+    const SweepChunk* chunks;
+    const SweepChunk* post;
+    unsigned next_task, blocks_done, bar_count, bar_gen, n_links, n_chunks, n_post;
+  } head{dchunks, dchunks + chunks.size(), 0, 0, 0, 0, n_links, (unsigned)chunks.size(), (unsigned)post.size()};
+  constexpr size_t kHead = offsetof(GroupCtl, n_post) + sizeof(unsigned);  // fields up to n_post
+  static_assert(offsetof(decltype(head), n_post) + sizeof(unsigned) == kHead, "GroupCtl head layout");
+  G_TRY(cudaMemcpyAsync(g->gctl(), &head, kHead, cudaMemcpyHostToDevice, g->st));
+  return cudaStreamSynchronize(g->st) == cudaSuccess ? SRLA_OK : SRLA_E_CUDA;
+}
+
+// ------------------------------------------------------------------ the slice end
+
+int enqueue_slice(srla_group_t* g, int q) {
+  const Fixed& F = g->F;
+  LinkDesc* descs = g->descs();
+  GroupCtl* gctl = g->gctl();
+  G_TRY(cudaMemcpyAsync(g->ws + F.tasks, g->h_tasks[q], sizeof(TaskHeader) + sizeof(ScanTask) * F.max_tasks,
+                        cudaMemcpyHostToDevice, g->st));
+  g->launches += 6;  // scan, sweep, lut, filter, sort, estimate, (post sweep below)
+  kg_scan<kGroupScanThreads><<<g->scan_grid, kGroupScanThreads, 0, g->st>>>(
+      descs, reinterpret_cast<const TaskHeader*>(g->ws + F.tasks), gctl);
+  kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 0);
+  G_TRY(cudaEventRecord(g->ev_fork, g->st));
+  G_TRY(cudaStreamWaitEvent(g->st_side, g->ev_fork, 0));
+  kg_lut<<<std::max(1, std::min<int>((int)g->max_links, g->sms * 4)), 256, 0, g->st_side>>>(descs, gctl);
+  G_TRY(cudaEventRecord(g->ev_join, g->st_side));
+  kg_filter<<<g->sms * 4, 256, 0, g->st>>>(descs, gctl);
+  uint32_t* rep_off = reinterpret_cast<uint32_t*>(g->ws + F.rep_off[q]);
+  void* args[] = {&descs, &gctl, &rep_off};
+  G_TRY(cudaLaunchCooperativeKernel((const void*)kg_sort, dim3(g->sort_grid), dim3(kSortThreads), args,
+                                    kSortSmallSmem, g->st));
+  G_TRY(cudaStreamWaitEvent(g->st, g->ev_join, 0));
+  kg_estimate<<<g->sms * 2, 256, 0, g->st>>>(descs, gctl, reinterpret_cast<srla_slice_stats*>(g->ws + F.gstats[q]),
+                                             rep_off, reinterpret_cast<srla_entry*>(g->ws + F.grep[q]));
+  g->launches += 1;
+  kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 1);
+  G_TRY(cudaGetLastError());
+  G_TRY(cudaMemcpyAsync(g->h_stats[q], g->ws + F.gstats[q], sizeof(srla_slice_stats) * g->max_links,
+                        cudaMemcpyDeviceToHost, g->st));
+  G_TRY(cudaMemcpyAsync(g->h_off[q], rep_off, sizeof(uint32_t) * (g->max_links + 1), cudaMemcpyDeviceToHost, g->st));
+  return SRLA_OK;
+}
+
+int capture(srla_group_t* g) {
+  cudaStream_t user = g->st;
+  g->st = g->st_copy;
+  int rc = SRLA_OK;
+  for (int q = 0; q < 2 && rc == SRLA_OK; q++) {
+    cudaGraph_t graph = nullptr;
+    const uint64_t before = g->launches;
+    if (cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      rc = SRLA_E_CUDA;
+      break;
+    }
+    rc = enqueue_slice(g, q);
+    const cudaError_t e = cudaStreamEndCapture(g->st, &graph);
+    if (rc == SRLA_OK && e != cudaSuccess) rc = SRLA_E_CUDA;
+    if (rc == SRLA_OK && cudaGraphInstantiate(&g->graph[q], graph, 0) != cudaSuccess) rc = SRLA_E_CUDA;
+    if (graph) cudaGraphDestroy(graph);
+    g->graph_launches = g->launches - before;
+    g->launches = before;
+  }
+  g->st = user;
+  if (rc != SRLA_OK) (void)cudaGetLastError();
+  return rc;
+}
+
+// Before reusing the parity-q task table and staging half, the slice that used them last
+// (two slices ago) must be past its copies.
+int wait_parity(srla_group_t* g, int q) {
+  if (g->valid[q]) G_TRY(cudaEventSynchronize(g->ev[q]));
+  return SRLA_OK;
+}
+
+bool slot_was_attached(const srla_group_t* g, uint32_t link, uint64_t gs) {
+  const Slot& s = g->slots[link];
+  return s.active && s.attached_at <= gs;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t srla_group_fixed_bytes(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_pkts, uint32_t max_report) {
+  if (max_links < 1 || max_links > (1u << 16) || max_report < 1) return 0;
+  return fixed_layout(max_links, max_pkts, max_host_pkts, max_report).total;
+}
+
+size_t srla_group_link_bytes(const srla_params* p) {
+  if (check(p) != SRLA_OK) return 0;
+  const srla_params q = link_params(*p);
+  return align_up(layout_of(&q).total);
+}
+
+int srla_group_create(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_pkts, uint32_t max_report,
+                      void* dev_workspace, size_t ws_bytes, void* stream, srla_group_t** out) {
+  if (!out) return SRLA_E_INVAL;
+  *out = nullptr;
+  const size_t fixed = srla_group_fixed_bytes(max_links, max_pkts, max_host_pkts, max_report);
+  if (!fixed || !dev_workspace || reinterpret_cast<uintptr_t>(dev_workspace) % kAlign) return SRLA_E_INVAL;
+  if (ws_bytes < fixed) return SRLA_E_NOMEM;
+  srla_group_t* g = new (std::nothrow) srla_group_s();
+  if (!g) return SRLA_E_NOMEM;
+  g->max_links = max_links;
+  g->max_pkts = max_pkts;
+  g->max_host_pkts = max_host_pkts;
+  g->max_report = max_report;
+  g->F = fixed_layout(max_links, max_pkts, max_host_pkts, max_report);
+  g->ws = static_cast<char*>(dev_workspace);
+  g->ws_bytes = ws_bytes;
+  g->st = static_cast<cudaStream_t>(stream);
+  g->slots.resize(max_links);
+  g->free_list.push_back(Region{g->F.total, (ws_bytes - g->F.total) & ~(kAlign - 1)});
+  int rc = SRLA_OK;
+  int dev = 0, occ_scan = 0, occ_sort = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    rc = SRLA_E_CUDA;
+  if (rc == SRLA_OK &&
+      (cudaStreamCreateWithFlags(&g->st_copy, cudaStreamNonBlocking) != cudaSuccess ||
+       cudaStreamCreateWithFlags(&g->st_side, cudaStreamNonBlocking) != cudaSuccess ||
+       cudaEventCreateWithFlags(&g->ev[0], cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&g->ev[1], cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&g->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+       cudaEventCreateWithFlags(&g->ev_join, cudaEventDisableTiming) != cudaSuccess))
+    rc = SRLA_E_CUDA;
+  const size_t tbytes = sizeof(TaskHeader) + sizeof(ScanTask) * g->F.max_tasks;
+  const size_t sbytes = sizeof(srla_slice_stats) * max_links, obytes = sizeof(uint32_t) * (max_links + 1);
+  if (rc == SRLA_OK && cudaHostAlloc(&g->h_pinned, 2 * (tbytes + sbytes + obytes) + 64, cudaHostAllocDefault) != cudaSuccess)
+    rc = SRLA_E_NOMEM;
+  if (rc == SRLA_OK) {
+    char* h = static_cast<char*>(g->h_pinned);
+    for (int q = 0; q < 2; q++) {
+      g->h_tasks[q] = reinterpret_cast<TaskHeader*>(h);
+      h += tbytes;
+      g->h_stats[q] = reinterpret_cast<srla_slice_stats*>(h);
+      h += sbytes;
+      g->h_off[q] = reinterpret_cast<uint32_t*>(h);
+      h += obytes;
+      std::memset(g->h_tasks[q], 0, tbytes);
+    }
+    cudaFuncSetAttribute(kg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmallSmem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_scan, kg_scan<kGroupScanThreads>, kGroupScanThreads, 0) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_sort, kg_sort, kSortThreads, kSortSmallSmem) != cudaSuccess ||
+        occ_sort < 1)
+      rc = SRLA_E_CUDA;
+    g->scan_grid = g->sms * std::max(1, occ_scan);
+    g->sort_grid = g->sms * occ_sort;
+  }
+  if (rc == SRLA_OK) rc = gerr(cudaMemsetAsync(g->ws, 0, g->F.total, g->st));
+  if (rc == SRLA_OK) {
+    GroupCtl c{};
+    c.rep_cap = max_report;
+    rc = gerr(cudaMemcpyAsync(g->gctl(), &c, sizeof(c), cudaMemcpyHostToDevice, g->st));
+  }
+  if (rc == SRLA_OK) rc = rebuild_work(g);
+  if (rc == SRLA_OK) rc = capture(g);
+  if (rc != SRLA_OK) {
+    srla_group_destroy(g);
+    return rc;
+  }
+  *out = g;
+  return SRLA_OK;
+}
+
+int srla_group_attach(srla_group_t* g, const srla_params* p, uint32_t* link) {
+  if (!g || !link || check(p) != SRLA_OK) return SRLA_E_INVAL;
+  if (!g->pending.empty()) return SRLA_E_ORDER;
+  uint32_t l = 0;
+  while (l < g->max_links && g->slots[l].active) l++;
+  if (l == g->max_links) return SRLA_E_CAPACITY;
+  // the slot's previous occupant may still be referenced by an enqueued slice end
+  for (int q = 0; q < 2; q++) G_TRY(cudaEventSynchronize(g->ev[q]));
+  const srla_params lp = link_params(*p);
+  const Layout L = layout_of(&lp);
+  size_t off = 0;
+  if (!arena_alloc(g, L.total, &off)) return SRLA_E_NOMEM;
+  Slot& s = g->slots[l];
+  s = Slot{};
+  s.active = true;
+  s.p = lp;
+  s.L = L;
+  s.off = off;
+  s.bytes = L.total;
+  s.T = p->start_slice;
+  s.attached_at = g->G;
+  char* base = g->ws + off;
+  G_TRY(cudaMemsetAsync(base, 0, L.total, g->st));
+  if (L.pairs) G_TRY(cudaMemsetAsync(base + L.ptab, 0xFF, ((size_t)L.pmask + 1) * 8, g->st));
+  Ctl c{};
+  c.T = s.T;
+  c.tm = (uint32_t)(s.T % ((1u << lp.z) - 1u));
+  c.w_star = lp.gl + 1;
+  c.pair_mode = 1;
+  G_TRY(cudaMemcpyAsync(base + L.ctl, &c, sizeof(c), cudaMemcpyHostToDevice, g->st));
+  const LinkDesc D = make_desc(g, s);
+  G_TRY(cudaMemcpyAsync(g->descs() + l, &D, sizeof(D), cudaMemcpyHostToDevice, g->st));
+  const int rc = rebuild_work(g);
+  if (rc != SRLA_OK) {
+    s.active = false;
+    arena_free(g, off, L.total);
+    return rc;
+  }
+  *link = l;
+  return SRLA_OK;
+}
+
+int srla_group_detach(srla_group_t* g, uint32_t link) {
+  if (!g || link >= g->max_links || !g->slots[link].active) return SRLA_E_INVAL;
+  if (!g->pending.empty()) return SRLA_E_ORDER;
+  for (int q = 0; q < 2; q++) G_TRY(cudaEventSynchronize(g->ev[q]));
+  Slot& s = g->slots[link];
+  s.active = false;
+  LinkDesc D{};
+  G_TRY(cudaMemcpyAsync(g->descs() + link, &D, sizeof(D), cudaMemcpyHostToDevice, g->st));
+  arena_free(g, s.off, s.bytes);
+  return rebuild_work(g);
+}
+
+int srla_group_push(srla_group_t* g, uint32_t link, const uint32_t* pairs, uint64_t n_pairs, int on_device) {
+  if (!g || link >= g->max_links || !g->slots[link].active || (!pairs && n_pairs)) return SRLA_E_INVAL;
+  if (n_pairs == 0) return SRLA_OK;
+  const int q = (int)(g->G & 1);
+  const uint32_t* src = pairs;
+  if (!on_device) {
+    if (g->stage_used + n_pairs > g->max_host_pkts) return SRLA_E_CAPACITY;
+    if (!g->stage_waited) {
+      const int r = wait_parity(g, q);
+      if (r != SRLA_OK) return r;
+      g->stage_waited = true;
+    }
+    uint32_t* dst = reinterpret_cast<uint32_t*>(g->ws + g->F.stage[q]) + 2 * g->stage_used;
+    G_TRY(cudaMemcpyAsync(dst, pairs, n_pairs * 8, cudaMemcpyHostToDevice, g->st));
+    src = dst;
+    g->stage_used += n_pairs;
+  }
+  const uint64_t ntask = (n_pairs + kTaskPkts - 1) / kTaskPkts;
+  if (g->pending.size() + ntask > g->F.max_tasks) return SRLA_E_CAPACITY;
+  for (uint64_t x = 0; x < n_pairs; x += kTaskPkts)
+    g->pending.push_back(ScanTask{reinterpret_cast<unsigned long long>(src + 2 * x),
+                                  (uint32_t)std::min<uint64_t>(kTaskPkts, n_pairs - x), link});
+  g->slots[link].pkts_open += n_pairs;
+  return SRLA_OK;
+}
+
+int srla_group_end_slice(srla_group_t* g, uint64_t* group_slice) {
+  if (!g) return SRLA_E_INVAL;
+  const int q = (int)(g->G & 1);
+  int r = wait_parity(g, q);
+  if (r != SRLA_OK) return r;
+  // tasks longest first, so the persistent scan blocks finish together
+  std::stable_sort(g->pending.begin(), g->pending.end(), [](const ScanTask& a, const ScanTask& b) { return a.n > b.n; });
+  g->h_tasks[q]->n_tasks = (unsigned)g->pending.size();
+  if (!g->pending.empty())
+    std::memcpy(reinterpret_cast<ScanTask*>(g->h_tasks[q] + 1), g->pending.data(), g->pending.size() * sizeof(ScanTask));
+  G_TRY(cudaGraphLaunch(g->graph[q], g->st));
+  g->launches += g->graph_launches;
+  G_TRY(cudaEventRecord(g->ev[q], g->st));
+  for (Slot& s : g->slots) {
+    if (!s.active) continue;
+    s.pkts_slice[q] = s.pkts_open;
+    s.pkts_open = 0;
+    s.T++;
+  }
+  g->valid[q] = true;
+  g->G_of[q] = g->G;
+  if (group_slice) *group_slice = g->G;
+  g->G++;
+  g->pending.clear();
+  g->stage_used = 0;
+  g->stage_waited = false;
+  return SRLA_OK;
+}
+
+int srla_group_report_all(srla_group_t* g, uint64_t gs, srla_entry* out, size_t cap, size_t* n_out, uint32_t* offsets,
+                          srla_slice_stats* stats) {
+  if (!g || (cap && !out)) return SRLA_E_INVAL;
+  const int q = (int)(gs & 1);
+  if (!g->valid[q] || g->G_of[q] != gs) return SRLA_E_ORDER;
+  G_TRY(cudaEventSynchronize(g->ev[q]));
+  const uint32_t* off = g->h_off[q];
+  uint32_t n_links = 0;
+  for (uint32_t l = 0; l < g->max_links; l++)
+    if (g->slots[l].active) n_links = l + 1;
+  const size_t total = std::min<size_t>(off[n_links], g->max_report);
+  uint32_t ovf = 0;
+  for (uint32_t l = 0; l < g->max_links; l++) {
+    const bool live = l < n_links && slot_was_attached(g, l, gs);
+    if (offsets) offsets[l] = l < n_links ? std::min<uint32_t>(off[l], (uint32_t)total) : (uint32_t)total;
+    if (stats) {
+      if (live) {
+        stats[l] = g->h_stats[q][l];
+        stats[l].n_pkts = g->slots[l].pkts_slice[q];
+      } else {
+        std::memset(&stats[l], 0, sizeof(srla_slice_stats));
+      }
+    }
+    if (live) ovf |= g->h_stats[q][l].overflow;
+  }
+  if (offsets) offsets[g->max_links] = (uint32_t)total;
+  if (n_out) *n_out = total;
+  const size_t take = std::min(total, cap);
+  if (take) {
+    G_TRY(cudaMemcpyAsync(out, g->ws + g->F.grep[q], take * sizeof(srla_entry), cudaMemcpyDeviceToHost, g->st_copy));
+    G_TRY(cudaStreamSynchronize(g->st_copy));
+  }
+  if (ovf & 4u) return SRLA_E_TIMEOUT;
+  if (ovf || off[n_links] > g->max_report) return SRLA_E_CAPACITY;
+  if (cap < total) return SRLA_E_NOMEM;
+  return SRLA_OK;
+}
+
+int srla_group_report(srla_group_t* g, uint32_t link, uint64_t gs, srla_entry* out, size_t cap, size_t* n_out,
+                      srla_slice_stats* stats) {
+  if (!g || link >= g->max_links || (cap && !out)) return SRLA_E_INVAL;
+  const int q = (int)(gs & 1);
+  if (!g->valid[q] || g->G_of[q] != gs || !slot_was_attached(g, link, gs)) return SRLA_E_ORDER;
+  G_TRY(cudaEventSynchronize(g->ev[q]));
+  const uint32_t a = std::min<uint32_t>(g->h_off[q][link], g->max_report);
+  const uint32_t b = std::min<uint32_t>(g->h_off[q][link + 1], g->max_report);
+  srla_slice_stats st = g->h_stats[q][link];
+  st.n_pkts = g->slots[link].pkts_slice[q];
+  const size_t n = st.n_candidates;
+  if (n_out) *n_out = n;
+  if (stats) *stats = st;
+  const size_t have = b > a ? b - a : 0;
+  const size_t take = std::min(std::min(n, cap), have);
+  if (take) {
+    G_TRY(cudaMemcpyAsync(out, g->ws + g->F.grep[q] + (size_t)a * sizeof(srla_entry), take * sizeof(srla_entry),
+                          cudaMemcpyDeviceToHost, g->st_copy));
+    G_TRY(cudaStreamSynchronize(g->st_copy));
+  }
+  if (st.overflow & 4u) return SRLA_E_TIMEOUT;
+  if (st.overflow || have < n) return SRLA_E_CAPACITY;
+  if (cap < n) return SRLA_E_NOMEM;
+  return SRLA_OK;
+}
+
+int srla_group_sync(srla_group_t* g) {
+  if (!g) return SRLA_E_INVAL;
+  return gerr(cudaStreamSynchronize(g->st));
+}
+
+uint64_t srla_group_kernel_launches(const srla_group_t* g) { return g ? g->launches : 0; }
+
+void srla_group_destroy(srla_group_t* g) {
+  if (!g) return;
+  if (g->st) cudaStreamSynchronize(g->st);
+  for (int q = 0; q < 2; q++) {
+    if (g->graph[q]) cudaGraphExecDestroy(g->graph[q]);
+    if (g->ev[q]) cudaEventDestroy(g->ev[q]);
+  }
+  if (g->ev_fork) cudaEventDestroy(g->ev_fork);
+  if (g->ev_join) cudaEventDestroy(g->ev_join);
+  if (g->st_copy) cudaStreamDestroy(g->st_copy);
+  if (g->st_side) cudaStreamDestroy(g->st_side);
+  if (g->h_pinned) cudaFreeHost(g->h_pinned);
+  delete g;
+}
+
+}  // extern "C"

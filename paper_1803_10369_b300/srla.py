@@ -69,6 +69,19 @@ SIGNATURES = {
     "srla_destroy": (None, [_P]),
     "srla_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "srla_batch_report_static": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P, _P, ctypes.c_size_t, _P, _P]),
+    "srla_group_fixed_bytes": (ctypes.c_size_t, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32]),
+    "srla_group_link_bytes": (ctypes.c_size_t, [_P]),
+    "srla_group_create": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P,
+                                         ctypes.c_size_t, _P, _P]),
+    "srla_group_attach": (ctypes.c_int, [_P, _P, _P]),
+    "srla_group_detach": (ctypes.c_int, [_P, ctypes.c_uint32]),
+    "srla_group_push": (ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.c_uint64, ctypes.c_int]),
+    "srla_group_end_slice": (ctypes.c_int, [_P, _P]),
+    "srla_group_report_all": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_size_t, _P, _P, _P]),
+    "srla_group_report": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, ctypes.c_size_t, _P, _P]),
+    "srla_group_sync": (ctypes.c_int, [_P]),
+    "srla_group_kernel_launches": (ctypes.c_uint64, [_P]),
+    "srla_group_destroy": (None, [_P]),
 }
 
 STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
@@ -253,6 +266,132 @@ class Link:
     def close(self):
         if getattr(self, "_h", None):
             self.L.srla_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _stats_dict(st, u):
+    d = {f: getattr(st, f) for f, _ in srla_slice_stats._fields_ if f != "census"}
+    d["census"] = np.array(st.census[:u], dtype=np.uint64)
+    return d
+
+
+def _pairs_arg(pairs):
+    """(pointer, n, on_device, keep-alive object) of a batch of (n, 2) uint32 pairs."""
+    import torch
+
+    if isinstance(pairs, torch.Tensor):
+        if pairs.dtype not in (torch.int32, torch.uint32) or not pairs.is_contiguous():
+            raise ValueError("pairs must be a contiguous int32/uint32 tensor of shape (n, 2)")
+        return pairs.data_ptr(), pairs.numel() // 2, 1 if pairs.is_cuda else 0, pairs
+    arr = np.ascontiguousarray(pairs, dtype=np.uint32)
+    return arr.ctypes.data, arr.size // 2, 0, arr
+
+
+class Group:
+    """Many links advanced together: one CUDA graph launch scans and closes every link's slice.
+
+    The workspace is one torch tensor: a fixed part plus an arena for link regions
+    (``arena_bytes``).  Links attach and detach between slices."""
+
+    def __init__(self, max_links, max_pkts, arena_bytes, max_host_pkts=0, max_report=1 << 16, device="cuda",
+                 stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libsrla needs a CUDA device")
+        self.L = lib()
+        self.max_links, self.max_report = max_links, max_report
+        fixed = self.L.srla_group_fixed_bytes(max_links, max_pkts, max_host_pkts, max_report)
+        if fixed == 0:
+            raise SRLAError(E_INVAL, "srla_group_fixed_bytes")
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(fixed + int(arena_bytes), dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            h = ctypes.c_void_p()
+            _ck(self.L.srla_group_create(max_links, max_pkts, max_host_pkts, max_report,
+                                         ctypes.c_void_p(self.workspace.data_ptr()), self.workspace.numel(),
+                                         ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+                "srla_group_create")
+        self._h = h
+        self.params = {}
+        self._keep = []
+        self._out = np.empty(max_report, dtype=ENTRY_DTYPE)
+
+    @staticmethod
+    def link_bytes(params: srla_params) -> int:
+        return lib().srla_group_link_bytes(ctypes.byref(params))
+
+    def attach(self, params: srla_params) -> int:
+        link = ctypes.c_uint32()
+        _ck(self.L.srla_group_attach(self._h, ctypes.byref(params), ctypes.byref(link)), "srla_group_attach")
+        self.params[link.value] = params
+        return link.value
+
+    def detach(self, link: int):
+        _ck(self.L.srla_group_detach(self._h, link), "srla_group_detach")
+        self.params.pop(link, None)
+
+    def push(self, link: int, pairs):
+        ptr, n, on_dev, keep = _pairs_arg(pairs)
+        self._keep.append(keep)
+        _ck(self.L.srla_group_push(self._h, link, ctypes.c_void_p(ptr), n, on_dev), "srla_group_push")
+
+    def end_slice(self) -> int:
+        gs = ctypes.c_uint64()
+        _ck(self.L.srla_group_end_slice(self._h, ctypes.byref(gs)), "srla_group_end_slice")
+        self._last = gs.value
+        self._keep = self._keep[-4096:]
+        return gs.value
+
+    def report_all(self, gs=None, allow_overflow=False):
+        """{link: report dict} for every link attached at group slice gs."""
+        if gs is None:
+            gs = self._last
+        n = ctypes.c_size_t()
+        offs = (ctypes.c_uint32 * (self.max_links + 1))()
+        stats = (srla_slice_stats * self.max_links)()
+        rc = self.L.srla_group_report_all(self._h, gs, ctypes.c_void_p(self._out.ctypes.data), self.max_report,
+                                          ctypes.byref(n), offs, stats)
+        if rc != OK and not (allow_overflow and rc == E_CAPACITY):
+            raise SRLAError(rc, "srla_group_report_all")
+        out = {}
+        for link, p in self.params.items():
+            e = self._out[offs[link]:offs[link + 1]]
+            out[link] = {"aip": e["aip"].copy(), "w": e["w"].copy(), "est": e["est"].copy(),
+                         "flags": e["flags"].copy(), "stats": _stats_dict(stats[link], p.u), "rc": rc}
+        return out
+
+    def report(self, link: int, gs=None, allow_overflow=False):
+        if gs is None:
+            gs = self._last
+        p = self.params[link]
+        out = np.empty(p.max_candidates, dtype=ENTRY_DTYPE)
+        n = ctypes.c_size_t()
+        st = srla_slice_stats()
+        rc = self.L.srla_group_report(self._h, link, gs, ctypes.c_void_p(out.ctypes.data), p.max_candidates,
+                                      ctypes.byref(n), ctypes.byref(st))
+        if rc != OK and not (allow_overflow and rc == E_CAPACITY):
+            raise SRLAError(rc, "srla_group_report")
+        e = out[:min(n.value, p.max_candidates)]
+        return {"aip": e["aip"].copy(), "w": e["w"].copy(), "est": e["est"].copy(), "flags": e["flags"].copy(),
+                "stats": _stats_dict(st, p.u), "rc": rc}
+
+    def sync(self):
+        _ck(self.L.srla_group_sync(self._h), "srla_group_sync")
+
+    def kernel_launches(self) -> int:
+        return self.L.srla_group_kernel_launches(self._h)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self.L.srla_group_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -371,10 +371,120 @@ def bench_srla(args):
         torch.distributed.destroy_process_group()
 
 
+def _pctl(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))]
+
+
+def bench_batched(args):
+    """64 independent links of uneven rates: one group (one graph launch per slice for all
+    links) against the plain per-link loop (one handle per link, its own scan and slice end),
+    on the same GPU and the same device-resident packets."""
+    import torch
+
+    import synth
+    from paper_1803_10369_b300 import srla
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    links = synth.batched_links(64)
+    params = []
+    for w, plog in links:
+        ha, hb = synth.hash_coefficients(w.hash_seed, w.u + 3)
+        params.append(srla.params_for(w, ha, hb, pair_slots_log2=plog))
+    n_distinct = 4
+    batches = [[synth.generate_slice(w.traffic, s, device=dev) for s in range(n_distinct)] for w, _ in links]
+    pkts_slice = sum(int(b[0].shape[0]) for b in batches)
+    prefill, W, K = (args.prefill if args.prefill >= 0 else 24), args.warmup, args.steps
+    stream = torch.cuda.Stream(dev)
+
+    # ---- the group
+    arena = sum(srla.Group.link_bytes(p) for p in params) + (64 << 20)
+    g = srla.Group(max_links=len(params), max_pkts=2 * pkts_slice, arena_bytes=arena, max_report=1 << 20,
+                   device=dev, stream=stream)
+    ids = [g.attach(p) for p in params]
+
+    def group_slice(s):
+        for i, l in enumerate(ids):
+            g.push(l, batches[i][s % n_distinct])
+        return g.end_slice()
+
+    with torch.cuda.stream(stream):
+        for s in range(prefill + W):
+            g.report_all(group_slice(s))
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        launches0 = g.kernel_launches()
+        e0.record(stream)
+        pending = None
+        for s in range(K):
+            gs = group_slice(prefill + W + s)
+            if pending is not None:
+                g.report_all(pending)
+            pending = gs
+        e1.record(stream)
+        g.report_all(pending)
+        torch.cuda.synchronize(dev)
+        group_ms = e0.elapsed_time(e1) / K
+        group_launches = (g.kernel_launches() - launches0) / K
+        lat_g = []
+        for s in range(max(K, 32)):
+            for i, l in enumerate(ids):
+                g.push(l, batches[i][s % n_distinct])
+            t0 = time.perf_counter()
+            g.report_all(g.end_slice())
+            lat_g.append((time.perf_counter() - t0) * 1e3)
+    g.close()
+
+    # ---- the plain per-link loop
+    solo = [srla.Link(p, device=dev, stream=stream) for p in params]
+    with torch.cuda.stream(stream):
+        def loop_slice(s, lat=None):
+            ends = []
+            for i, L in enumerate(solo):
+                L.push(batches[i][s % n_distinct])
+                ends.append((time.perf_counter(), L.end_slice()))
+            for i, L in enumerate(solo):
+                L.report(ends[i][1])
+                if lat is not None:
+                    lat.append((time.perf_counter() - ends[i][0]) * 1e3)
+
+        for s in range(prefill + W):
+            loop_slice(s)
+        torch.cuda.synchronize(dev)
+        e0.record(stream)
+        for s in range(K):
+            loop_slice(prefill + W + s)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        loop_ms = e0.elapsed_time(e1) / K
+        lat_l = []
+        for s in range(max(K, 32)):
+            loop_slice(s, lat_l)
+    for L in solo:
+        L.close()
+    line = {
+        "metric": METRIC, "value": round(pkts_slice / (group_ms * 1e-3) / 1e6, 3), "unit": "Mpkts/s", "n_gpus": 1,
+        "steps": K, "warmup": W, "ms_per_step": round(group_ms, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8/u16", "data": "synthetic",
+        "config": {"workload": "batched-64-links-rates-1e4-5e6-k16-300", "links": len(params),
+                   "pkts_per_slice": pkts_slice, "prefill_slices": prefill},
+        "latency_ms": {"p50": round(_pctl(lat_g, 0.5), 4), "p99": round(_pctl(lat_g, 0.99), 4),
+                       "what": "end_slice call to every link's report on the host (scan included)"},
+        "gpu_launches_per_slice": group_launches,
+        "per_link_loop": {"value": round(pkts_slice / (loop_ms * 1e-3) / 1e6, 3), "ms_per_step": round(loop_ms, 4),
+                          "latency_ms": {"p50": round(_pctl(lat_l, 0.5), 4), "p99": round(_pctl(lat_l, 0.99), 4),
+                                         "what": "a link's end_slice call to its report on the host"}},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         bench_reference(args)
+    elif args.workload == "batched":
+        bench_batched(args)
     else:
         bench_srla(args)
 

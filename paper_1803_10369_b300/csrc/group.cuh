@@ -226,8 +226,27 @@ __device__ __forceinline__ void group_sweep_chunk(const SweepChunk& c, const Lin
 
 // Census and ageing of every link's recorders, and clearing of the pair tables.  The
 // post-close variant ages the links with k = 2^z - 1 after their slice was closed.
+// Index of the link whose half-open range [off[l], off[l+1]) holds item i (off ascending).
+__device__ __forceinline__ unsigned link_of(const uint32_t* off, unsigned nl, uint32_t i) {
+  unsigned lo = 0, hi = nl;  // off[lo] <= i < off[hi]
+  while (hi - lo > 1) {
+    const unsigned mid = (lo + hi) >> 1;
+    if (off[mid] <= i) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(256) kg_sweep(const LinkDesc* __restrict__ descs, const GroupCtl* __restrict__ gctl,
-                                                int post) {
+                                                int post, uint32_t* __restrict__ filt_off) {
+  if (!post && blockIdx.x == 0 && threadIdx.x == 0) {  // host pairs per link for the flat filter
+    uint32_t run = 0;
+    for (unsigned l = 0; l < gctl->n_links; l++) {
+      filt_off[l] = run;
+      const LinkDesc& D = descs[l];
+      if (D.active) run += (min(D.ctl->n_sampled, D.umax) + 1u) / 2u;
+    }
+    filt_off[gctl->n_links] = run;
+  }
   const unsigned n = post ? gctl->n_post : gctl->n_chunks;
   const SweepChunk* __restrict__ chunks = post ? gctl->post : gctl->chunks;
   for (unsigned ci = blockIdx.x; ci < n; ci += gridDim.x) {
@@ -271,8 +290,9 @@ __global__ void kg_lut(const LinkDesc* __restrict__ descs, const GroupCtl* __res
 
 // ------------------------------------------------------------- new candidates
 
+// One pair of sampled hosts of one link (the second may be absent).
 template <typename CellT>
-__device__ __forceinline__ void group_filter_link(const LinkDesc& D, uint32_t gw, uint32_t nw, int lane) {
+__device__ __forceinline__ void group_filter_pair(const LinkDesc& D, uint32_t q, int lane) {
   Ctl* ctl = D.ctl;
   const unsigned long long T = ctl->T;
   const int par = (int)(T & 1);
@@ -280,37 +300,39 @@ __device__ __forceinline__ void group_filter_link(const LinkDesc& D, uint32_t gw
   const uint32_t n = min(ctl->n_sampled, D.umax);
   const Win win = make_win<CellT>(ctl->tm, D.geo.P, D.geo.k);
   const CellT* re = static_cast<const CellT*>(D.re);
-  for (uint32_t idx = 2 * gw; idx < n; idx += 2 * nw) {
-    const bool two = idx + 1 < n;
-    const uint32_t aip0 = D.ulist[idx];
-    const uint32_t aip1 = two ? D.ulist[idx + 1] : aip0;
-    const bool mine = (uint32_t)lane < D.geo.u;
-    const uint32_t col0 = mine ? hash61(D.coef.a[lane], D.coef.b[lane], aip0) & D.geo.vmask : 0u;
-    const uint32_t col1 = mine ? hash61(D.coef.a[lane], D.coef.b[lane], aip1) & D.geo.vmask : 0u;
-    uint32_t cnt0, cnt1;
-    union_count_atleast2<CellT>(re, D.geo.v, D.geo.g, D.geo.u, col0, col1, win, D.geo.rho_g, lane, cnt0, cnt1);
-    if (lane == 0) {
-      filter_admit(ctl, D.ctab[par], D.cflags[par], D.cmask, D.clist[par], D.cmax, par, tag, aip0,
-                   cnt0 >= D.geo.rho_g);
-      if (two)
-        filter_admit(ctl, D.ctab[par], D.cflags[par], D.cmask, D.clist[par], D.cmax, par, tag, aip1,
-                     cnt1 >= D.geo.rho_g);
-    }
+  const uint32_t idx = 2 * q;
+  const bool two = idx + 1 < n;
+  const uint32_t aip0 = D.ulist[idx];
+  const uint32_t aip1 = two ? D.ulist[idx + 1] : aip0;
+  const bool mine = (uint32_t)lane < D.geo.u;
+  const uint32_t col0 = mine ? hash61(D.coef.a[lane], D.coef.b[lane], aip0) & D.geo.vmask : 0u;
+  const uint32_t col1 = mine ? hash61(D.coef.a[lane], D.coef.b[lane], aip1) & D.geo.vmask : 0u;
+  uint32_t cnt0, cnt1;
+  union_count_atleast2<CellT>(re, D.geo.v, D.geo.g, D.geo.u, col0, col1, win, D.geo.rho_g, lane, cnt0, cnt1);
+  if (lane == 0) {
+    filter_admit(ctl, D.ctab[par], D.cflags[par], D.cmask, D.clist[par], D.cmax, par, tag, aip0, cnt0 >= D.geo.rho_g);
+    if (two)
+      filter_admit(ctl, D.ctab[par], D.cflags[par], D.cmask, D.clist[par], D.cmax, par, tag, aip1,
+                   cnt1 >= D.geo.rho_g);
   }
 }
 
+// Every link's sampled hosts in one flat range of host pairs (prefixed by the sweep).
 __global__ void __launch_bounds__(256, 2) kg_filter(const LinkDesc* __restrict__ descs,
-                                                    const GroupCtl* __restrict__ gctl) {
+                                                    const GroupCtl* __restrict__ gctl,
+                                                    const uint32_t* __restrict__ filt_off) {
   const int lane = threadIdx.x & 31;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (unsigned l = 0; l < gctl->n_links; l++) {
+  const unsigned nl = gctl->n_links;
+  const uint32_t total = filt_off[nl];
+  for (uint32_t i = gw; i < total; i += nw) {
+    const unsigned l = link_of(filt_off, nl, i);
     const LinkDesc& D = descs[l];
-    if (!D.active) continue;
     if (D.cell_bytes == 1)
-      group_filter_link<uint8_t>(D, gw, nw, lane);
+      group_filter_pair<uint8_t>(D, i - filt_off[l], lane);
     else
-      group_filter_link<uint16_t>(D, gw, nw, lane);
+      group_filter_pair<uint16_t>(D, i - filt_off[l], lane);
   }
 }
 
@@ -398,46 +420,43 @@ __global__ void __launch_bounds__(kSortThreads) kg_sort(const LinkDesc* __restri
 
 __device__ __forceinline__ bool grep_off_ok(uint32_t idx, uint32_t cap) { return idx < cap; }
 
+// One candidate of one link: union SLE weight, Eq. 9 lookup, report entry, carry test.
 template <typename CellT>
-__device__ __forceinline__ void group_estimate_link(const LinkDesc& D, uint32_t gw, uint32_t nw, int lane,
-                                                    srla_entry* grep, uint32_t rep_cap, GroupCtl* gctl) {
+__device__ __forceinline__ void group_estimate_one(const LinkDesc& D, uint32_t idx, int lane, srla_entry* grep,
+                                                   uint32_t rep_cap, GroupCtl* gctl) {
   Ctl* ctl = D.ctl;
   const unsigned long long T = ctl->T;
   const int par = (int)(T & 1);
   const uint32_t tag = slice_tag(T), ntag = slice_tag(T + 1);
-  const uint32_t n = min(ctl->cat_count[par], D.cmax);
   const Win win = make_win<CellT>(ctl->tm, D.geo.P, D.geo.k);
   const Win win_post = make_win<CellT>(ctl->tm, D.geo.P, D.geo.k - 1u);
   const CellT* re = static_cast<const CellT*>(D.re);
   const CellT* le = static_cast<const CellT*>(D.le);
-  const uint32_t* clist = D.clist[par];
-  for (uint32_t idx = gw; idx < n; idx += nw) {
-    const uint32_t aip = clist[idx];
-    const uint32_t mycol = (uint32_t)lane < D.geo.u ? hash61(D.coef.a[lane], D.coef.b[lane], aip) & D.geo.vmask : 0u;
-    const uint32_t w = union_count<CellT>(le, D.geo.v, D.geo.gl, D.geo.u, mycol, win, lane);
-    const uint32_t cw = union_count<CellT>(re, D.geo.v, D.geo.g, D.geo.u, mycol, win_post, lane);
-    if (lane == 0) {
-      const uint32_t s = set_find(D.ctab[par], D.cmask, tag, aip);
-      const uint32_t origin = (s != 0xFFFFFFFFu) ? D.cflags[par][s] : 0u;
-      srla_entry e;
-      e.aip = aip;
-      e.w = w;
-      e.est = D.lut_est[w];
-      e.flags = origin | D.lut_flags[w];
-      if (grep_off_ok(idx, rep_cap)) grep[idx] = e; else atomicOr(&gctl->overflow, 2u);
-      if (cw >= D.geo.rho_g) {
-        uint32_t slot;
-        const int r = set_insert(D.ctab[par ^ 1], D.cmask, ntag, aip, &slot);
-        if (r == 1) {
-          D.cflags[par ^ 1][slot] = SRLA_CARRIED;
-          const unsigned at = atomicAdd(&ctl->cat_count[par ^ 1], 1u);
-          if (at < D.cmax)
-            D.clist[par ^ 1][at] = aip;
-          else
-            atomicOr(&ctl->overflow_next, 2u);
-        } else if (r < 0) {
+  const uint32_t aip = D.clist[par][idx];
+  const uint32_t mycol = (uint32_t)lane < D.geo.u ? hash61(D.coef.a[lane], D.coef.b[lane], aip) & D.geo.vmask : 0u;
+  const uint32_t w = union_count<CellT>(le, D.geo.v, D.geo.gl, D.geo.u, mycol, win, lane);
+  const uint32_t cw = union_count<CellT>(re, D.geo.v, D.geo.g, D.geo.u, mycol, win_post, lane);
+  if (lane == 0) {
+    const uint32_t s = set_find(D.ctab[par], D.cmask, tag, aip);
+    const uint32_t origin = (s != 0xFFFFFFFFu) ? D.cflags[par][s] : 0u;
+    srla_entry e;
+    e.aip = aip;
+    e.w = w;
+    e.est = D.lut_est[w];
+    e.flags = origin | D.lut_flags[w];
+    if (grep_off_ok(idx, rep_cap)) grep[idx] = e; else atomicOr(&gctl->overflow, 2u);
+    if (cw >= D.geo.rho_g) {
+      uint32_t slot;
+      const int r = set_insert(D.ctab[par ^ 1], D.cmask, ntag, aip, &slot);
+      if (r == 1) {
+        D.cflags[par ^ 1][slot] = SRLA_CARRIED;
+        const unsigned at = atomicAdd(&ctl->cat_count[par ^ 1], 1u);
+        if (at < D.cmax)
+          D.clist[par ^ 1][at] = aip;
+        else
           atomicOr(&ctl->overflow_next, 2u);
-        }
+      } else if (r < 0) {
+        atomicOr(&ctl->overflow_next, 2u);
       }
     }
   }
@@ -453,15 +472,16 @@ __global__ void __launch_bounds__(256) kg_estimate(const LinkDesc* __restrict__ 
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const unsigned nl = gctl->n_links;
-  for (unsigned l = 0; l < nl; l++) {
+  const uint32_t total = rep_off[nl];  // every link's candidates in one flat range
+  for (uint32_t i = gw; i < total; i += nw) {
+    const unsigned l = link_of(rep_off, nl, i);
     const LinkDesc& D = descs[l];
-    if (!D.active) continue;
     const uint32_t off = rep_off[l];
     const uint32_t cap = gctl->rep_cap > off ? gctl->rep_cap - off : 0u;
     if (D.cell_bytes == 1)
-      group_estimate_link<uint8_t>(D, gw, nw, lane, grep + off, cap, gctl);
+      group_estimate_one<uint8_t>(D, i - off, lane, grep + off, cap, gctl);
     else
-      group_estimate_link<uint16_t>(D, gw, nw, lane, grep + off, cap, gctl);
+      group_estimate_one<uint16_t>(D, i - off, lane, grep + off, cap, gctl);
   }
   __syncthreads();
   if (threadIdx.x == 0) {

@@ -37,7 +37,7 @@ uint64_t max_tasks_for(uint32_t max_links, uint64_t max_pkts) {
 }
 
 struct Fixed {
-  size_t gctl, descs, tasks, gstats[2], rep_off[2], grep[2], stage[2], total;
+  size_t gctl, descs, tasks, filt_off, gstats[2], rep_off[2], grep[2], stage[2], total;
   uint64_t max_tasks;
 };
 
@@ -53,6 +53,7 @@ Fixed fixed_layout(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_pkts
   F.gctl = take(sizeof(GroupCtl));
   F.descs = take(sizeof(LinkDesc) * max_links);
   F.tasks = take(sizeof(TaskHeader) + sizeof(ScanTask) * F.max_tasks);
+  F.filt_off = take(sizeof(uint32_t) * (max_links + 1));
   for (int q = 0; q < 2; q++) {
     F.gstats[q] = take(sizeof(srla_slice_stats) * max_links);
     F.rep_off[q] = take(sizeof(uint32_t) * (max_links + 1));
@@ -256,12 +257,13 @@ int enqueue_slice(srla_group_t* g, int q) {
   g->launches += 6;  // scan, sweep, lut, filter, sort, estimate, (post sweep below)
   kg_scan<kGroupScanThreads><<<g->scan_grid, kGroupScanThreads, 0, g->st>>>(
       descs, reinterpret_cast<const TaskHeader*>(g->ws + F.tasks), gctl);
-  kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 0);
+  uint32_t* filt_off = reinterpret_cast<uint32_t*>(g->ws + F.filt_off);
+  kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 0, filt_off);
   G_TRY(cudaEventRecord(g->ev_fork, g->st));
   G_TRY(cudaStreamWaitEvent(g->st_side, g->ev_fork, 0));
   kg_lut<<<std::max(1, std::min<int>((int)g->max_links, g->sms * 4)), 256, 0, g->st_side>>>(descs, gctl);
   G_TRY(cudaEventRecord(g->ev_join, g->st_side));
-  kg_filter<<<g->sms * 4, 256, 0, g->st>>>(descs, gctl);
+  kg_filter<<<g->sms * 4, 256, 0, g->st>>>(descs, gctl, filt_off);
   uint32_t* rep_off = reinterpret_cast<uint32_t*>(g->ws + F.rep_off[q]);
   void* args[] = {&descs, &gctl, &rep_off};
   G_TRY(cudaLaunchCooperativeKernel((const void*)kg_sort, dim3(g->sort_grid), dim3(kSortThreads), args,
@@ -270,7 +272,7 @@ int enqueue_slice(srla_group_t* g, int q) {
   kg_estimate<<<g->sms * 2, 256, 0, g->st>>>(descs, gctl, reinterpret_cast<srla_slice_stats*>(g->ws + F.gstats[q]),
                                              rep_off, reinterpret_cast<srla_entry*>(g->ws + F.grep[q]));
   g->launches += 1;
-  kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 1);
+  kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 1, filt_off);
   G_TRY(cudaGetLastError());
   G_TRY(cudaMemcpyAsync(g->h_stats[q], g->ws + F.gstats[q], sizeof(srla_slice_stats) * g->max_links,
                         cudaMemcpyDeviceToHost, g->st));

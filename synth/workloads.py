@@ -8,6 +8,9 @@ threshold ``theta`` (Definition 2).  ``gl`` is the per-row SLE size divided by `
 from __future__ import annotations
 
 import dataclasses
+import math
+
+import numpy as np
 
 from .traces import TrafficSpec
 
@@ -87,3 +90,33 @@ WORKLOADS = {"tiny": TINY, "paper": PAPER, "longwin": LONGWIN}
 
 def workload(name: str) -> Workload:
     return WORKLOADS[name]
+
+
+def batched_links(n_links: int = 64, seed: int = 4):
+    """Many independent links of uneven rates (one estimator array each).
+
+    Rates are log-uniform in [10^4, 5*10^6] packets per slice, windows log-uniform in
+    [16, 300] slices, 8- or 16-bit recorders (8-bit only where the window fits), and the SLE
+    is scaled to the rate (2^16 .. 2^22 cells per row, g' = 256).  Returns a list of
+    (Workload, pair_slots_log2) with the per-slice pair table sized to the rate.
+    """
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 0xBA7C])))
+    out = []
+    for i in range(n_links):
+        rate = int(math.exp(rng.uniform(math.log(1e4), math.log(5e6))))
+        k = int(round(math.exp(rng.uniform(math.log(16), math.log(300)))))
+        one_byte = k <= 255 and rng.random() < 0.5
+        cells = 1 << int(np.clip(round(math.log2(rate)), 16, 22))
+        gl = 256
+        traffic = TrafficSpec(
+            seed=1000 + i, pkts_per_slice=rate, n_src=int(np.clip(rate // 5, 1 << 10, 1 << 20)), zipf_s=1.2,
+            dst_model="pool", pool_alpha=1.5, pool_max=128,
+            n_planted=max(1, rate // 20000), planted_card=(1 << 10, 1 << 16), planted_card_dist="loguniform",
+            planted_spread=k, churn_frac=0.3, churn_run=(max(4, k // 4), k))
+        w = Workload(
+            name=f"link{i}-r{rate}-k{k}", u=8, v=cells // gl, g=128, gl=gl, dr_bytes=1 if one_byte else 2,
+            z=8 if one_byte else 16, k=k, theta=1024, n_slices=16, traffic=traffic, hash_seed=100 + i,
+            max_sampled=1 << int(np.clip(math.ceil(math.log2(max(rate, 1) / 4)), 12, 20)),
+            max_candidates=1 << 14)
+        out.append((w, int(np.clip(round(math.log2(rate / 2)), 12, 21))))
+    return out

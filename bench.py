@@ -411,6 +411,12 @@ def bench_batched(args):
 
     with torch.cuda.stream(stream):
         for s in range(prefill + W):
+            if s == prefill // 2:  # autotune the scan launch shape on a live slice
+                for i, l in enumerate(ids):
+                    g.push(l, batches[i][s % n_distinct])
+                tuned = g.autotune(reps=3)
+                g.report_all(g.end_slice())
+                continue
             g.report_all(group_slice(s))
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -472,6 +478,7 @@ def bench_batched(args):
         "latency_ms": {"p50": round(_pctl(lat_g, 0.5), 4), "p99": round(_pctl(lat_g, 0.99), 4),
                        "what": "end_slice call to every link's report on the host (scan included)"},
         "gpu_launches_per_slice": group_launches,
+        "scan_autotune": {"block_threads": tuned[0], "packets_per_task": tuned[1]},
         "per_link_loop": {"value": round(pkts_slice / (loop_ms * 1e-3) / 1e6, 3), "ms_per_step": round(loop_ms, 4),
                           "latency_ms": {"p50": round(_pctl(lat_l, 0.5), 4), "p99": round(_pctl(lat_l, 0.99), 4),
                                          "what": "a link's end_slice call to its report on the host"}},

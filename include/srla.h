@@ -261,6 +261,13 @@ int srla_group_report_all(srla_group_t *g, uint64_t group_slice, srla_entry *out
 int srla_group_report(srla_group_t *g, uint32_t link, uint64_t group_slice, srla_entry *out,
                       size_t cap, size_t *n_out, srla_slice_stats *stats);
 
+/* Scan autotuner: with the open slice's packets pushed, time the group scan with block sizes
+ * 128/256/512 and tasks of 2^14/2^16/2^18 packets (reps runs each, on empty pair tables),
+ * keep the fastest (median) for all later slices, and leave the slice's results unchanged
+ * (the trial scans repeat the slice's own idempotent recorder stores).  Errors: ORDER when
+ * nothing was pushed, CUDA.                                                              */
+int srla_group_autotune(srla_group_t *g, int reps, uint32_t *best_threads, uint32_t *best_task_pkts);
+
 int srla_group_sync(srla_group_t *g);
 uint64_t srla_group_kernel_launches(const srla_group_t *g);
 void srla_group_destroy(srla_group_t *g);

@@ -17,7 +17,7 @@ using namespace srla::host;
 namespace {
 
 constexpr uint64_t kChunkVecs = 1ull << 14;  // 256 KB of recorders per sweep chunk
-constexpr int kGroupScanThreads = 256;
+constexpr int kGroupScanThreads = 256;       // default scan block size (the tuner may change it)
 
 int gerr(cudaError_t e) {
   if (e == cudaSuccess) return SRLA_OK;
@@ -31,9 +31,11 @@ int gerr(cudaError_t e) {
     if (_r != SRLA_OK) return _r;  \
   } while (0)
 
+constexpr uint32_t kMinTaskPkts = 1u << 14;  // the smallest task size the tuner tries
+
 uint64_t max_tasks_for(uint32_t max_links, uint64_t max_pkts) {
   // every push may leave one partial task behind
-  return max_pkts / kTaskPkts + 8ull * max_links + 64;
+  return max_pkts / kMinTaskPkts + 8ull * max_links + 64;
 }
 
 struct Fixed {
@@ -109,9 +111,19 @@ struct srla_group_s {
   bool valid[2] = {false, false};
   uint64_t G_of[2] = {0, 0};
   std::vector<ScanTask> pending;
+  uint64_t n_tasks_open = 0;
   uint64_t stage_used = 0;
   bool stage_waited = false;
   uint64_t launches = 0, graph_launches = 0;
+  int scan_threads = kGroupScanThreads;  // scan block size: 128, 256 or 512
+  uint32_t task_pkts = kTaskPkts;        // packets per scan task
+  int scan_grid_of[3] = {0, 0, 0};       // resident blocks of each block size
+  struct Segment {
+    uint32_t link;
+    const uint32_t* ptr;
+    uint64_t n;
+  };
+  std::vector<Segment> segments;  // the open slice's batches, before splitting into tasks
 
   GroupCtl* gctl() const { return reinterpret_cast<GroupCtl*>(ws + F.gctl); }
   LinkDesc* descs() const { return reinterpret_cast<LinkDesc*>(ws + F.descs); }
@@ -248,6 +260,31 @@ int rebuild_work(srla_group_t* g) {
 
 // ------------------------------------------------------------------ the slice end
 
+int scan_grid_index(int threads) { return threads == 128 ? 0 : threads == 256 ? 1 : 2; }
+
+void launch_group_scan(srla_group_t* g, int threads, const TaskHeader* tasks) {
+  const int grid = g->scan_grid_of[scan_grid_index(threads)];
+  if (threads == 128)
+    kg_scan<128><<<grid, 128, 0, g->st>>>(g->descs(), tasks, g->gctl());
+  else if (threads == 512)
+    kg_scan<512><<<grid, 512, 0, g->st>>>(g->descs(), tasks, g->gctl());
+  else
+    kg_scan<256><<<grid, 256, 0, g->st>>>(g->descs(), tasks, g->gctl());
+}
+
+// Split the open slice's batches into scan tasks of at most task_pkts packets.
+int split_tasks(srla_group_t* g) {
+  g->pending.clear();
+  for (const auto& sg : g->segments)
+    for (uint64_t x = 0; x < sg.n; x += g->task_pkts)
+      g->pending.push_back(ScanTask{reinterpret_cast<unsigned long long>(sg.ptr + 2 * x),
+                                    (uint32_t)std::min<uint64_t>(g->task_pkts, sg.n - x), sg.link});
+  if (g->pending.size() > g->F.max_tasks) return SRLA_E_CAPACITY;
+  // longest first, so that the persistent scan blocks finish together
+  std::stable_sort(g->pending.begin(), g->pending.end(), [](const ScanTask& a, const ScanTask& b) { return a.n > b.n; });
+  return SRLA_OK;
+}
+
 int enqueue_slice(srla_group_t* g, int q) {
   const Fixed& F = g->F;
   LinkDesc* descs = g->descs();
@@ -255,8 +292,7 @@ int enqueue_slice(srla_group_t* g, int q) {
   G_TRY(cudaMemcpyAsync(g->ws + F.tasks, g->h_tasks[q], sizeof(TaskHeader) + sizeof(ScanTask) * F.max_tasks,
                         cudaMemcpyHostToDevice, g->st));
   g->launches += 6;  // scan, sweep, lut, filter, sort, estimate, (post sweep below)
-  kg_scan<kGroupScanThreads><<<g->scan_grid, kGroupScanThreads, 0, g->st>>>(
-      descs, reinterpret_cast<const TaskHeader*>(g->ws + F.tasks), gctl);
+  launch_group_scan(g, g->scan_threads, reinterpret_cast<const TaskHeader*>(g->ws + F.tasks));
   uint32_t* filt_off = reinterpret_cast<uint32_t*>(g->ws + F.filt_off);
   kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 0, filt_off);
   G_TRY(cudaEventRecord(g->ev_fork, g->st));
@@ -378,12 +414,17 @@ int srla_group_create(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_p
       std::memset(g->h_tasks[q], 0, tbytes);
     }
     cudaFuncSetAttribute(kg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmallSmem);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_scan, kg_scan<kGroupScanThreads>, kGroupScanThreads, 0) !=
-            cudaSuccess ||
+    int o128 = 0, o512 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_scan, kg_scan<256>, 256, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o128, kg_scan<128>, 128, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o512, kg_scan<512>, 512, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_sort, kg_sort, kSortThreads, kSortSmallSmem) != cudaSuccess ||
         occ_sort < 1)
       rc = SRLA_E_CUDA;
-    g->scan_grid = g->sms * std::max(1, occ_scan);
+    g->scan_grid_of[0] = g->sms * std::max(1, o128);
+    g->scan_grid_of[1] = g->sms * std::max(1, occ_scan);
+    g->scan_grid_of[2] = g->sms * std::max(1, o512);
+    g->scan_grid = g->scan_grid_of[1];
     g->sort_grid = g->sms * occ_sort;
   }
   if (rc == SRLA_OK) rc = gerr(cudaMemsetAsync(g->ws, 0, g->F.total, g->st));
@@ -404,7 +445,7 @@ int srla_group_create(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_p
 
 int srla_group_attach(srla_group_t* g, const srla_params* p, uint32_t* link) {
   if (!g || !link || check(p) != SRLA_OK) return SRLA_E_INVAL;
-  if (!g->pending.empty()) return SRLA_E_ORDER;
+  if (!g->segments.empty()) return SRLA_E_ORDER;
   uint32_t l = 0;
   while (l < g->max_links && g->slots[l].active) l++;
   if (l == g->max_links) return SRLA_E_CAPACITY;
@@ -446,7 +487,7 @@ int srla_group_attach(srla_group_t* g, const srla_params* p, uint32_t* link) {
 
 int srla_group_detach(srla_group_t* g, uint32_t link) {
   if (!g || link >= g->max_links || !g->slots[link].active) return SRLA_E_INVAL;
-  if (!g->pending.empty()) return SRLA_E_ORDER;
+  if (!g->segments.empty()) return SRLA_E_ORDER;
   for (int q = 0; q < 2; q++) G_TRY(cudaEventSynchronize(g->ev[q]));
   Slot& s = g->slots[link];
   s.active = false;
@@ -473,11 +514,12 @@ int srla_group_push(srla_group_t* g, uint32_t link, const uint32_t* pairs, uint6
     src = dst;
     g->stage_used += n_pairs;
   }
-  const uint64_t ntask = (n_pairs + kTaskPkts - 1) / kTaskPkts;
-  if (g->pending.size() + ntask > g->F.max_tasks) return SRLA_E_CAPACITY;
-  for (uint64_t x = 0; x < n_pairs; x += kTaskPkts)
-    g->pending.push_back(ScanTask{reinterpret_cast<unsigned long long>(src + 2 * x),
-                                  (uint32_t)std::min<uint64_t>(kTaskPkts, n_pairs - x), link});
+  g->n_tasks_open += (n_pairs + g->task_pkts - 1) / g->task_pkts;
+  if (g->n_tasks_open > g->F.max_tasks) {
+    g->n_tasks_open -= (n_pairs + g->task_pkts - 1) / g->task_pkts;
+    return SRLA_E_CAPACITY;
+  }
+  g->segments.push_back(srla_group_s::Segment{link, src, n_pairs});
   g->slots[link].pkts_open += n_pairs;
   return SRLA_OK;
 }
@@ -487,8 +529,7 @@ int srla_group_end_slice(srla_group_t* g, uint64_t* group_slice) {
   const int q = (int)(g->G & 1);
   int r = wait_parity(g, q);
   if (r != SRLA_OK) return r;
-  // tasks longest first, so the persistent scan blocks finish together
-  std::stable_sort(g->pending.begin(), g->pending.end(), [](const ScanTask& a, const ScanTask& b) { return a.n > b.n; });
+  if ((r = split_tasks(g)) != SRLA_OK) return r;
   g->h_tasks[q]->n_tasks = (unsigned)g->pending.size();
   if (!g->pending.empty())
     std::memcpy(reinterpret_cast<ScanTask*>(g->h_tasks[q] + 1), g->pending.data(), g->pending.size() * sizeof(ScanTask));
@@ -506,6 +547,8 @@ int srla_group_end_slice(srla_group_t* g, uint64_t* group_slice) {
   if (group_slice) *group_slice = g->G;
   g->G++;
   g->pending.clear();
+  g->segments.clear();
+  g->n_tasks_open = 0;
   g->stage_used = 0;
   g->stage_waited = false;
   return SRLA_OK;
@@ -573,6 +616,79 @@ int srla_group_report(srla_group_t* g, uint32_t link, uint64_t gs, srla_entry* o
   if (st.overflow || have < n) return SRLA_E_CAPACITY;
   if (cap < n) return SRLA_E_NOMEM;
   return SRLA_OK;
+}
+
+int srla_group_autotune(srla_group_t* g, int reps, uint32_t* best_threads, uint32_t* best_task_pkts) {
+  if (!g || reps < 1) return SRLA_E_INVAL;
+  if (g->segments.empty()) return SRLA_E_ORDER;
+  const int threads[3] = {128, 256, 512};
+  const uint32_t tasks[3] = {1u << 14, 1u << 16, 1u << 18};
+  const int q = (int)(g->G & 1);
+  int r = wait_parity(g, q);
+  if (r != SRLA_OK) return r;
+  G_TRY(cudaStreamSynchronize(g->st));
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return SRLA_E_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return SRLA_E_CUDA;
+  }
+  std::vector<std::vector<float>> ms(9);
+  for (int rep = 0; rep < reps && r == SRLA_OK; rep++) {
+    for (int c = 0; c < 9 && r == SRLA_OK; c++) {
+      g->task_pkts = tasks[c % 3];
+      if ((r = split_tasks(g)) != SRLA_OK) break;
+      g->h_tasks[q]->n_tasks = (unsigned)g->pending.size();
+      std::memcpy(reinterpret_cast<ScanTask*>(g->h_tasks[q] + 1), g->pending.data(), g->pending.size() * sizeof(ScanTask));
+      // each trial starts from empty pair tables and a zero task counter; the recorder stores and
+      // sampled-host inserts repeat the slice's own, so the state after tuning is unchanged
+      for (const Slot& s : g->slots)
+        if (s.active && s.L.pairs)
+          r = r ? r : gerr(cudaMemsetAsync(g->ws + s.off + s.L.ptab, 0xFF, ((size_t)s.L.pmask + 1) * 8, g->st));
+      r = r ? r : gerr(cudaMemsetAsync(&g->gctl()->next_task, 0, sizeof(unsigned), g->st));
+      r = r ? r : gerr(cudaMemcpyAsync(g->ws + g->F.tasks, g->h_tasks[q], sizeof(TaskHeader) + sizeof(ScanTask) * g->pending.size(),
+                                       cudaMemcpyHostToDevice, g->st));
+      r = r ? r : gerr(cudaEventRecord(e0, g->st));
+      if (r == SRLA_OK) {
+        g->launches++;
+        launch_group_scan(g, threads[c / 3], reinterpret_cast<const TaskHeader*>(g->ws + g->F.tasks));
+      }
+      r = r ? r : gerr(cudaEventRecord(e1, g->st));
+      r = r ? r : gerr(cudaEventSynchronize(e1));
+      float t = 0;
+      if (r == SRLA_OK && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms[c].push_back(t);
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  int best = 4;  // 256 threads, 64K packets
+  float best_ms = 1e30f;
+  for (int c = 0; c < 9; c++) {
+    if (ms[c].empty()) continue;
+    std::sort(ms[c].begin(), ms[c].end());
+    const float med = ms[c][ms[c].size() / 2];
+    if (med < best_ms) {
+      best_ms = med;
+      best = c;
+    }
+  }
+  // the slice end starts from empty pair tables and a zero task counter, as without tuning
+  for (const Slot& s : g->slots)
+    if (s.active && s.L.pairs)
+      r = r ? r : gerr(cudaMemsetAsync(g->ws + s.off + s.L.ptab, 0xFF, ((size_t)s.L.pmask + 1) * 8, g->st));
+  r = r ? r : gerr(cudaMemsetAsync(&g->gctl()->next_task, 0, sizeof(unsigned), g->st));
+  g->scan_threads = threads[best / 3];
+  g->task_pkts = tasks[best % 3];
+  g->pending.clear();
+  // the captured slice ends must launch the chosen scan
+  for (int x = 0; x < 2; x++) {
+    if (g->graph[x]) cudaGraphExecDestroy(g->graph[x]);
+    g->graph[x] = nullptr;
+  }
+  r = r ? r : capture(g);
+  if (best_threads) *best_threads = (uint32_t)g->scan_threads;
+  if (best_task_pkts) *best_task_pkts = g->task_pkts;
+  return r;
 }
 
 int srla_group_sync(srla_group_t* g) {

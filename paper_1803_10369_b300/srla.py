@@ -79,6 +79,7 @@ SIGNATURES = {
     "srla_group_end_slice": (ctypes.c_int, [_P, _P]),
     "srla_group_report_all": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_size_t, _P, _P, _P]),
     "srla_group_report": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, ctypes.c_size_t, _P, _P]),
+    "srla_group_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
     "srla_group_sync": (ctypes.c_int, [_P]),
     "srla_group_kernel_launches": (ctypes.c_uint64, [_P]),
     "srla_group_destroy": (None, [_P]),
@@ -382,6 +383,12 @@ class Group:
         e = out[:min(n.value, p.max_candidates)]
         return {"aip": e["aip"].copy(), "w": e["w"].copy(), "est": e["est"].copy(), "flags": e["flags"].copy(),
                 "stats": _stats_dict(st, p.u), "rc": rc}
+
+    def autotune(self, reps=3):
+        """Pick the scan block size and task size on the open slice's packets; returns both."""
+        t, k = ctypes.c_uint32(), ctypes.c_uint32()
+        _ck(self.L.srla_group_autotune(self._h, reps, ctypes.byref(t), ctypes.byref(k)), "srla_group_autotune")
+        return t.value, k.value
 
     def sync(self):
         _ck(self.L.srla_group_sync(self._h), "srla_group_sync")

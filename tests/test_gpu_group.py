@@ -70,6 +70,9 @@ def test_group_equals_links_alone(cuda_device):
             else:
                 g.push(ids[i], pk)  # host batch, staged by the group
             solo[i].push(pk.to(cuda_device))
+        if s == 2:  # tuning repeats the slice's own scan with other launch shapes: no effect on results
+            threads, task = g.autotune(reps=1)
+            assert threads in (128, 256, 512) and task in (1 << 14, 1 << 16, 1 << 18)
         gs = g.end_slice()
         want = [solo[i].report(solo[i].end_slice()) for i in range(len(links))]
         allr = g.report_all(gs)

@@ -272,6 +272,64 @@ int srla_group_sync(srla_group_t *g);
 uint64_t srla_group_kernel_launches(const srla_group_t *g);
 void srla_group_destroy(srla_group_t *g);
 
+
+/* ======================================================================================
+ * Serving: a request loop over one group.  Links arrive (open), depart (close) and send
+ * packet batches (submit) from any host thread; one driver thread calls srla_server_tick
+ * once per slice.  A tick applies the departures, admits waiting links in arrival order
+ * while their arena bytes fit the HBM budget and a slot is free (continuous batching: a link
+ * that arrives while slices are running joins at the next tick), pushes the batches that
+ * arrived for admitted links, and closes the slice of every admitted link with one graph
+ * launch.  Links are named by the caller's 64-bit keys.
+ * ====================================================================================== */
+typedef struct srla_server_s srla_server_t;
+
+typedef struct srla_server_config {
+  uint32_t max_links;      /* group slots */
+  uint32_t max_report;     /* report entries per slice over all links */
+  uint64_t max_pkts;       /* packets per slice over all links */
+  uint64_t max_host_pkts;  /* of which from host memory */
+  uint64_t budget_bytes;   /* admission budget for link regions (at most the arena) */
+} srla_server_config;
+
+/* One admitted link's result of a closed slice. */
+typedef struct srla_server_result {
+  uint64_t key;
+  uint32_t first, count;   /* its entries: entries[first .. first + count) */
+  srla_slice_stats stats;
+} srla_server_result;
+
+/* Workspace bytes: the group's fixed part plus `arena_bytes` for link regions. */
+size_t srla_server_workspace_bytes(const srla_server_config *c, uint64_t arena_bytes);
+int srla_server_create(const srla_server_config *c, void *dev_workspace, size_t ws_bytes,
+                       void *stream, srla_server_t **out);
+
+/* A link arrives with parameters p (queued until admitted).  INVAL: bad p or key in use;
+ * NOMEM: the link alone exceeds the budget.                                               */
+int srla_server_open(srla_server_t *s, uint64_t key, const srla_params *p);
+/* A link departs at the next tick (or leaves the admission queue).                      */
+int srla_server_close(srla_server_t *s, uint64_t key);
+/* A batch for the link's open slice, pushed at the next tick.  Device or host memory (see
+ * srla_push_packets); it must stay unchanged until the tick that pushes it has returned
+ * and, for device memory, until that slice's results are polled.  ORDER: the link is not
+ * admitted (the batch is not taken).                                                     */
+int srla_server_submit(srla_server_t *s, uint64_t key, const uint32_t *pairs, uint64_t n_pairs,
+                       int on_device);
+
+/* Close a slice (driver thread).  *slice receives its index; *admitted / *waiting (may be
+ * NULL) the links in it and the links still queued for admission.                       */
+int srla_server_tick(srla_server_t *s, uint64_t *slice, uint32_t *admitted, uint32_t *waiting);
+
+/* Results of one of the two most recent slices: per admitted link, its key, statistics and
+ * entry range in `entries` (sorted by aip within a link).                               */
+int srla_server_poll(srla_server_t *s, uint64_t slice, srla_server_result *results,
+                     size_t result_cap, size_t *n_results, srla_entry *entries,
+                     size_t entry_cap, size_t *n_entries);
+
+/* Bytes of the budget in use by admitted links. */
+uint64_t srla_server_used_bytes(const srla_server_t *s);
+void srla_server_destroy(srla_server_t *s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,6 +5,7 @@ from .srla import (  # noqa: F401
     Group,
     NEW,
     SATURATED,
+    Server,
     SUPER,
     Link,
     SRLAError,

@@ -83,6 +83,15 @@ SIGNATURES = {
     "srla_group_sync": (ctypes.c_int, [_P]),
     "srla_group_kernel_launches": (ctypes.c_uint64, [_P]),
     "srla_group_destroy": (None, [_P]),
+    "srla_server_workspace_bytes": (ctypes.c_size_t, [_P, ctypes.c_uint64]),
+    "srla_server_create": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P]),
+    "srla_server_open": (ctypes.c_int, [_P, ctypes.c_uint64, _P]),
+    "srla_server_close": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "srla_server_submit": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_uint64, ctypes.c_int]),
+    "srla_server_tick": (ctypes.c_int, [_P, _P, _P, _P]),
+    "srla_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_size_t, _P, _P, ctypes.c_size_t, _P]),
+    "srla_server_used_bytes": (ctypes.c_uint64, [_P]),
+    "srla_server_destroy": (None, [_P]),
 }
 
 STATIC_SCRATCH_BYTES = 32 * 1024 * 1024
@@ -404,6 +413,100 @@ class Group:
     def __del__(self):
         try:
             self.close()
+        except Exception:
+            pass
+
+
+class srla_server_config(ctypes.Structure):
+    _fields_ = [("max_links", ctypes.c_uint32), ("max_report", ctypes.c_uint32), ("max_pkts", ctypes.c_uint64),
+                ("max_host_pkts", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64)]
+
+
+class srla_server_result(ctypes.Structure):
+    _fields_ = [("key", ctypes.c_uint64), ("first", ctypes.c_uint32), ("count", ctypes.c_uint32),
+                ("stats", srla_slice_stats)]
+
+
+class Server:
+    """Serving loop over one link group: links open and close, batches arrive, tick() closes
+    a slice for every admitted link (admission in arrival order under a byte budget)."""
+
+    def __init__(self, max_links, max_pkts, budget_bytes, arena_bytes=None, max_host_pkts=0, max_report=1 << 20,
+                 device="cuda", stream=None):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise RuntimeError("libsrla needs a CUDA device")
+        self.L = lib()
+        self.cfg = srla_server_config(max_links, max_report, max_pkts, max_host_pkts, budget_bytes)
+        arena = int(arena_bytes if arena_bytes is not None else budget_bytes + (64 << 20))
+        nbytes = self.L.srla_server_workspace_bytes(ctypes.byref(self.cfg), arena)
+        if nbytes == 0:
+            raise SRLAError(E_INVAL, "srla_server_workspace_bytes")
+        self.device = torch.device(device)
+        with torch.cuda.device(self.device):
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            h = ctypes.c_void_p()
+            _ck(self.L.srla_server_create(ctypes.byref(self.cfg), ctypes.c_void_p(self.workspace.data_ptr()), nbytes,
+                                          ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+                "srla_server_create")
+        self._h = h
+        self.params = {}
+        self._keep = []
+        self._res = (srla_server_result * max_links)()
+        self._ent = np.empty(max_report, dtype=ENTRY_DTYPE)
+
+    def open(self, key: int, params: srla_params):
+        _ck(self.L.srla_server_open(self._h, key, ctypes.byref(params)), "srla_server_open")
+        self.params[key] = params
+
+    def close(self, key: int):
+        _ck(self.L.srla_server_close(self._h, key), "srla_server_close")
+
+    def submit(self, key: int, pairs) -> bool:
+        """Queue a batch; False if the link is not admitted yet (the batch is not taken)."""
+        ptr, n, on_dev, keep = _pairs_arg(pairs)
+        rc = self.L.srla_server_submit(self._h, key, ctypes.c_void_p(ptr), n, on_dev)
+        if rc == E_ORDER:
+            return False
+        _ck(rc, "srla_server_submit")
+        self._keep.append(keep)
+        return True
+
+    def tick(self):
+        sl, adm, wt = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()
+        _ck(self.L.srla_server_tick(self._h, ctypes.byref(sl), ctypes.byref(adm), ctypes.byref(wt)), "srla_server_tick")
+        self._keep = self._keep[-8192:]
+        return sl.value, adm.value, wt.value
+
+    def poll(self, slice_id: int):
+        """{key: report dict} of the links admitted in that slice."""
+        nr, ne = ctypes.c_size_t(), ctypes.c_size_t()
+        rc = self.L.srla_server_poll(self._h, slice_id, self._res, len(self._res), ctypes.byref(nr),
+                                     ctypes.c_void_p(self._ent.ctypes.data), len(self._ent), ctypes.byref(ne))
+        if rc not in (OK, E_CAPACITY):
+            raise SRLAError(rc, "srla_server_poll")
+        out = {}
+        for i in range(nr.value):
+            r = self._res[i]
+            e = self._ent[r.first:r.first + r.count]
+            u = self.params[r.key].u if r.key in self.params else MAX_ROWS
+            out[r.key] = {"aip": e["aip"].copy(), "w": e["w"].copy(), "est": e["est"].copy(),
+                          "flags": e["flags"].copy(), "stats": _stats_dict(r.stats, u), "rc": rc}
+        return out
+
+    def used_bytes(self) -> int:
+        return self.L.srla_server_used_bytes(self._h)
+
+    def destroy(self):
+        if getattr(self, "_h", None):
+            self.L.srla_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.destroy()
         except Exception:
             pass
 

@@ -486,12 +486,179 @@ def bench_batched(args):
     print(json.dumps(line), flush=True)
 
 
+def bench_served(args):
+    """Serving loop: links of the served workload arrive (Poisson) and depart (mean lifetime 600
+    slices), each sends its slice's packets as batches of 4K..1M pairs; the server admits links
+    under a 60 GB budget and closes one slice per tick for all of them.  Compared with the
+    plain per-link loop (one handle per link, created at arrival) on the same schedule."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1803_10369_b300 import srla
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    ident = synth.served_links(256)
+    params = []
+    for w, plog in ident:
+        ha, hb = synth.hash_coefficients(w.hash_seed, w.u + 3)
+        params.append(srla.params_for(w, ha, hb, pair_slots_log2=plog))
+    rng = np.random.default_rng(7)
+    conc, life = 96, 600.0
+    ticks = args.prefill if args.prefill >= 0 else 8
+    K, W = args.steps, args.warmup
+    n_ticks = ticks + W + K + max(K, 32)
+    # the schedule: who is open at each tick (identities are never reused)
+    order = list(rng.permutation(len(ident)))
+    active = [order.pop() for _ in range(conc)]
+    events = []
+    for t in range(n_ticks):
+        gone = [k for k in active if rng.random() < 1.0 / life]
+        new = [order.pop() for _ in range(min(len(order), rng.poisson(conc / life)))]
+        active = [k for k in active if k not in gone] + new
+        events.append((gone, new, list(active)))
+    used = sorted(set(k for _, _, a in events for k in a) | set(events[0][2]))
+    pool = {k: [synth.generate_slice(ident[k][0].traffic, s, device=dev) for s in range(2)] for k in used}
+
+    def batches_of(k, t):
+        pk = pool[k][t % 2]
+        n, out, a = pk.shape[0], [], 0
+        while a < n:
+            b = min(n, a + int(np.exp(rng.uniform(np.log(4096), np.log(1 << 20)))))
+            out.append(pk[a:b])
+            a = b
+        return out
+
+    plan = [{k: batches_of(k, t) for k in events[t][2]} for t in range(n_ticks)]
+    pkts = [sum(int(x.shape[0]) for bs in plan[t].values() for x in bs) for t in range(n_ticks)]
+    stream = torch.cuda.Stream(dev)
+
+    # ---- the server
+    budget = 60 << 30
+    arena = min(budget, sum(srla.Group.link_bytes(params[k]) for k in used) + (256 << 20))
+    srv = srla.Server(max_links=256, max_pkts=2 * max(pkts), budget_bytes=budget, arena_bytes=arena,
+                      max_report=1 << 21, device=dev, stream=stream)
+    for k in events[0][2]:
+        srv.open(k, params[k])
+    srv.tick()
+
+    flat = [([k for k, bs in plan[t].items() for _ in bs], [x for bs in plan[t].values() for x in bs])
+            for t in range(n_ticks)]
+
+    def server_tick(t):
+        gone, new, _ = events[t]
+        for k in gone:
+            srv.close(k)
+        for k in new:
+            srv.open(k, params[k])
+        srv.submit_many(*flat[t])
+        return srv.tick()[0]
+
+    with torch.cuda.stream(stream):
+        t = 1
+        for i in range(ticks + W):
+            if i == ticks // 2:
+                srv.autotune(3)  # the scan launch shape, tuned on a live tick
+            srv.poll(server_tick(t))
+            t += 1
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        pending, n_srv = None, 0
+        for _ in range(K):
+            sl = server_tick(t)
+            n_srv += pkts[t]
+            t += 1
+            if pending is not None:
+                srv.poll(pending)
+            pending = sl
+        srv.poll(pending)
+        torch.cuda.synchronize(dev)
+        srv_s = time.perf_counter() - t0
+        lat_s = []
+        for _ in range(max(K, 32)):
+            if t >= n_ticks:
+                break
+            gone, new, _ = events[t]
+            for k in gone:
+                srv.close(k)
+            for k in new:
+                srv.open(k, params[k])
+            srv.submit_many(*flat[t])
+            t0 = time.perf_counter()
+            srv.poll(srv.tick()[0])
+            lat_s.append((time.perf_counter() - t0) * 1e3)
+            t += 1
+    srv.destroy()
+    del srv
+
+    # ---- the plain per-link loop on the same schedule
+    links = {}
+
+    def loop_tick(t, lat=None):
+        gone, new, _ = events[t]
+        for k in gone:
+            links.pop(k).close()
+        for k in new:
+            links[k] = srla.Link(params[k], device=dev, stream=stream)
+        ends = []
+        for k, L in links.items():
+            for x in plan[t].get(k, []):
+                L.push(x)
+            ends.append((k, time.perf_counter(), L.end_slice()))
+        for k, t_end, sid in ends:
+            links[k].report(sid)
+            if lat is not None:
+                lat.append((time.perf_counter() - t_end) * 1e3)
+
+    with torch.cuda.stream(stream):
+        for k in events[0][2]:
+            links[k] = srla.Link(params[k], device=dev, stream=stream)
+        t = 1
+        for _ in range(ticks + W):
+            loop_tick(t)
+            t += 1
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        n_loop = 0
+        for _ in range(K):
+            loop_tick(t)
+            n_loop += pkts[t]
+            t += 1
+        torch.cuda.synchronize(dev)
+        loop_s = time.perf_counter() - t0
+        lat_l = []
+        for _ in range(max(K, 32)):
+            if t >= n_ticks:
+                break
+            loop_tick(t, lat_l)
+            t += 1
+    for L in links.values():
+        L.close()
+    line = {
+        "metric": METRIC, "value": round(n_srv / srv_s / 1e6, 3), "unit": "Mpkts/s", "n_gpus": 1, "steps": K,
+        "warmup": W, "ms_per_step": round(1e3 * srv_s / K, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8/u16", "data": "synthetic",
+        "config": {"workload": "served-poisson-links-mean-life-600-batches-4k-1M-budget-60GB",
+                   "identities": len(ident), "concurrent_links": conc,
+                   "pkts_per_tick_mean": int(np.mean(pkts)), "timing": "host wall clock, pipelined ticks"},
+        "latency_ms": {"p50": round(_pctl(lat_s, 0.5), 4), "p99": round(_pctl(lat_s, 0.99), 4),
+                       "what": "tick call to every link's results on the host (scan included)"},
+        "per_link_loop": {"value": round(n_loop / loop_s / 1e6, 3), "ms_per_step": round(1e3 * loop_s / K, 4),
+                          "latency_ms": {"p50": round(_pctl(lat_l, 0.5), 4), "p99": round(_pctl(lat_l, 0.99), 4),
+                                         "what": "a link's end_slice call to its report on the host"}},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = _args()
     if args.impl == "reference":
         bench_reference(args)
     elif args.workload == "batched":
         bench_batched(args)
+    elif args.workload == "served":
+        bench_served(args)
     else:
         bench_srla(args)
 

@@ -316,6 +316,16 @@ int srla_server_close(srla_server_t *s, uint64_t key);
 int srla_server_submit(srla_server_t *s, uint64_t key, const uint32_t *pairs, uint64_t n_pairs,
                        int on_device);
 
+/* n batches at once (keys[i], pairs[i], n_pairs[i], all in device or all in host memory).
+ * *taken receives how many were queued; batches of links not admitted are skipped.       */
+int srla_server_submit_many(srla_server_t *s, uint32_t n, const uint64_t *keys,
+                            const uint32_t *const *pairs, const uint64_t *n_pairs, int on_device,
+                            uint32_t *taken);
+
+/* Ask the next tick to autotune the group scan on its own batches (srla_group_autotune with
+ * reps runs per configuration) before closing the slice.                                 */
+int srla_server_autotune(srla_server_t *s, int reps);
+
 /* Close a slice (driver thread).  *slice receives its index; *admitted / *waiting (may be
  * NULL) the links in it and the links still queued for admission.                       */
 int srla_server_tick(srla_server_t *s, uint64_t *slice, uint32_t *admitted, uint32_t *waiting);

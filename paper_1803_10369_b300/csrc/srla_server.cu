@@ -49,6 +49,7 @@ struct srla_server_s {
   uint64_t used = 0;
   std::vector<Member> members[2];  // links of the two most recent slices, by parity
   uint64_t slice_of[2] = {~0ull, ~0ull};
+  int tune_reps = 0;               // autotune the scan at the next tick
   std::vector<srla_entry> all;     // scratch for report_all
   std::vector<uint32_t> offs;
   std::vector<srla_slice_stats> stats;
@@ -116,6 +117,28 @@ int srla_server_submit(srla_server_t* s, uint64_t key, const uint32_t* pairs, ui
   return SRLA_OK;
 }
 
+int srla_server_submit_many(srla_server_t* s, uint32_t n, const uint64_t* keys, const uint32_t* const* pairs,
+                            const uint64_t* n_pairs, int on_device, uint32_t* taken) {
+  if (!s || (n && (!keys || !pairs || !n_pairs))) return SRLA_E_INVAL;
+  uint32_t k = 0;
+  std::lock_guard<std::mutex> lock(s->mu);
+  for (uint32_t i = 0; i < n; i++) {
+    if (!pairs[i] && n_pairs[i]) return SRLA_E_INVAL;
+    if (!s->link_of.count(keys[i])) continue;
+    if (n_pairs[i]) s->batches.push_back(Batch{keys[i], pairs[i], n_pairs[i], on_device});
+    k++;
+  }
+  if (taken) *taken = k;
+  return SRLA_OK;
+}
+
+int srla_server_autotune(srla_server_t* s, int reps) {
+  if (!s || reps < 1) return SRLA_E_INVAL;
+  std::lock_guard<std::mutex> lock(s->mu);
+  s->tune_reps = reps;
+  return SRLA_OK;
+}
+
 int srla_server_tick(srla_server_t* s, uint64_t* slice, uint32_t* admitted, uint32_t* waiting) {
   if (!s) return SRLA_E_INVAL;
   std::vector<uint64_t> closes;
@@ -170,6 +193,16 @@ int srla_server_tick(srla_server_t* s, uint64_t* slice, uint32_t* admitted, uint
       link = it->second;
     }
     if ((r = srla_group_push(s->g, link, b.pairs, b.n, b.on_device)) != SRLA_OK) return r;
+  }
+  int reps = 0;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    reps = s->tune_reps;
+    s->tune_reps = 0;
+  }
+  if (reps && !batches.empty()) {
+    r = srla_group_autotune(s->g, reps, nullptr, nullptr);
+    if (r != SRLA_OK) return r;
   }
   uint64_t gs = 0;
   if ((r = srla_group_end_slice(s->g, &gs)) != SRLA_OK) return r;

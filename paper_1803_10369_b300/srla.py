@@ -88,6 +88,8 @@ SIGNATURES = {
     "srla_server_open": (ctypes.c_int, [_P, ctypes.c_uint64, _P]),
     "srla_server_close": (ctypes.c_int, [_P, ctypes.c_uint64]),
     "srla_server_submit": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_uint64, ctypes.c_int]),
+    "srla_server_submit_many": (ctypes.c_int, [_P, ctypes.c_uint32, _P, _P, _P, ctypes.c_int, _P]),
+    "srla_server_autotune": (ctypes.c_int, [_P, ctypes.c_int]),
     "srla_server_tick": (ctypes.c_int, [_P, _P, _P, _P]),
     "srla_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_size_t, _P, _P, ctypes.c_size_t, _P]),
     "srla_server_used_bytes": (ctypes.c_uint64, [_P]),
@@ -473,6 +475,25 @@ class Server:
         _ck(rc, "srla_server_submit")
         self._keep.append(keep)
         return True
+
+    def submit_many(self, keys, batches) -> int:
+        """Queue many device batches in one call (all CUDA tensors); returns how many were taken."""
+        n = len(keys)
+        if n == 0:
+            return 0
+        karr = (ctypes.c_uint64 * n)(*keys)
+        parr = (ctypes.c_void_p * n)(*[b.data_ptr() for b in batches])
+        narr = (ctypes.c_uint64 * n)(*[b.numel() // 2 for b in batches])
+        if not all(b.is_cuda and b.is_contiguous() for b in batches):
+            raise ValueError("submit_many takes contiguous CUDA tensors")
+        taken = ctypes.c_uint32()
+        _ck(self.L.srla_server_submit_many(self._h, n, karr, parr, narr, 1, ctypes.byref(taken)),
+            "srla_server_submit_many")
+        self._keep.extend(batches)
+        return taken.value
+
+    def autotune(self, reps=3):
+        _ck(self.L.srla_server_autotune(self._h, reps), "srla_server_autotune")
 
     def tick(self):
         sl, adm, wt = ctypes.c_uint64(), ctypes.c_uint32(), ctypes.c_uint32()

@@ -14,4 +14,4 @@ from .traces import (  # noqa: F401
     planted_hosts,
     random_pairs,
 )
-from .workloads import WORKLOADS, Workload, batched_links, workload  # noqa: F401
+from .workloads import WORKLOADS, Workload, batched_links, served_links, workload  # noqa: F401

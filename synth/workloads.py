@@ -120,3 +120,14 @@ def batched_links(n_links: int = 64, seed: int = 4):
             max_candidates=1 << 14)
         out.append((w, int(np.clip(round(math.log2(rate / 2)), 12, 21))))
     return out
+
+
+def served_links(n_links: int = 256, seed: int = 5):
+    """Link identities of the serving workload: like batched_links, with Zipf(1.1) sources and
+    1 to 50 planted super points per link.  Returns a list of (Workload, pair_slots_log2)."""
+    rng = np.random.Generator(np.random.PCG64(np.random.SeedSequence([seed, 0x5E7F])))
+    out = []
+    for i, (w, plog) in enumerate(batched_links(n_links, seed)):
+        t = dataclasses.replace(w.traffic, seed=5000 + i, zipf_s=1.1, n_planted=int(rng.integers(1, 51)))
+        out.append((dataclasses.replace(w, name=f"served-{w.name}", traffic=t, hash_seed=700 + i), plog))
+    return out

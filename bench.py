@@ -69,7 +69,7 @@ def _algorithmic_bytes_per_pkt(w, tau):
 
 # DRAM traffic of one k_scan launch (5M packets of the paper-scale workload) from one ncu
 # capture (profiles/k_scan_paper_scale.md), valid only for the kernel sources it was taken on.
-SCAN_TRAFFIC = {"bytes_per_launch": 103.865344e6 + 56.594688e6, "pkts": 5_000_000, "sources": "f0e31af2f691c56f"}
+SCAN_TRAFFIC = {"bytes_per_launch": 103.844352e6 + 56.071424e6, "pkts": 5_000_000, "sources": "2863fa01a6bfae46"}
 
 
 def _kernel_sources_hash():

@@ -69,7 +69,11 @@ def _algorithmic_bytes_per_pkt(w, tau):
 
 # DRAM traffic of one k_scan launch (5M packets of the paper-scale workload) from one ncu
 # capture (profiles/k_scan_paper_scale.md), valid only for the kernel sources it was taken on.
-SCAN_TRAFFIC = {"bytes_per_launch": 103.844352e6 + 56.071424e6, "pkts": 5_000_000, "sources": "2863fa01a6bfae46"}
+SCAN_TRAFFIC = {
+    "sources": "2863fa01a6bfae46",
+    "paper-1link-u8-v16384-g128-gl256-z16-k300-5Mpps": {"bytes_per_launch": 103.844352e6 + 56.071424e6,
+                                                         "pkts": 5_000_000},
+}
 
 
 def _kernel_sources_hash():
@@ -83,10 +87,13 @@ def _kernel_sources_hash():
     return h.hexdigest()[:16]
 
 
-def _scan_traffic(pkts_per_launch):
-    if _kernel_sources_hash() != SCAN_TRAFFIC["sources"] or pkts_per_launch != SCAN_TRAFFIC["pkts"]:
+def _scan_traffic(workload, pkts_per_launch):
+    """DRAM bytes (read + write) of one scan launch from the ncu capture of this workload, or
+    None when the kernel sources changed since the capture or the launch size differs."""
+    t = SCAN_TRAFFIC.get(workload)
+    if t is None or _kernel_sources_hash() != SCAN_TRAFFIC["sources"] or pkts_per_launch != t["pkts"]:
         return None
-    return SCAN_TRAFFIC["bytes_per_launch"]
+    return t["bytes_per_launch"]
 
 
 def _peaks():
@@ -349,7 +356,7 @@ def bench_srla(args):
                        "slice_end_gpu_p50": round(statistics.median(lat_gpu), 4)},
         "scan_mpkts_s": round(per_launch_pkts / (scan_avg_ms * 1e-3) / 1e6, 3),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 5), "traffic": _scan_traffic(int(per_launch_pkts)),
+                     "frac": round(achieved / peak, 5), "traffic": _scan_traffic(w.name, int(per_launch_pkts)),
                      "kernel": "k_scan", "bytes_per_pkt": bpp, "peak_kind": peak_kind},
         "e2e": {"value": round(e2e, 3), "unit": "Mpkts/s", "h2d_bytes_per_step": int(8 * per_launch_pkts),
                 "d2h_bytes_per_step": int(statistics.mean(d2h))},

@@ -85,7 +85,17 @@ LONGWIN = Workload(
     max_sampled=1 << 21, max_candidates=1 << 20,
 )
 
-WORKLOADS = {"tiny": TINY, "paper": PAPER, "longwin": LONGWIN}
+# The paper's own parameters (Section 5): u=4 rows, v=65536 columns, g=8 SRE cells and
+# g'=1024 SLE cells per estimator, 16-bit recorders, window 300 slices, 4.5M packets per slice
+# (the traces' average rate); same traffic recipe as PAPER.
+PAPER_OWN = Workload(
+    name="paperown-1link-u4-v65536-g8-gl1024-z16-k300-4.5Mpps",
+    u=4, v=1 << 16, g=8, gl=1024, dr_bytes=2, z=16, k=300, theta=1024, n_slices=320,
+    traffic=dataclasses.replace(PAPER.traffic, seed=6, pkts_per_slice=4_500_000),
+    max_sampled=1 << 18, max_candidates=1 << 18,
+)
+
+WORKLOADS = {"tiny": TINY, "paper": PAPER, "longwin": LONGWIN, "paperown": PAPER_OWN}
 
 
 def workload(name: str) -> Workload:

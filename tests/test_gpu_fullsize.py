@@ -51,3 +51,11 @@ def test_paper_scale_uniform_destinations(cuda_device):
     w = synth.workload("paper").replace(dst_model="uniform", dst_space=1 << 20, planted_spread=3,
                                         pkts_per_slice=2_000_000)
     _run(w, 2, cuda_device, state_every=2)
+
+
+def test_paper_own_parameters(cuda_device):
+    """The paper's own parameters: u=4, v=65536, g=8 (tau=7, ceil(rho*g)=3), g'=1024, 16-bit
+    recorders (512 MiB of SLE), k=300, 4.5M packets per slice."""
+    w = synth.workload("paperown").replace(planted_spread=3)
+    n_cand = _run(w, 4, cuda_device, state_every=2)
+    assert n_cand >= 100

@@ -62,9 +62,11 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
 
 def _algorithmic_bytes_per_pkt(w, tau):
     """Bytes the scan must move per packet: the 8-byte pair, u SLE recorders, u SRE recorders
-    for the 2^-tau sampled share, and a 4-byte sampled-host record for that share."""
+    for the 2^-tau sampled share, and a 4-byte sampled-host record for that share (a one-bit
+    recorder counts 1/8 byte)."""
     s = 2.0 ** -tau
-    return 8.0 + w.u * w.dr_bytes + s * w.u * w.dr_bytes + s * 4.0
+    b = w.dr_bytes if w.dr_bytes else 0.125
+    return 8.0 + w.u * b + s * w.u * b + s * 4.0
 
 
 # DRAM traffic of one k_scan launch (5M packets of the paper-scale workload) from one ncu
@@ -351,7 +353,7 @@ def bench_srla(args):
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpkts/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(elapsed_ms / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "u16" if w.dr_bytes == 2 else "u8", "data": "synthetic", "config": _config(w),
+        "dtype": {0: "u1", 1: "u8", 2: "u16"}[w.dr_bytes], "data": "synthetic", "config": _config(w),
         "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "slices": n_lat,
                        "slice_end_gpu_p50": round(statistics.median(lat_gpu), 4)},
         "scan_mpkts_s": round(per_launch_pkts / (scan_avg_ms * 1e-3) / 1e6, 3),

@@ -48,8 +48,11 @@ extern "C" {
  * Parameters (Sections 3.2, 4.1, 5).  v, g and gl must be powers of two.
  *   u, v        rows and columns of the sliding estimator array (u <= SRLA_MAX_ROWS)
  *   g, gl       distance recorders per SRE and per SLE (the paper's g and g')
- *   dr_bytes    bytes that hold one recorder: 1 or 2
- *   z           recorder bits, 1 <= z <= 8 * dr_bytes; the largest distance is 2^z - 1
+ *   dr_bytes    bytes that hold one recorder: 1 or 2; 0 packs one-bit recorders 32 to a word
+ *               (then z = 1, so k = 1: the discrete window of Section 3.1; 8x less memory
+ *               than 1-byte recorders)
+ *   z           recorder bits, 1 <= z <= 8 * dr_bytes (z = 1 when dr_bytes = 0); the largest
+ *               distance is 2^z - 1
  *   k           window length in slices, 1 <= k <= 2^z - 1 (Section 3.2)
  *   theta       super point threshold, >= 1 (Definition 2)
  *   start_slice index of the first open slice
@@ -63,7 +66,8 @@ extern "C" {
  *               pair per role: rows 0..u-1 (column of aip in row i), u (SLE cell of bip),
  *               u+1 (SRE cell of bip), u+2 (sampling hash of bip); a in [1, 2^61-2],
  *               b in [0, 2^61-2].  The paper leaves the family open (Section 3.2).
- * Sizes: v*g*dr_bytes and v*gl*dr_bytes are at least 16 bytes.
+ * Sizes: a row of SRE (v*g recorders) and of SLE (v*gl) recorders takes at least 16 bytes;
+ * g*dr_bytes and gl*dr_bytes are at least 4 (g, gl >= 4 for one-bit recorders).
  */
 typedef struct srla_params {
   uint32_t u, v, g, gl;

@@ -3,6 +3,7 @@
 #pragma once
 
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "srla.h"
@@ -87,6 +88,75 @@ __device__ __forceinline__ uint32_t stamp_age(uint32_t c, uint32_t tm, uint32_t 
 }
 
 
+// ------------------------------------------------------------------ one-bit recorders
+//
+// With z = 1 the window is one slice (k = 1, the discrete window of Section 3.1) and a
+// recorder only says whether it was set in the open slice.  Such recorders are packed 32 to a
+// 32-bit word: recorder x of an array is bit (x mod 32) of word x / 32; set = DRset in the open
+// slice (distance 0), clear = empty (distance 1 = 2^z - 1).  `Bit` selects this storage in the
+// templates below; its arrays are only ever addressed as words.
+struct Bit {};
+
+template <typename CellT>
+inline constexpr bool kIsBit = std::is_same_v<CellT, Bit>;
+
+// 32-bit words holding the run of `cells` recorders of one estimator (runs of fewer than 32
+// one-bit recorders share a word and never straddle two).
+template <typename CellT>
+__host__ __device__ constexpr uint32_t run_words(uint32_t cells) {
+  if constexpr (kIsBit<CellT>)
+    return cells >= 32u ? cells / 32u : 1u;
+  else
+    return cells * (uint32_t)sizeof(CellT) / 4u;
+}
+
+// Bytes of an array of n recorders.
+template <typename CellT>
+__host__ __device__ constexpr size_t cell_array_bytes(size_t n) {
+  if constexpr (kIsBit<CellT>)
+    return n / 8;
+  else
+    return n * sizeof(CellT);
+}
+
+// The recorders from index x of `arr` on (x a multiple of 32 for one-bit storage).
+template <typename CellT>
+__host__ __device__ inline CellT* cells_from(CellT* arr, size_t x) {
+  return reinterpret_cast<CellT*>(reinterpret_cast<char*>(arr) + cell_array_bytes<CellT>(x));
+}
+
+// The same, as 32-bit words (x a multiple of 32 recorders, or of 4 bytes of byte cells).
+template <typename CellT>
+__host__ __device__ inline uint32_t* words_at(CellT* arr, size_t x) {
+  return reinterpret_cast<uint32_t*>(cells_from(arr, x));
+}
+
+// The stamp a DRset writes in the open slice (tm = T mod P).
+template <typename CellT>
+__device__ __forceinline__ CellT stamp_code(uint32_t tm) {
+  if constexpr (kIsBit<CellT>)
+    return CellT{};
+  else
+    return (CellT)(tm + 1u);
+}
+
+// The word holding one-bit recorder idx, as this SM sees it.  Within a slice bits are only
+// ever set (the sweep that clears them is another launch), so a bit seen set is set.
+template <typename CellT>
+__device__ __forceinline__ uint32_t bit_peek(const CellT* arr, size_t idx) {
+  return reinterpret_cast<const uint32_t*>(arr)[idx >> 5];
+}
+
+// DRset of recorder idx.  Every writer of a slice writes the same stamp, so a plain store
+// suffices for byte cells; one-bit recorders share words, so they are set with an atomic OR.
+template <typename CellT>
+__device__ __forceinline__ void dr_set(CellT* __restrict__ arr, size_t idx, CellT code) {
+  if constexpr (kIsBit<CellT>)
+    atomicOr(reinterpret_cast<uint32_t*>(arr) + (idx >> 5), 1u << (idx & 31u));
+  else
+    arr[idx] = code;
+}
+
 // The stamps inside the window of the last `lim` slices (ages 0 .. lim-1) are the codes
 // 1 + ((tm - j) mod P), j < lim: one cyclic interval of codes ending at hi = tm + 1, either
 // [lo, hi] or, when it wraps past P, [lo, P] and [1, hi].  Empty cells (code 0) are never in
@@ -105,6 +175,11 @@ template <typename CellT>
 __device__ __forceinline__ Win make_win(uint32_t tm, uint32_t P, uint32_t lim) {
   Win w;
   w.none = lim == 0;
+  if constexpr (kIsBit<CellT>) {  // a set bit is inside any window of at least one slice
+    w.lo = w.hi = 0u;
+    w.wrap = false;
+    return w;
+  }
   const uint32_t hi = tm + 1u;
   uint32_t lo;
   if (lim <= hi) {
@@ -123,6 +198,7 @@ __device__ __forceinline__ Win make_win(uint32_t tm, uint32_t P, uint32_t lim) {
 template <typename CellT>
 __device__ __forceinline__ uint32_t window_mask(uint32_t word, const Win& w) {
   if (w.none) return 0u;
+  if constexpr (kIsBit<CellT>) return word;
   if (sizeof(CellT) == 1) {
     const uint32_t ge = __vcmpgeu4(word, w.lo), le = __vcmpleu4(word, w.hi);
     return w.wrap ? (ge | (le & __vcmpne4(word, 0u))) : (ge & le);
@@ -135,7 +211,10 @@ __device__ __forceinline__ uint32_t window_mask(uint32_t word, const Win& w) {
 // Number of cells set in a sum of popcounts of per-cell masks.
 template <typename CellT>
 __device__ __forceinline__ uint32_t cells_of_bits(uint32_t bits) {
-  return bits / (8u * (uint32_t)sizeof(CellT));
+  if constexpr (kIsBit<CellT>)
+    return bits;
+  else
+    return bits / (8u * (uint32_t)sizeof(CellT));
 }
 
 // ------------------------------------------------------------------------- host sets
@@ -249,11 +328,32 @@ __device__ __forceinline__ void load_words(const uint32_t* run, uint32_t w0, uin
   }
 }
 
+// Words w0.. of the run of estimator (row i, column c); a one-bit run shorter than a word is
+// returned in wd[0], shifted down, to the lane with w0 = 0.
+template <typename CellT, int WPL>
+__device__ __forceinline__ void load_run(const CellT* __restrict__ arr, uint32_t v, uint32_t cells, uint32_t i,
+                                         uint32_t c, uint32_t w0, uint32_t wd[WPL]) {
+  const size_t se = (size_t)i * v + c;
+  if constexpr (kIsBit<CellT>) {
+    const uint32_t* words = reinterpret_cast<const uint32_t*>(arr);
+    if (cells >= 32u) {
+      load_words<WPL>(words + se * (cells / 32u), w0, wd);
+    } else {
+      const size_t bit = se * cells;
+      wd[0] = (__ldg(words + (bit >> 5)) >> (bit & 31u)) & ((1u << cells) - 1u);
+#pragma unroll
+      for (int q = 1; q < WPL; q++) wd[q] = 0u;
+    }
+  } else {
+    load_words<WPL>(reinterpret_cast<const uint32_t*>(arr + se * cells), w0, wd);
+  }
+}
+
 // Rows are fetched four at a time, all loads in flight before any is used.
 template <typename CellT, int WPL>
 __device__ __forceinline__ uint32_t union_count_w(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
                                                   uint32_t u, uint32_t mycol, const Win& win, int lane) {
-  const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;  // 32-bit words per run
+  const uint32_t R = run_words<CellT>(cells);
   const uint32_t trips = (R + 32u * WPL - 1) / (32u * WPL);
   uint32_t total = 0;
   for (uint32_t t = 0; t < trips; t++) {
@@ -268,8 +368,7 @@ __device__ __forceinline__ uint32_t union_count_w(const CellT* __restrict__ arr,
       for (int r = 0; r < 4; r++) {
         const uint32_t i = i0 + (uint32_t)r;
         const uint32_t c = __shfl_sync(kFull, mycol, (int)(i & 31u));
-        if (ok && i < u)
-          load_words<WPL>(reinterpret_cast<const uint32_t*>(arr + ((size_t)i * v + c) * cells), w0, wd[r]);
+        if (ok && i < u) load_run<CellT, WPL>(arr, v, cells, i, c, w0, wd[r]);
       }
 #pragma unroll
       for (int r = 0; r < 4; r++)
@@ -289,7 +388,7 @@ __device__ __forceinline__ uint32_t union_count_w(const CellT* __restrict__ arr,
 template <typename CellT>
 __device__ __forceinline__ uint32_t union_count(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
                                                 uint32_t u, uint32_t mycol, const Win& win, int lane) {
-  const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;
+  const uint32_t R = run_words<CellT>(cells);
   if (R >= 128) return union_count_w<CellT, 4>(arr, v, cells, u, mycol, win, lane);
   if (R >= 64) return union_count_w<CellT, 2>(arr, v, cells, u, mycol, win, lane);
   return union_count_w<CellT, 1>(arr, v, cells, u, mycol, win, lane);
@@ -307,7 +406,7 @@ template <typename CellT, int WPL>
 __device__ __forceinline__ void union_count_atleast2_w(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
                                                        uint32_t u, uint32_t col0, uint32_t col1, const Win& win,
                                                        uint32_t need, int lane, uint32_t& out0, uint32_t& out1) {
-  const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;
+  const uint32_t R = run_words<CellT>(cells);
   const uint32_t w0 = (uint32_t)lane * WPL;
   const bool ok = w0 < R;
   uint32_t m0[WPL], m1[WPL];
@@ -318,8 +417,8 @@ __device__ __forceinline__ void union_count_atleast2_w(const CellT* __restrict__
   for (uint32_t i = 0; i < u && (live0 || live1); i++) {
     const uint32_t c0 = __shfl_sync(kFull, col0, (int)i), c1 = __shfl_sync(kFull, col1, (int)i);
     uint32_t wd0[WPL], wd1[WPL];
-    if (ok && live0) load_words<WPL>(reinterpret_cast<const uint32_t*>(arr + ((size_t)i * v + c0) * cells), w0, wd0);
-    if (ok && live1) load_words<WPL>(reinterpret_cast<const uint32_t*>(arr + ((size_t)i * v + c1) * cells), w0, wd1);
+    if (ok && live0) load_run<CellT, WPL>(arr, v, cells, i, c0, w0, wd0);
+    if (ok && live1) load_run<CellT, WPL>(arr, v, cells, i, c1, w0, wd1);
     uint32_t p0 = 0, p1 = 0;
 #pragma unroll
     for (int q = 0; q < WPL; q++) {
@@ -343,7 +442,7 @@ template <typename CellT>
 __device__ __forceinline__ void union_count_atleast2(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
                                                      uint32_t u, uint32_t col0, uint32_t col1, const Win& win,
                                                      uint32_t need, int lane, uint32_t& out0, uint32_t& out1) {
-  const uint32_t R = cells * (uint32_t)sizeof(CellT) / 4u;
+  const uint32_t R = run_words<CellT>(cells);
   if (R <= 32) return union_count_atleast2_w<CellT, 1>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
   if (R <= 64) return union_count_atleast2_w<CellT, 2>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
   if (R <= 128) return union_count_atleast2_w<CellT, 4>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);

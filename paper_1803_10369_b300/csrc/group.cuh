@@ -14,7 +14,7 @@ struct LinkDesc {
   Geo geo;
   Coef coef;
   uint32_t active;      // 0: free slot
-  uint32_t cell_bytes;  // 1 or 2
+  uint32_t cell_bytes;  // 1 or 2; 0: one-bit recorders
   uint32_t k_is_P;
   uint32_t umask, umax, cmask, cmax, ntiles, pmask;
   uint32_t pad;
@@ -72,6 +72,17 @@ struct TaskHeader {
   unsigned int pad[3];
 };
 
+// Calls f with a value of the link's recorder storage type.
+template <typename F>
+__device__ __forceinline__ void with_cells(uint32_t cell_bytes, F&& f) {
+  if (cell_bytes == 1)
+    f(uint8_t{});
+  else if (cell_bytes == 2)
+    f(uint16_t{});
+  else
+    f(Bit{});
+}
+
 // ------------------------------------------------------------------------ scan
 
 template <typename CellT, bool kVec>
@@ -83,8 +94,7 @@ __device__ __forceinline__ void group_scan_task(const ScanTask& t, const LinkDes
   CellT* re = static_cast<CellT*>(D.re);
   CellT* le = static_cast<CellT*>(D.le);
   unsigned long long* ptab = (D.ptab && ctl->pair_mode) ? D.ptab : nullptr;
-  const uint32_t tm = ctl->tm;
-  const CellT code = (CellT)(tm + 1u);
+  const CellT code = stamp_code<CellT>(ctl->tm);
   const uint32_t tag = slice_tag(ctl->T);
   const Geo& geo = D.geo;
   const Coef& coef = D.coef;
@@ -159,13 +169,13 @@ __global__ void __launch_bounds__(kThreads) kg_scan(const LinkDesc* __restrict__
     uint32_t n_miss = 0, n_gdup = 0;
     const bool vec = (stask.ptr & 15ull) == 0;
     Ctl* ctl = sdesc.ctl;
-    if (sdesc.cell_bytes == 1) {
-      if (vec) group_scan_task<uint8_t, true>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, n_miss, n_gdup);
-      else group_scan_task<uint8_t, false>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, n_miss, n_gdup);
-    } else {
-      if (vec) group_scan_task<uint16_t, true>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, n_miss, n_gdup);
-      else group_scan_task<uint16_t, false>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, n_miss, n_gdup);
-    }
+    with_cells(sdesc.cell_bytes, [&](auto cell) {
+      using CellT = decltype(cell);
+      if (vec)
+        group_scan_task<CellT, true>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, n_miss, n_gdup);
+      else
+        group_scan_task<CellT, false>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, n_miss, n_gdup);
+    });
     n_miss = warp_sum(n_miss);
     n_gdup = warp_sum(n_gdup);
     if (lane == 0 && (n_miss | n_gdup)) {
@@ -188,7 +198,8 @@ __device__ __forceinline__ void group_sweep_chunk(const SweepChunk& c, const Lin
   Ctl* ctl = D.ctl;
   const bool is_le = c.kind == 0;
   const size_t cells = (size_t)D.geo.v * (is_le ? D.geo.gl : D.geo.g);
-  uint4* base = reinterpret_cast<uint4*>(static_cast<CellT*>(is_le ? D.le : D.re) + (size_t)c.row * cells) + c.begin;
+  uint4* base = reinterpret_cast<uint4*>(words_at(static_cast<CellT*>(is_le ? D.le : D.re), (size_t)c.row * cells)) +
+                c.begin;
   const uint32_t tm = ctl->tm, P = D.geo.P;
   const uint32_t alias = 1u + (after_close ? tm : ((tm + 1u == P) ? 0u : tm + 1u));
   const uint32_t asplat = splat<CellT>(alias);
@@ -258,10 +269,7 @@ __global__ void __launch_bounds__(256) kg_sweep(const LinkDesc* __restrict__ des
       for (size_t x = threadIdx.x; x < c.count; x += blockDim.x) p[x] = ones;
       continue;
     }
-    if (D.cell_bytes == 1)
-      group_sweep_chunk<uint8_t>(c, D, post);
-    else
-      group_sweep_chunk<uint16_t>(c, D, post);
+    with_cells(D.cell_bytes, [&](auto cell) { group_sweep_chunk<decltype(cell)>(c, D, post); });
   }
 }
 
@@ -329,10 +337,7 @@ __global__ void __launch_bounds__(256, 2) kg_filter(const LinkDesc* __restrict__
   for (uint32_t i = gw; i < total; i += nw) {
     const unsigned l = link_of(filt_off, nl, i);
     const LinkDesc& D = descs[l];
-    if (D.cell_bytes == 1)
-      group_filter_pair<uint8_t>(D, i - filt_off[l], lane);
-    else
-      group_filter_pair<uint16_t>(D, i - filt_off[l], lane);
+    with_cells(D.cell_bytes, [&](auto cell) { group_filter_pair<decltype(cell)>(D, i - filt_off[l], lane); });
   }
 }
 
@@ -478,10 +483,8 @@ __global__ void __launch_bounds__(256) kg_estimate(const LinkDesc* __restrict__ 
     const LinkDesc& D = descs[l];
     const uint32_t off = rep_off[l];
     const uint32_t cap = gctl->rep_cap > off ? gctl->rep_cap - off : 0u;
-    if (D.cell_bytes == 1)
-      group_estimate_one<uint8_t>(D, i - off, lane, grep + off, cap, gctl);
-    else
-      group_estimate_one<uint16_t>(D, i - off, lane, grep + off, cap, gctl);
+    with_cells(D.cell_bytes,
+               [&](auto cell) { group_estimate_one<decltype(cell)>(D, i - off, lane, grep + off, cap, gctl); });
   }
   __syncthreads();
   if (threadIdx.x == 0) {

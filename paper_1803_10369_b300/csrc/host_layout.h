@@ -44,17 +44,25 @@ inline uint32_t tau_of(uint32_t theta, uint32_t g) {
 // ceil(rho * g) with rho = 0.99 (1 - e^{-1/3}) (Section 3.2), evaluated in FP64.
 inline uint32_t rho_g_of(uint32_t g) { return (uint32_t)std::ceil(0.99 * (1.0 - std::exp(-1.0 / 3.0)) * (double)g); }
 
+// Bytes of `cells` recorders: dr_bytes each, or one bit each when dr_bytes = 0.
+inline size_t recorder_bytes(const srla_params* p, uint64_t cells) {
+  return p->dr_bytes ? (size_t)cells * p->dr_bytes : (size_t)(cells / 8);
+}
+
 inline int check(const srla_params* p) {
   if (!p) return SRLA_E_INVAL;
   if (p->u < 1 || p->u > SRLA_MAX_ROWS) return SRLA_E_INVAL;
   if (!pow2(p->v) || !pow2(p->g) || !pow2(p->gl)) return SRLA_E_INVAL;
-  if (p->dr_bytes != 1 && p->dr_bytes != 2) return SRLA_E_INVAL;
-  if (p->z < 1 || p->z > 8 * p->dr_bytes) return SRLA_E_INVAL;
+  if (p->dr_bytes > 2) return SRLA_E_INVAL;
+  if (p->z < 1 || p->z > (p->dr_bytes ? 8 * p->dr_bytes : 1u)) return SRLA_E_INVAL;
   const uint32_t P = (1u << p->z) - 1u;
   if (p->k < 1 || p->k > P) return SRLA_E_INVAL;
   if (p->theta < 1) return SRLA_E_INVAL;
-  if ((uint64_t)p->g * p->dr_bytes < 4 || (uint64_t)p->gl * p->dr_bytes < 4) return SRLA_E_INVAL;
-  if ((uint64_t)p->v * p->g * p->dr_bytes < 16 || (uint64_t)p->v * p->gl * p->dr_bytes < 16) return SRLA_E_INVAL;
+  if (p->dr_bytes && ((uint64_t)p->g * p->dr_bytes < 4 || (uint64_t)p->gl * p->dr_bytes < 4)) return SRLA_E_INVAL;
+  if (!p->dr_bytes && (p->g < 4 || p->gl < 4)) return SRLA_E_INVAL;
+  // every row of recorders is a whole number of 16-byte vectors
+  if (recorder_bytes(p, (uint64_t)p->v * p->g) < 16 || recorder_bytes(p, (uint64_t)p->v * p->gl) < 16)
+    return SRLA_E_INVAL;
   if ((uint64_t)p->v * p->gl > (1ull << 40) || (uint64_t)p->v * p->g > (1ull << 40)) return SRLA_E_INVAL;
   if (p->gl > (1u << 24)) return SRLA_E_INVAL;
   if (p->max_sampled < 1 || p->max_sampled > (1u << 30)) return SRLA_E_INVAL;
@@ -76,16 +84,15 @@ inline Layout layout_of(const srla_params* p) {
     off = align_up(off + bytes);
     return at;
   };
-  const size_t B = p->dr_bytes;
-  L.staging_pkts = p->staging_pkts ? std::max<uint64_t>(p->staging_pkts, 4) : (1ull << 20);
+  L.staging_pkts = p->staging_pkts ? std::max<uint64_t>(p->staging_pkts, 8) : (1ull << 20);
   const uint64_t ucap = std::max<uint64_t>(64, next_pow2(2ull * p->max_sampled));
   const uint64_t ccap = std::max<uint64_t>(64, next_pow2(2ull * p->max_candidates));
   L.umask = (uint32_t)(ucap - 1);
   L.cmask = (uint32_t)(ccap - 1);
   L.ntiles = (p->max_candidates + kSortTile - 1) / kSortTile;
   L.ctl = take(sizeof(Ctl));
-  L.re = take((size_t)p->u * p->v * p->g * B);
-  L.le = take((size_t)p->u * p->v * p->gl * B);
+  L.re = take(recorder_bytes(p, (uint64_t)p->u * p->v * p->g));
+  L.le = take(recorder_bytes(p, (uint64_t)p->u * p->v * p->gl));
   L.staging = take(L.staging_pkts * 8);
   L.utab = take(ucap * 8);
   L.ulist = take((size_t)p->max_sampled * 4);

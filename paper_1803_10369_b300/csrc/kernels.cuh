@@ -23,7 +23,7 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan(const uint32_t* __rest
   __syncthreads();
   if (ptab && ctl->pair_mode == 0) ptab = nullptr;
   const uint32_t tm = ctl->tm;
-  const CellT code = (CellT)(tm + 1u);
+  const CellT code = stamp_code<CellT>(tm);
   const uint32_t tag = slice_tag(ctl->T);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
@@ -106,8 +106,8 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
   const bool reset = do_reset != 0;
   const uint32_t row = is_le ? y : y - geo.u;
   const size_t cells = (size_t)geo.v * (is_le ? geo.gl : geo.g);
-  uint4* base = reinterpret_cast<uint4*>((is_le ? le : re) + (size_t)row * cells);
-  const size_t nvec = cells * sizeof(CellT) / 16;
+  uint4* base = reinterpret_cast<uint4*>(words_at<CellT>(is_le ? le : re, (size_t)row * cells));
+  const size_t nvec = cell_array_bytes<CellT>(cells) / 16;
   const uint32_t tm = ctl->tm, P = geo.P;
   // stamp of the slice that opens next: after the slice was closed, that is the open slice
   const uint32_t alias = 1u + (after_close ? tm : ((tm + 1u == P) ? 0u : tm + 1u));
@@ -282,23 +282,36 @@ __global__ void k_decode(const CellT* __restrict__ cells, uint16_t* __restrict__
                          const Ctl* __restrict__ ctl, uint32_t P) {
   const uint32_t tm = ctl->tm;
   for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t c = cells[x];
-    out[x] = (uint16_t)(c == 0 ? P : stamp_age(c, tm, P));
+    if constexpr (kIsBit<CellT>) {
+      const uint32_t word = reinterpret_cast<const uint32_t*>(cells)[x >> 5];
+      out[x] = (uint16_t)(((word >> (x & 31u)) & 1u) ? 0u : P);
+    } else {
+      const uint32_t c = cells[x];
+      out[x] = (uint16_t)(c == 0 ? P : stamp_age(c, tm, P));
+    }
   }
 }
 
-// Distances -> stamps at open slice with T mod P = tm.
+// Distances -> stamps at open slice with T mod P = tm (one-bit recorders: 32 per thread).
 template <typename CellT>
 __global__ void k_encode(const uint16_t* __restrict__ d, CellT* __restrict__ cells, size_t n, uint32_t tm,
                          uint32_t P) {
-  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
-    const uint32_t dd = d[x];
-    uint32_t c = 0;
-    if (dd < P) {
-      const int s = ((int)tm - (int)dd) % (int)P;
-      c = 1u + (uint32_t)(s < 0 ? s + (int)P : s);
+  if constexpr (kIsBit<CellT>) {
+    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n / 32; x += (size_t)gridDim.x * blockDim.x) {
+      uint32_t word = 0;
+      for (int b = 0; b < 32; b++) word |= (d[32 * x + b] < P ? 1u : 0u) << b;
+      reinterpret_cast<uint32_t*>(cells)[x] = word;
     }
-    cells[x] = (CellT)c;
+  } else {
+    for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
+      const uint32_t dd = d[x];
+      uint32_t c = 0;
+      if (dd < P) {
+        const int s = ((int)tm - (int)dd) % (int)P;
+        c = 1u + (uint32_t)(s < 0 ? s + (int)P : s);
+      }
+      cells[x] = (CellT)c;
+    }
   }
 }
 

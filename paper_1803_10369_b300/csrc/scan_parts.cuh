@@ -73,12 +73,37 @@ __device__ __forceinline__ void scan_dense(uint32_t aip, uint32_t bip, bool ok, 
     const uint32_t jr = hash61(coef.a[u + 1], coef.b[u + 1], bip) & geo.gmask;
     const uint32_t hs = hash61(coef.a[u + 2], coef.b[u + 2], bip);
     samp = (hs & geo.samp_mask) == 0;
+    if constexpr (kIsBit<CellT>) {
+      // Four rows at a time: their words are read first (all loads in flight), and only
+      // the bits not yet set are OR-ed in.  Under heavy sources most bits of a run are set
+      // early in the slice; skipping those ORs keeps their hot L2 lines from serialising.
+      for (uint32_t i0 = 0; i0 < u; i0 += 4) {
+        size_t xl[4], xr[4];
+        uint32_t hl[4], hr[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          const uint32_t i = i0 + (uint32_t)r;
+          const uint32_t c = i < u ? hash61(coef.a[i], coef.b[i], aip) & geo.vmask : 0u;
+          const size_t se = (size_t)i * geo.v + c;
+          xl[r] = se * geo.gl + jl;
+          xr[r] = se * geo.g + jr;
+          hl[r] = i < u ? bit_peek(le, xl[r]) : ~0u;
+          hr[r] = (i < u && samp) ? bit_peek(re, xr[r]) : ~0u;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          if (!((hl[r] >> (xl[r] & 31u)) & 1u)) dr_set<CellT>(le, xl[r], code);
+          if (!((hr[r] >> (xr[r] & 31u)) & 1u)) dr_set<CellT>(re, xr[r], code);
+        }
+      }
+    } else {
 #pragma unroll 4
-    for (uint32_t i = 0; i < u; i++) {
-      const uint32_t c = hash61(coef.a[i], coef.b[i], aip) & geo.vmask;
-      const size_t se = (size_t)i * geo.v + c;
-      le[se * geo.gl + jl] = code;
-      if (samp) re[se * geo.g + jr] = code;
+      for (uint32_t i = 0; i < u; i++) {
+        const uint32_t c = hash61(coef.a[i], coef.b[i], aip) & geo.vmask;
+        const size_t se = (size_t)i * geo.v + c;
+        dr_set<CellT>(le, se * geo.gl + jl, code);
+        if (samp) dr_set<CellT>(re, se * geo.g + jr, code);
+      }
     }
   }
   const unsigned sm = __ballot_sync(kFull, samp);
@@ -207,6 +232,7 @@ __device__ __forceinline__ void load_pairs(const uint32_t* __restrict__ pairs, u
 template <typename CellT>
 __device__ __forceinline__ uint32_t count_in_window(uint32_t word, uint32_t lo, uint32_t len, bool wrap,
                                                     uint32_t hi) {
+  if constexpr (kIsBit<CellT>) return (uint32_t)__popc(word);  // the window is the open slice
   constexpr int kCells = 4 / (int)sizeof(CellT);
   constexpr int kBits = 8 * (int)sizeof(CellT);
   constexpr uint32_t kMask = (1u << kBits) - 1u;
@@ -222,12 +248,14 @@ __device__ __forceinline__ uint32_t count_in_window(uint32_t word, uint32_t lo, 
 // Nonzero iff some cell of the word equals the splatted stamp (exact zero-cell test).
 template <typename CellT>
 __device__ __forceinline__ uint32_t has_stamp(uint32_t word, uint32_t asplat) {
+  if constexpr (kIsBit<CellT>) return word;  // every set bit carries the open slice's stamp
   const uint32_t x = word ^ asplat;
   return sizeof(CellT) == 1 ? ((x - 0x01010101u) & ~x & 0x80808080u) : ((x - 0x00010001u) & ~x & 0x80008000u);
 }
 
 template <typename CellT>
 __device__ __forceinline__ uint32_t clear_stamp(uint32_t word, uint32_t alias) {
+  if constexpr (kIsBit<CellT>) return 0u;
   constexpr int kCells = 4 / (int)sizeof(CellT);
   constexpr int kBits = 8 * (int)sizeof(CellT);
   constexpr uint32_t kMask = (1u << kBits) - 1u;

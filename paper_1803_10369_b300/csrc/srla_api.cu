@@ -84,6 +84,14 @@ int cuda_err(cudaError_t e) {
     if (_r != SRLA_OK) return _r;         \
   } while (0)
 
+// Calls f with a value of the handle's recorder storage type (one-bit, 8-bit or 16-bit).
+template <typename F>
+int with_cells(uint32_t dr_bytes, F&& f) {
+  if (dr_bytes == 1) return f(uint8_t{});
+  if (dr_bytes == 2) return f(uint16_t{});
+  return f(Bit{});
+}
+
 int grid_for(uint64_t items, int per_block, int cap) {
   const uint64_t b = (items + per_block - 1) / per_block;
   return (int)std::max<uint64_t>(1, std::min<uint64_t>(b, (uint64_t)cap));
@@ -107,7 +115,7 @@ int launch_scan(srla_t* h, const uint32_t* pairs, uint64_t n) {
 template <typename CellT>
 int launch_sweep(srla_t* h, int census, int reset, int after_close) {
   const size_t cells_max = (size_t)h->p.v * std::max(h->p.g, h->p.gl);
-  const size_t nvec = cells_max * sizeof(CellT) / 16;
+  const size_t nvec = cell_array_bytes<CellT>(cells_max) / 16;
   const int gx = grid_for(nvec, 256, std::max(1, h->sms * 8 / (int)(2 * h->p.u)));
   h->launches++;
   k_sweep<CellT><<<dim3(gx, 2 * h->p.u), 256, 0, h->st>>>(h->geo, h->at<CellT>(h->L.re), h->at<CellT>(h->L.le),
@@ -199,7 +207,7 @@ int capture_graphs(srla_t* h) {
       rc = SRLA_E_CUDA;
       break;
     }
-    rc = h->p.dr_bytes == 1 ? enqueue_end_slice<uint8_t>(h, q) : enqueue_end_slice<uint16_t>(h, q);
+    rc = with_cells(h->p.dr_bytes, [&](auto c) { return enqueue_end_slice<decltype(c)>(h, q); });
     const cudaError_t e = cudaStreamEndCapture(h->st, &g);
     if (rc == SRLA_OK && e != cudaSuccess) rc = SRLA_E_CUDA;
     if (rc == SRLA_OK && cudaGraphInstantiate(&h->graph[q], g, 0) != cudaSuccess) rc = SRLA_E_CUDA;
@@ -224,15 +232,14 @@ int reset_tables(srla_t* h, bool all) {
 // Resident blocks per SM of the scan, and the cooperative sort's grid (all co-resident).
 int occupancy(srla_t* h) {
   int a = 0, b = 0, c = 0;
-  const bool one = h->p.dr_bytes == 1;
-  if ((one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_scan<uint8_t, false>, kScanThreads, 0)
-           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_scan<uint16_t, false>, kScanThreads, 0)) !=
-      cudaSuccess)
-    return SRLA_E_CUDA;
-  if ((one ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan<uint8_t, true>, kScanThreads, 0)
-           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan<uint16_t, true>, kScanThreads, 0)) !=
-      cudaSuccess)
-    return SRLA_E_CUDA;
+  const int rs = with_cells(h->p.dr_bytes, [&](auto cell) {
+    using CellT = decltype(cell);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_scan<CellT, false>, kScanThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan<CellT, true>, kScanThreads, 0) != cudaSuccess)
+      return SRLA_E_CUDA;
+    return SRLA_OK;
+  });
+  if (rs != SRLA_OK) return rs;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&c, k_sort, kSortThreads, kSortSmallSmem) != cudaSuccess || c < 1)
     return SRLA_E_CUDA;
   h->occ_scan[0] = std::max(1, a);
@@ -351,7 +358,7 @@ int srla_push_packets(srla_t* h, const uint32_t* pairs, uint64_t n_pairs, int on
   if (!h || (!pairs && n_pairs)) return SRLA_E_INVAL;
   if (n_pairs == 0) return SRLA_OK;
   auto scan = [&](const uint32_t* src, uint64_t n) {
-    return h->p.dr_bytes == 1 ? launch_scan<uint8_t>(h, src, n) : launch_scan<uint16_t>(h, src, n);
+    return with_cells(h->p.dr_bytes, [&](auto c) { return launch_scan<decltype(c)>(h, src, n); });
   };
   if (on_device) {
     const int r = scan(pairs, n_pairs);
@@ -390,7 +397,7 @@ int srla_end_slice(srla_t* h, uint64_t* slice_id) {
     SRLA_TRY(cudaGraphLaunch(h->graph[q], h->st));
     h->launches += h->graph_launches;
   } else {
-    const int r = h->p.dr_bytes == 1 ? enqueue_end_slice<uint8_t>(h, q) : enqueue_end_slice<uint16_t>(h, q);
+    const int r = with_cells(h->p.dr_bytes, [&](auto c) { return enqueue_end_slice<decltype(c)>(h, q); });
     if (r != SRLA_OK) return r;
   }
   SRLA_TRY(cudaEventRecord(s.ev, h->st));
@@ -472,14 +479,14 @@ namespace {
 
 template <typename CellT>
 int export_cells(srla_t* h, size_t off, size_t n, uint16_t* dst) {
-  // decode through the staging area, one chunk at a time
-  const size_t chunk = h->L.staging_pkts * 8 / 2;  // uint16 per chunk
+  // decode through the staging area, one chunk (a multiple of 32 recorders) at a time
+  const size_t chunk = (h->L.staging_pkts * 8 / 2) & ~(size_t)31;  // uint16 per chunk
   uint16_t* stage = h->at<uint16_t>(h->L.staging);
   for (size_t x = 0; x < n; x += chunk) {
     const size_t m = std::min(chunk, n - x);
     h->launches++;
-    k_decode<CellT><<<grid_for(m, 256, h->sms * 8), 256, 0, h->st>>>(h->at<CellT>(off) + x, stage, m, h->ctl(),
-                                                                      h->geo.P);
+    k_decode<CellT><<<grid_for(m, 256, h->sms * 8), 256, 0, h->st>>>(cells_from(h->at<CellT>(off), x), stage, m,
+                                                                      h->ctl(), h->geo.P);
     SRLA_TRY(cudaGetLastError());
     SRLA_TRY(cudaMemcpyAsync(dst + x, stage, m * 2, cudaMemcpyDeviceToHost, h->st));
     SRLA_TRY(cudaStreamSynchronize(h->st));
@@ -489,14 +496,14 @@ int export_cells(srla_t* h, size_t off, size_t n, uint16_t* dst) {
 
 template <typename CellT>
 int import_cells(srla_t* h, size_t off, size_t n, const uint16_t* src, uint32_t tm) {
-  const size_t chunk = h->L.staging_pkts * 8 / 2;
+  const size_t chunk = (h->L.staging_pkts * 8 / 2) & ~(size_t)31;
   uint16_t* stage = h->at<uint16_t>(h->L.staging);
   for (size_t x = 0; x < n; x += chunk) {
     const size_t m = std::min(chunk, n - x);
     SRLA_TRY(cudaMemcpyAsync(stage, src + x, m * 2, cudaMemcpyHostToDevice, h->st));
     h->launches++;
-    k_encode<CellT><<<grid_for(m, 256, h->sms * 8), 256, 0, h->st>>>(stage, h->at<CellT>(off) + x, m, tm,
-                                                                      h->geo.P);
+    k_encode<CellT><<<grid_for(m, 256, h->sms * 8), 256, 0, h->st>>>(stage, cells_from(h->at<CellT>(off), x), m,
+                                                                      tm, h->geo.P);
     SRLA_TRY(cudaGetLastError());
     SRLA_TRY(cudaStreamSynchronize(h->st));
   }
@@ -523,9 +530,9 @@ int srla_export_state(srla_t* h, void* host_buf, size_t cap) {
   std::memcpy(b, &hd, sizeof(hd));
   uint16_t* dre = reinterpret_cast<uint16_t*>(b + sizeof(hd));
   uint16_t* dle = dre + nre;
-  int r = p.dr_bytes == 1 ? export_cells<uint8_t>(h, h->L.re, nre, dre) : export_cells<uint16_t>(h, h->L.re, nre, dre);
+  int r = with_cells(p.dr_bytes, [&](auto c) { return export_cells<decltype(c)>(h, h->L.re, nre, dre); });
   if (r != SRLA_OK) return r;
-  r = p.dr_bytes == 1 ? export_cells<uint8_t>(h, h->L.le, nle, dle) : export_cells<uint16_t>(h, h->L.le, nle, dle);
+  r = with_cells(p.dr_bytes, [&](auto c) { return export_cells<decltype(c)>(h, h->L.le, nle, dle); });
   if (r != SRLA_OK) return r;
   uint32_t* carry = reinterpret_cast<uint32_t*>(dle + nle);
   if (nc) {
@@ -557,11 +564,9 @@ int srla_import_state(srla_t* h, const void* host_buf, size_t len) {
   const uint32_t tm = (uint32_t)(h->T % h->geo.P);
   const uint16_t* sre = reinterpret_cast<const uint16_t*>(static_cast<const char*>(host_buf) + sizeof(hd));
   const uint16_t* sle = sre + nre;
-  r = p.dr_bytes == 1 ? import_cells<uint8_t>(h, h->L.re, nre, sre, tm)
-                      : import_cells<uint16_t>(h, h->L.re, nre, sre, tm);
+  r = with_cells(p.dr_bytes, [&](auto c) { return import_cells<decltype(c)>(h, h->L.re, nre, sre, tm); });
   if (r != SRLA_OK) return r;
-  r = p.dr_bytes == 1 ? import_cells<uint8_t>(h, h->L.le, nle, sle, tm)
-                      : import_cells<uint16_t>(h, h->L.le, nle, sle, tm);
+  r = with_cells(p.dr_bytes, [&](auto c) { return import_cells<decltype(c)>(h, h->L.le, nle, sle, tm); });
   if (r != SRLA_OK) return r;
   if (hd.n_carry) {
     const uint32_t* carry = reinterpret_cast<const uint32_t*>(sle + nle);
@@ -703,7 +708,7 @@ extern "C" int srla_batch_report_static(const srla_params* p, const uint32_t* d_
   c.w_star = h.geo.gl + 1;
   c.pair_mode = 1;
   SRLA_TRY(cudaMemcpyAsync(h.ctl(), &c, sizeof(Ctl), cudaMemcpyHostToDevice, h.st));
-  r = q.dr_bytes == 1 ? static_batch<uint8_t>(&h, d_pairs, n_pairs) : static_batch<uint16_t>(&h, d_pairs, n_pairs);
+  r = with_cells(q.dr_bytes, [&](auto c) { return static_batch<decltype(c)>(&h, d_pairs, n_pairs); });
   if (r != SRLA_OK) return r;
 
   const int par = (int)(h.T & 1);

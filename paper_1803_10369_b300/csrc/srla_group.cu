@@ -224,7 +224,8 @@ int rebuild_work(srla_group_t* g) {
     if (!s.active) continue;
     n_links = l + 1;
     const srla_params& p = s.p;
-    const uint64_t le_vecs = (uint64_t)p.v * p.gl * p.dr_bytes / 16, re_vecs = (uint64_t)p.v * p.g * p.dr_bytes / 16;
+    const uint64_t le_vecs = recorder_bytes(&p, (uint64_t)p.v * p.gl) / 16,
+                   re_vecs = recorder_bytes(&p, (uint64_t)p.v * p.g) / 16;
     const bool kP = p.k == (1u << p.z) - 1u;
     add_rows(chunks, l, 0, p.u, le_vecs);
     if (!kP) add_rows(chunks, l, 1, p.u, re_vecs);

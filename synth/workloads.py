@@ -95,7 +95,15 @@ PAPER_OWN = Workload(
     max_sampled=1 << 18, max_candidates=1 << 18,
 )
 
-WORKLOADS = {"tiny": TINY, "paper": PAPER, "longwin": LONGWIN, "paperown": PAPER_OWN}
+# The paper's discrete-window regime (Section 5: z = 1, k = 1) at its own sketch sizes, with
+# one-bit recorders packed 32 to a word (33 MiB of recorders instead of 516 MiB at 16 bits).
+# Each slice is a whole window, so a planted host reaches its cardinality within one slice;
+# 60 planted hosts keep their packets near a fifth of the slice.
+DISCRETE = PAPER_OWN.replace(
+    name="discrete-1link-u4-v65536-g8-gl1024-z1-k1-bits-4.5Mpps", dr_bytes=0, z=1, k=1, n_slices=16,
+    n_planted=60, planted_spread=1, churn_run=(1, 4))
+
+WORKLOADS = {"tiny": TINY, "paper": PAPER, "longwin": LONGWIN, "paperown": PAPER_OWN, "discrete": DISCRETE}
 
 
 def workload(name: str) -> Workload:

@@ -73,6 +73,20 @@ def test_param_validation():
     assert srla.check_params(_params(z=1, k=1)) == 0
 
 
+def test_one_bit_recorders():
+    """dr_bytes = 0 packs one-bit recorders (z = 1, the discrete window): valid only with z = 1,
+    rows of at least 128 recorders, and 1/8 of the recorder bytes of 1-byte cells."""
+    one = _params(dr_bytes=0, z=1, k=1)
+    assert srla.check_params(one) == 0
+    for kw in (dict(z=2, k=1), dict(z=1, k=2), dict(g=2, gl=64), dict(v=16, g=4, gl=64)):
+        assert srla.check_params(_params(dr_bytes=0, **{"z": 1, "k": 1, **kw})) == srla.E_INVAL, kw
+    big = dict(u=4, v=1 << 16, g=8, gl=1024, z=1, k=1)
+    bits = srla.workspace_bytes(_params(dr_bytes=0, **big))
+    bytes1 = srla.workspace_bytes(_params(dr_bytes=1, **big))
+    cells = 4 * (1 << 16) * (8 + 1024)
+    assert bytes1 - bits == cells - cells // 8
+
+
 def test_workspace_grows_with_sketch():
     small = srla.workspace_bytes(_params())
     big = srla.workspace_bytes(_params(v=1 << 14, gl=256, g=128, u=8, dr_bytes=2, z=16, k=300))

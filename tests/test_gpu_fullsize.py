@@ -59,3 +59,11 @@ def test_paper_own_parameters(cuda_device):
     w = synth.workload("paperown").replace(planted_spread=3)
     n_cand = _run(w, 4, cuda_device, state_every=2)
     assert n_cand >= 100
+
+
+def test_discrete_window_one_bit_recorders(cuda_device):
+    """The discrete window (z=1, k=1) at the paper's own sketch sizes with one-bit recorders:
+    every slice starts from empty recorders and nothing is carried."""
+    w = synth.workload("discrete")
+    n_cand = _run(w, 3, cuda_device, state_every=1)
+    assert n_cand >= 40

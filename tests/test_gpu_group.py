@@ -27,6 +27,7 @@ def _links():
         (TINY.replace(u=2, v=256, g=32, gl=128, dr_bytes=2, z=12, k=100, theta=64, seed=23,
                       pkts_per_slice=50_000), {"pair_slots_log2": -1}),
         (TINY.replace(z=1, k=1, seed=24, pkts_per_slice=40_000), {}),
+        (TINY.replace(dr_bytes=0, z=1, k=1, g=8, gl=256, seed=25, pkts_per_slice=40_000), {}),
         (many, {}),
     ]
 

@@ -31,6 +31,11 @@ VARIANTS = {
     "paper-g8": TINY.replace(g=8, gl=256, dr_bytes=2, z=16, k=6),
     "tag-wrap-2^31": TINY.replace(start_slice=(1 << 31) - 5),
     "slice-wrap-2^64": TINY.replace(start_slice=(1 << 64) - 6),
+    # one-bit recorders packed 32 to a word (z = 1, k = 1); runs of 8 and of 4/16 recorders
+    # share words, runs of 64 and 1024 span whole words
+    "bits-discrete": TINY.replace(dr_bytes=0, z=1, k=1),
+    "bits-g8-gl1024": TINY.replace(dr_bytes=0, z=1, k=1, g=8, gl=1024, theta=128),
+    "bits-u3-g4-gl16": TINY.replace(dr_bytes=0, z=1, k=1, u=3, g=4, gl=16, theta=64),
 }
 
 

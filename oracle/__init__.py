@@ -71,6 +71,8 @@ def _load():
             "orc_hash_many": (None, [P, i32, P, sz, P]),
             "orc_ure_count": (u32, [P, u32, u32]),
             "orc_ule_count": (u32, [P, u32, u32]),
+            "orc_set_inline": (i32, [P, i32]),
+            "orc_get_si": (None, [P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(lib, name)
@@ -122,7 +124,7 @@ def estimate(gl: int, up: float, w: float) -> tuple[float, int]:
 class Oracle:
     """One monitored link: the sliding estimator array and its candidate lists."""
 
-    def __init__(self, u, v, g, gl, z, k, theta, ha, hb, start_slice=0):
+    def __init__(self, u, v, g, gl, z, k, theta, ha, hb, start_slice=0, inline=False):
         self._lib = _load()
         self.u, self.v, self.g, self.gl, self.z, self.k, self.theta = u, v, g, gl, z, k, theta
         ha = np.ascontiguousarray(ha, dtype=np.uint64)
@@ -132,10 +134,13 @@ class Oracle:
         self._h = self._lib.orc_create(u, v, g, gl, z, k, theta, _ptr(ha), _ptr(hb), start_slice)
         if not self._h:
             raise ValueError("invalid oracle parameters")
+        self.inline = bool(inline)
+        if self.inline and self._lib.orc_set_inline(self._h, 1) != 0:
+            raise MemoryError("oracle inline mode")
 
     @classmethod
-    def for_workload(cls, w, ha, hb):
-        return cls(w.u, w.v, w.g, w.gl, w.z, w.k, w.theta, ha, hb, w.start_slice)
+    def for_workload(cls, w, ha, hb, inline=False):
+        return cls(w.u, w.v, w.g, w.gl, w.z, w.k, w.theta, ha, hb, w.start_slice, inline=inline)
 
     def close(self):
         if getattr(self, "_h", None):
@@ -204,6 +209,12 @@ class Oracle:
         carry = np.ascontiguousarray(carry, np.uint32)
         if self._lib.orc_set_state(self._h, _ptr(re), _ptr(le), T, _ptr(carry), carry.size) != 0:
             raise MemoryError("oracle set_state")
+
+    def si(self) -> np.ndarray:
+        """Super point indicator bits (inline mode): si[u, v] as uint16."""
+        out = np.zeros((self.u, self.v), np.uint16)
+        self._lib.orc_get_si(self._h, _ptr(out))
+        return out
 
     def hash(self, role: int, x) -> np.ndarray:
         x = np.ascontiguousarray(x, dtype=np.uint32).ravel()

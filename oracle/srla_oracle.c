@@ -29,6 +29,13 @@
  *   R5  Eq. 9 edges: w <= g'*UP gives 0; w == g' (or UP == 1) gives +infinity, flagged
  *       saturated; the super point test is est >= theta (Definition 2).
  *   R6  carried hosts (Algorithm 3) join the next slice's candidate list unconditionally.
+ *  R11  inline mode (orc_set_inline): the candidate test of Algorithm 2 as printed, run at
+ *       packet time after the SRE update, with the 16 super point indicator bits SI of
+ *       Section 4.1 suppressing repeats.  The SI bit of a host is chosen from aip (the paper
+ *       names H3(aip), H4(aip) and H4(bip) in different places; hashing bip would let one
+ *       host in many times): bits 28..31 of the sampling-role hash applied to aip.  The
+ *       threshold is ceil(rho*g) as in R4.  SI is cleared at every slice end and set again
+ *       for the carried hosts (Algorithm 3).  The result depends on packet order.
  */
 #include <math.h>
 #include <stdint.h>
@@ -57,6 +64,11 @@ typedef struct orc {
   size_t ns, caps;
   uint32_t *carry; /* NCSIP of the previous slice end (Algorithm 3), ascending */
   size_t ncarry;
+  /* inline mode (R11) */
+  int inline_mode;
+  uint16_t *si;     /* SI[i][c]: 16 super point indicator bits per estimator */
+  uint32_t *ins;    /* hosts inserted into CSIP by the scan in the open slice */
+  size_t nins, capins;
   /* results of the last slice end */
   uint64_t cnt[ORC_MAX_ROWS];
   double up;
@@ -150,8 +162,34 @@ static void orc_free_report(orc *o) {
 void orc_destroy(orc *o) {
   if (!o) return;
   orc_free_report(o);
-  free(o->re); free(o->le); free(o->s); free(o->carry);
+  free(o->re); free(o->le); free(o->s); free(o->carry); free(o->si); free(o->ins);
   free(o);
+}
+
+/* R11: the SI bit of host aip. */
+static uint32_t si_index(const orc *o, uint32_t aip) { return orc_hash(o, (int)o->u + 2, aip) >> 28; }
+
+/* Set the SI bit of aip in each of its u estimators. */
+static void si_mark(orc *o, uint32_t aip) {
+  uint32_t b = si_index(o, aip);
+  for (uint32_t i = 0; i < o->u; i++) {
+    uint32_t c = orc_hash(o, (int)i, aip) & (o->v - 1);
+    o->si[(size_t)i * o->v + c] |= (uint16_t)(1u << b);
+  }
+}
+
+/* Switch to the inline candidate test (R11) before the first packet; the SI bits start
+   clear, then hold the bits of the carried hosts.  Returns 0, or -1 without memory. */
+int orc_set_inline(orc *o, int on) {
+  o->inline_mode = on ? 1 : 0;
+  if (!on) return 0;
+  if (!o->si) {
+    o->si = (uint16_t *)calloc((size_t)o->u * o->v, sizeof(uint16_t));
+    if (!o->si) return -1;
+  }
+  memset(o->si, 0, (size_t)o->u * o->v * sizeof(uint16_t));
+  for (size_t x = 0; x < o->ncarry; x++) si_mark(o, o->carry[x]);
+  return 0;
 }
 
 static size_t re_at(const orc *o, uint32_t i, uint32_t c, uint32_t j) {
@@ -160,6 +198,8 @@ static size_t re_at(const orc *o, uint32_t i, uint32_t c, uint32_t j) {
 static size_t le_at(const orc *o, uint32_t i, uint32_t c, uint32_t j) {
   return ((size_t)i * o->v + c) * o->gl + j;
 }
+
+uint32_t orc_ure_count(const orc *o, uint32_t aip, uint32_t limit);
 
 /* -------------------------------------------------------------- the scan ---------- */
 
@@ -188,6 +228,29 @@ int orc_push(orc *o, const uint32_t *pairs, size_t n) {
         o->caps = nc;
       }
       o->s[o->ns++] = aip;
+      if (o->inline_mode) {
+        /* Algorithm 2: the host is tested by its union SRE right after the update, and
+           inserted into CSIP unless its SI bit is already set in all u estimators. */
+        if (orc_ure_count(o, aip, o->k) >= o->rho_g) {
+          uint32_t b = si_index(o, aip);
+          uint16_t usi = 0xFFFFu; /* USI: AND over the rows (Algorithm 1) */
+          for (uint32_t i = 0; i < o->u; i++) {
+            uint32_t c = orc_hash(o, (int)i, aip) & (o->v - 1);
+            usi &= o->si[(size_t)i * o->v + c];
+          }
+          if (!((usi >> b) & 1u)) {
+            if (o->nins == o->capins) {
+              size_t nc = o->capins ? 2 * o->capins : 256;
+              uint32_t *ni = (uint32_t *)realloc(o->ins, nc * sizeof(uint32_t));
+              if (!ni) return -1;
+              o->ins = ni;
+              o->capins = nc;
+            }
+            o->ins[o->nins++] = aip;
+            si_mark(o, aip);
+          }
+        }
+      }
     }
   }
   return 0;
@@ -263,14 +326,20 @@ long orc_end_slice(orc *o) {
   for (uint32_t i = 0; i < u; i++) up *= (double)o->cnt[i] / ((double)gl * (double)v);
   o->up = up;
 
-  /* New candidates (R4): sampled hosts of this slice passing the union SRE test now. */
+  /* New candidates (R4): sampled hosts of this slice passing the union SRE test now.  In
+     inline mode (R11) they are the hosts the scan inserted. */
   size_t nsu = sort_unique(o->s, o->ns);
   o->nsu = nsu;
-  uint32_t *newc = (uint32_t *)malloc((nsu ? nsu : 1) * sizeof(uint32_t));
+  uint32_t *newc = (uint32_t *)malloc(((nsu > o->nins ? nsu : o->nins) + 1) * sizeof(uint32_t));
   if (!newc) return -1;
   size_t nnew = 0;
-  for (size_t x = 0; x < nsu; x++)
-    if (orc_ure_count(o, o->s[x], k) >= o->rho_g) newc[nnew++] = o->s[x];
+  if (o->inline_mode) {
+    for (size_t x = 0; x < o->nins; x++) newc[nnew++] = o->ins[x];
+    nnew = sort_unique(newc, nnew);
+  } else {
+    for (size_t x = 0; x < nsu; x++)
+      if (orc_ure_count(o, o->s[x], k) >= o->rho_g) newc[nnew++] = o->s[x];
+  }
   o->nnew = nnew;
 
   /* Candidate list: union of the new candidates and the carried list (R6), ascending. */
@@ -318,7 +387,9 @@ long orc_end_slice(orc *o) {
     o->rep_flags[x] = f;
   }
 
-  /* Algorithm 3: DRslide on every recorder of the SRE and SLE arrays. */
+  /* Algorithm 3: clear every SI (inline mode), DRslide on every recorder of the SRE and
+     SLE arrays. */
+  if (o->inline_mode) memset(o->si, 0, (size_t)u * v * sizeof(uint16_t));
   for (size_t x = 0; x < (size_t)u * v * g; x++)
     if (o->re[x] < o->dmax) o->re[x]++;
   for (size_t x = 0; x < (size_t)u * v * gl; x++)
@@ -330,9 +401,13 @@ long orc_end_slice(orc *o) {
   if (!o->carry) return -1;
   o->ncarry = 0;
   for (size_t x = 0; x < n; x++)
-    if (orc_ure_count(o, o->rep_aip[x], k) >= o->rho_g) o->carry[o->ncarry++] = o->rep_aip[x];
+    if (orc_ure_count(o, o->rep_aip[x], k) >= o->rho_g) {
+      o->carry[o->ncarry++] = o->rep_aip[x];
+      if (o->inline_mode) si_mark(o, o->rep_aip[x]);
+    }
 
   o->ns = 0;
+  o->nins = 0;
   o->T++;
   return (long)n;
 }
@@ -389,7 +464,13 @@ int orc_set_state(orc *o, const uint16_t *re, const uint16_t *le, uint64_t T,
   memcpy(o->carry, carry, ncarry * sizeof(uint32_t));
   o->ncarry = ncarry;
   o->ns = 0;
-  return 0;
+  o->nins = 0;
+  return o->inline_mode ? orc_set_inline(o, 1) : 0;
+}
+
+/* The SI bits (inline mode), u*v uint16. */
+void orc_get_si(const orc *o, uint16_t *out) {
+  if (o->si) memcpy(out, o->si, (size_t)o->u * o->v * sizeof(uint16_t));
 }
 
 /* Hash a batch of values with one role (tests build brute-force sets from it). */

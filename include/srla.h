@@ -44,6 +44,15 @@ extern "C" {
 #define SRLA_CARRIED 4u             /* carried from the previous slice end (Algorithm 3) */
 #define SRLA_NEW 8u                 /* sampled in this slice and passing the union SRE test */
 
+/* Candidate rules (srla_params.mode). */
+#define SRLA_MODE_ORDER_FREE 0u     /* a host sampled in the slice is a new candidate iff its
+                                       union SRE passes at the end of the slice; exact,
+                                       independent of packet order */
+#define SRLA_MODE_INLINE 1u         /* Algorithm 2 as printed: the union SRE test runs at packet
+                                       time and the 16 super point indicator bits of Section 4.1
+                                       suppress repeats; depends on packet order (parallel
+                                       threads race), single links only */
+
 /*
  * Parameters (Sections 3.2, 4.1, 5).  v, g and gl must be powers of two.
  *   u, v        rows and columns of the sliding estimator array (u <= SRLA_MAX_ROWS)
@@ -62,6 +71,11 @@ extern "C" {
  *   pair_slots_log2 size of the per-slice table of scanned pairs that lets the scan skip a
  *               pair already scanned in the open slice (it writes the same stamps): 0 gives
  *               2^21 slots, -1 disables the table, 10..28 choose 2^value slots (8 bytes each)
+ *   mode        SRLA_MODE_ORDER_FREE (0) or SRLA_MODE_INLINE (1).  In the inline mode the SI
+ *               bit of a host is bits 28..31 of the sampling-role hash applied to aip, the
+ *               SI bits are cleared at each slice end and set again for the carried hosts
+ *               (Algorithm 3), pairs are not de-duplicated within the slice (each packet
+ *               runs the test), and the slice statistics count no sampled hosts.
  *   hash_a, hash_b  coefficients of the hash family h(x) = (a*x + b) mod (2^61 - 1), one
  *               pair per role: rows 0..u-1 (column of aip in row i), u (SLE cell of bip),
  *               u+1 (SRE cell of bip), u+2 (sampling hash of bip); a in [1, 2^61-2],
@@ -76,7 +90,7 @@ typedef struct srla_params {
   uint64_t staging_pkts;
   uint32_t max_sampled, max_candidates;
   int32_t pair_slots_log2;
-  uint32_t reserved;
+  uint32_t mode;
   uint64_t hash_a[SRLA_N_HASH];
   uint64_t hash_b[SRLA_N_HASH];
 } srla_params;

@@ -315,42 +315,47 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t x) {
 // whose recorder is inside the window in every row i, i.e. whose DRjoin (max) over the u
 // rows is below lim.  One warp per host; lane i < u holds the column of row i in `mycol`.
 // Every lane runs the same number of trips (the shuffles need the whole warp).
-template <int WPL>
+// kFresh: the words may have been written by the running kernel (inline candidate test), so
+// they are read through L2 instead of the read-only path.
+template <int WPL, bool kFresh = false>
 __device__ __forceinline__ void load_words(const uint32_t* run, uint32_t w0, uint32_t wd[WPL]) {
   if constexpr (WPL == 4) {
-    const uint4 q4 = __ldg(reinterpret_cast<const uint4*>(run + w0));
+    const uint4* p = reinterpret_cast<const uint4*>(run + w0);
+    const uint4 q4 = kFresh ? __ldcg(p) : __ldg(p);
     wd[0] = q4.x; wd[1] = q4.y; wd[2] = q4.z; wd[3] = q4.w;
   } else if constexpr (WPL == 2) {
-    const uint2 q2 = __ldg(reinterpret_cast<const uint2*>(run + w0));
+    const uint2* p = reinterpret_cast<const uint2*>(run + w0);
+    const uint2 q2 = kFresh ? __ldcg(p) : __ldg(p);
     wd[0] = q2.x; wd[1] = q2.y;
   } else {
-    wd[0] = __ldg(run + w0);
+    wd[0] = kFresh ? __ldcg(run + w0) : __ldg(run + w0);
   }
 }
 
 // Words w0.. of the run of estimator (row i, column c); a one-bit run shorter than a word is
 // returned in wd[0], shifted down, to the lane with w0 = 0.
-template <typename CellT, int WPL>
+template <typename CellT, int WPL, bool kFresh = false>
 __device__ __forceinline__ void load_run(const CellT* __restrict__ arr, uint32_t v, uint32_t cells, uint32_t i,
                                          uint32_t c, uint32_t w0, uint32_t wd[WPL]) {
   const size_t se = (size_t)i * v + c;
   if constexpr (kIsBit<CellT>) {
     const uint32_t* words = reinterpret_cast<const uint32_t*>(arr);
     if (cells >= 32u) {
-      load_words<WPL>(words + se * (cells / 32u), w0, wd);
+      load_words<WPL, kFresh>(words + se * (cells / 32u), w0, wd);
     } else {
       const size_t bit = se * cells;
-      wd[0] = (__ldg(words + (bit >> 5)) >> (bit & 31u)) & ((1u << cells) - 1u);
+      const uint32_t word = kFresh ? __ldcg(words + (bit >> 5)) : __ldg(words + (bit >> 5));
+      wd[0] = (word >> (bit & 31u)) & ((1u << cells) - 1u);
 #pragma unroll
       for (int q = 1; q < WPL; q++) wd[q] = 0u;
     }
   } else {
-    load_words<WPL>(reinterpret_cast<const uint32_t*>(arr + se * cells), w0, wd);
+    load_words<WPL, kFresh>(reinterpret_cast<const uint32_t*>(arr + se * cells), w0, wd);
   }
 }
 
 // Rows are fetched four at a time, all loads in flight before any is used.
-template <typename CellT, int WPL>
+template <typename CellT, int WPL, bool kFresh = false>
 __device__ __forceinline__ uint32_t union_count_w(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
                                                   uint32_t u, uint32_t mycol, const Win& win, int lane) {
   const uint32_t R = run_words<CellT>(cells);
@@ -368,7 +373,7 @@ __device__ __forceinline__ uint32_t union_count_w(const CellT* __restrict__ arr,
       for (int r = 0; r < 4; r++) {
         const uint32_t i = i0 + (uint32_t)r;
         const uint32_t c = __shfl_sync(kFull, mycol, (int)(i & 31u));
-        if (ok && i < u) load_run<CellT, WPL>(arr, v, cells, i, c, w0, wd[r]);
+        if (ok && i < u) load_run<CellT, WPL, kFresh>(arr, v, cells, i, c, w0, wd[r]);
       }
 #pragma unroll
       for (int r = 0; r < 4; r++)
@@ -385,13 +390,13 @@ __device__ __forceinline__ uint32_t union_count_w(const CellT* __restrict__ arr,
   return cells_of_bits<CellT>(warp_sum(total));
 }
 
-template <typename CellT>
+template <typename CellT, bool kFresh = false>
 __device__ __forceinline__ uint32_t union_count(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
                                                 uint32_t u, uint32_t mycol, const Win& win, int lane) {
   const uint32_t R = run_words<CellT>(cells);
-  if (R >= 128) return union_count_w<CellT, 4>(arr, v, cells, u, mycol, win, lane);
-  if (R >= 64) return union_count_w<CellT, 2>(arr, v, cells, u, mycol, win, lane);
-  return union_count_w<CellT, 1>(arr, v, cells, u, mycol, win, lane);
+  if (R >= 128) return union_count_w<CellT, 4, kFresh>(arr, v, cells, u, mycol, win, lane);
+  if (R >= 64) return union_count_w<CellT, 2, kFresh>(arr, v, cells, u, mycol, win, lane);
+  return union_count_w<CellT, 1, kFresh>(arr, v, cells, u, mycol, win, lane);
 }
 
 // Same count as union_count, for a caller that only needs to know whether it reaches
@@ -402,7 +407,7 @@ __device__ __forceinline__ uint32_t union_count(const CellT* __restrict__ arr, u
 // know whether each reaches `need`: rows are joined one at a time, and a host stops as soon
 // as fewer than `need` cells remain inside the window in every row so far (the union can
 // only shrink).  A count is exact when it is >= need; below need it is some value < need.
-template <typename CellT, int WPL>
+template <typename CellT, int WPL, bool kFresh = false>
 __device__ __forceinline__ void union_count_atleast2_w(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
                                                        uint32_t u, uint32_t col0, uint32_t col1, const Win& win,
                                                        uint32_t need, int lane, uint32_t& out0, uint32_t& out1) {
@@ -417,8 +422,8 @@ __device__ __forceinline__ void union_count_atleast2_w(const CellT* __restrict__
   for (uint32_t i = 0; i < u && (live0 || live1); i++) {
     const uint32_t c0 = __shfl_sync(kFull, col0, (int)i), c1 = __shfl_sync(kFull, col1, (int)i);
     uint32_t wd0[WPL], wd1[WPL];
-    if (ok && live0) load_run<CellT, WPL>(arr, v, cells, i, c0, w0, wd0);
-    if (ok && live1) load_run<CellT, WPL>(arr, v, cells, i, c1, w0, wd1);
+    if (ok && live0) load_run<CellT, WPL, kFresh>(arr, v, cells, i, c0, w0, wd0);
+    if (ok && live1) load_run<CellT, WPL, kFresh>(arr, v, cells, i, c1, w0, wd1);
     uint32_t p0 = 0, p1 = 0;
 #pragma unroll
     for (int q = 0; q < WPL; q++) {
@@ -438,16 +443,19 @@ __device__ __forceinline__ void union_count_atleast2_w(const CellT* __restrict__
   }
 }
 
-template <typename CellT>
+template <typename CellT, bool kFresh = false>
 __device__ __forceinline__ void union_count_atleast2(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
                                                      uint32_t u, uint32_t col0, uint32_t col1, const Win& win,
                                                      uint32_t need, int lane, uint32_t& out0, uint32_t& out1) {
   const uint32_t R = run_words<CellT>(cells);
-  if (R <= 32) return union_count_atleast2_w<CellT, 1>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
-  if (R <= 64) return union_count_atleast2_w<CellT, 2>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
-  if (R <= 128) return union_count_atleast2_w<CellT, 4>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
-  out0 = union_count<CellT>(arr, v, cells, u, col0, win, lane);
-  out1 = union_count<CellT>(arr, v, cells, u, col1, win, lane);
+  if (R <= 32)
+    return union_count_atleast2_w<CellT, 1, kFresh>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
+  if (R <= 64)
+    return union_count_atleast2_w<CellT, 2, kFresh>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
+  if (R <= 128)
+    return union_count_atleast2_w<CellT, 4, kFresh>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
+  out0 = union_count<CellT, kFresh>(arr, v, cells, u, col0, win, lane);
+  out1 = union_count<CellT, kFresh>(arr, v, cells, u, col1, win, lane);
 }
 
 }  // namespace srla

@@ -28,7 +28,7 @@ inline uint64_t next_pow2(uint64_t x) {
 
 struct Layout {
   size_t ctl, re, le, staging, utab, ulist, ctab[2], cflags[2], clist[2], sort_tmp, sort_hist, lut_est,
-      lut_flags, rep_stats[2], rep_entries[2], ptab, total;
+      lut_flags, rep_stats[2], rep_entries[2], ptab, si[2], total;
   uint64_t staging_pkts;
   uint32_t umask, cmask, ntiles, pmask;
   bool pairs;  // per-slice pair table present
@@ -69,6 +69,7 @@ inline int check(const srla_params* p) {
   if (p->max_candidates < 1 || p->max_candidates > (1u << 26)) return SRLA_E_INVAL;
   if (p->pair_slots_log2 != 0 && p->pair_slots_log2 != -1 && (p->pair_slots_log2 < 10 || p->pair_slots_log2 > 28))
     return SRLA_E_INVAL;
+  if (p->mode != SRLA_MODE_ORDER_FREE && p->mode != SRLA_MODE_INLINE) return SRLA_E_INVAL;
   for (uint32_t r = 0; r < p->u + 3; r++) {
     if (p->hash_a[r] < 1 || p->hash_a[r] >= kP61) return SRLA_E_INVAL;
     if (p->hash_b[r] >= kP61) return SRLA_E_INVAL;
@@ -113,6 +114,8 @@ inline Layout layout_of(const srla_params* p) {
   const uint32_t plog = p->pair_slots_log2 > 0 ? (uint32_t)p->pair_slots_log2 : 21u;
   L.pmask = L.pairs ? (1u << plog) - 1u : 0u;
   L.ptab = take(L.pairs ? ((size_t)1 << plog) * 8 : 0);
+  // inline mode: one 32-bit word of super point indicator bits per estimator, by parity
+  for (int q = 0; q < 2; q++) L.si[q] = take(p->mode == SRLA_MODE_INLINE ? (size_t)p->u * p->v * 4 : 0);
   L.total = off;
   return L;
 }

@@ -8,23 +8,27 @@ namespace srla {
 
 // Packets are read as 16-byte vectors (two pairs) when the batch is 16-byte aligned.
 // Each warp iteration covers 128 packets: lane l holds packets 2l, 2l+1, 64+2l, 65+2l; the
-// next iteration's packets are loaded before the current ones are scanned.
-template <typename CellT, bool kVec>
-__global__ void __launch_bounds__(kScanThreads, 4) k_scan(const uint32_t* __restrict__ pairs, uint64_t n, Geo geo,
+// next iteration's packets are loaded before the current ones are scanned.  kInline: the
+// candidate test of Algorithm 2 runs at packet time (SRLA_MODE_INLINE); every packet is
+// scanned (no pair de-duplication), since each one runs the test on the SRE as it stands.
+template <typename CellT, bool kVec, bool kInline = false>
+__global__ void __launch_bounds__(kScanThreads, kInline ? 2 : 4) k_scan(const uint32_t* __restrict__ pairs, uint64_t n, Geo geo,
                                                           const __grid_constant__ Coef coef, CellT* __restrict__ re,
                                                           CellT* __restrict__ le, Ctl* __restrict__ ctl,
                                                           unsigned long long* __restrict__ utab, uint32_t umask,
                                                           uint32_t* __restrict__ ulist, uint32_t umax,
-                                                          unsigned long long* __restrict__ ptab, uint32_t pmask) {
+                                                          unsigned long long* __restrict__ ptab, uint32_t pmask,
+                                                          const __grid_constant__ InlineArgs ia) {
   __shared__ unsigned long long seen_mem[kSeen];
   __shared__ unsigned long long queue_mem[kScanThreads / 32][2][kQueue];
   volatile unsigned long long* seen = seen_mem;
   for (int x = threadIdx.x; x < kSeen; x += blockDim.x) seen[x] = kNoPair;
   __syncthreads();
-  if (ptab && ctl->pair_mode == 0) ptab = nullptr;
+  if (kInline || (ptab && ctl->pair_mode == 0)) ptab = nullptr;
   const uint32_t tm = ctl->tm;
   const CellT code = stamp_code<CellT>(tm);
   const uint32_t tag = slice_tag(ctl->T);
+  const Win win = make_win<CellT>(tm, geo.P, geo.k);
   const int lane = threadIdx.x & 31;
   const int warp = threadIdx.x >> 5;
   ScanQueues Q{queue_mem[warp][0], queue_mem[warp][1], 0u, 0u};
@@ -44,7 +48,9 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan(const uint32_t* __rest
     for (int j = 0; j < 4; j++) {
       const unsigned long long key = ((unsigned long long)a[j] << 32) | b[j];
       bool miss = false;
-      if (ok[j]) {  // this block's table of recently scanned pairs
+      if (kInline) {
+        miss = ok[j];
+      } else if (ok[j]) {  // this block's table of recently scanned pairs
         const uint32_t h = seen_slot(key);
         if (key == kNoPair || seen[h] != key) {
           miss = true;
@@ -61,7 +67,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan(const uint32_t* __rest
                              tag, lane);
       } else {
         queue_push(Q.q2, Q.n2, miss, key, lane);
-        if (Q.n2 >= 32) drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+        if (Q.n2 >= 32)
+          drain_scan<CellT, kInline>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, &ia, &win);
       }
     }
 #pragma unroll
@@ -74,7 +81,8 @@ __global__ void __launch_bounds__(kScanThreads, 4) k_scan(const uint32_t* __rest
   if (ptab && Q.n1)
     drain_claim<CellT>(Q, ptab, pmask, n_miss, n_gdup, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag,
                        lane);
-  while (Q.n2) drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+  while (Q.n2)
+    drain_scan<CellT, kInline>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, &ia, &win);
   if (ptab) {  // one global update per block
     __shared__ unsigned s_miss, s_gdup;
     if (threadIdx.x == 0) s_miss = s_gdup = 0;
@@ -216,7 +224,8 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
                                                   srla_entry* rep0, srla_entry* rep1, srla_slice_stats* st0,
                                                   srla_slice_stats* st1, uint32_t umax,
                                                   const float* __restrict__ lut_est,
-                                                  const uint32_t* __restrict__ lut_flags) {
+                                                  const uint32_t* __restrict__ lut_flags, uint32_t* si0,
+                                                  uint32_t* si1) {
   __shared__ int s_last;
   const unsigned long long T = ctl->T;
   const int par = (int)(T & 1);
@@ -239,6 +248,10 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
     const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
     const uint32_t w = union_count<CellT>(le, geo.v, geo.gl, geo.u, mycol, win, lane);
     const uint32_t cw = union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, win_post, lane);
+    // inline mode: a carried host gets its SI bits in the next slice's indicators (Algorithm 3)
+    uint32_t* si_next = par ? si0 : si1;
+    if (si_next && cw >= geo.rho_g && (uint32_t)lane < geo.u)
+      atomicOr(si_next + (size_t)lane * geo.v + mycol, 1u << si_bit(coef, geo.u, aip));
     if (lane == 0) {
       const uint32_t s = set_find(ctab, cmask, tag, aip);
       const uint32_t origin = (s != 0xFFFFFFFFu) ? cflags[s] : 0u;
@@ -315,11 +328,12 @@ __global__ void k_encode(const uint16_t* __restrict__ d, CellT* __restrict__ cel
   }
 }
 
-// Insert carried hosts (checkpoint import) into the open slice's candidate set.
+// Insert carried hosts (checkpoint import) into the open slice's candidate set, and set
+// their SI bits in the open slice's indicators (inline mode, si non-null).
 __global__ void k_insert_carried(const uint32_t* __restrict__ hosts, uint32_t n, Ctl* __restrict__ ctl,
                                  unsigned long long* ctab0, unsigned long long* ctab1, uint32_t* cflags0,
                                  uint32_t* cflags1, uint32_t cmask, uint32_t* clist0, uint32_t* clist1,
-                                 uint32_t cmax) {
+                                 uint32_t cmax, Geo geo, const __grid_constant__ Coef coef, uint32_t* si) {
   const unsigned long long T = ctl->T;
   const int par = (int)(T & 1);
   unsigned long long* ctab = par ? ctab1 : ctab0;
@@ -329,6 +343,10 @@ __global__ void k_insert_carried(const uint32_t* __restrict__ hosts, uint32_t n,
   for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < n; x += gridDim.x * blockDim.x) {
     uint32_t slot;
     const int r = set_insert(ctab, cmask, tag, hosts[x], &slot);
+    if (si)
+      for (uint32_t i = 0; i < geo.u; i++)
+        atomicOr(si + (size_t)i * geo.v + (hash61(coef.a[i], coef.b[i], hosts[x]) & geo.vmask),
+                 1u << si_bit(coef, geo.u, hosts[x]));
     if (r == 1) {
       cflags[slot] = SRLA_CARRIED;
       const unsigned at = atomicAdd(&ctl->cat_count[par], 1u);

@@ -60,8 +60,8 @@ __device__ __forceinline__ uint32_t seen_slot(unsigned long long key) {
 // Full scan of one pair per lane (a dense batch): Algorithm 2's DRsets, and the sampled host
 // into the slice's set (one probe per distinct host of the warp, one append counter update
 // per warp).  All 32 lanes call it; `ok` marks the lanes that hold a pair.
-template <typename CellT>
-__device__ __forceinline__ void scan_dense(uint32_t aip, uint32_t bip, bool ok, const Geo& geo, const Coef& coef,
+template <typename CellT, bool kInline = false>
+__device__ __forceinline__ unsigned scan_dense(uint32_t aip, uint32_t bip, bool ok, const Geo& geo, const Coef& coef,
                                            CellT code, CellT* __restrict__ re, CellT* __restrict__ le,
                                            Ctl* __restrict__ ctl, unsigned long long* __restrict__ utab,
                                            uint32_t umask, uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag,
@@ -78,22 +78,28 @@ __device__ __forceinline__ void scan_dense(uint32_t aip, uint32_t bip, bool ok, 
       // the bits not yet set are OR-ed in.  Under heavy sources most bits of a run are set
       // early in the slice; skipping those ORs keeps their hot L2 lines from serialising.
       for (uint32_t i0 = 0; i0 < u; i0 += 4) {
-        size_t xl[4], xr[4];
-        uint32_t hl[4], hr[4];
+        uint32_t c[4], h[4];
+        size_t x[4];
 #pragma unroll
         for (int r = 0; r < 4; r++) {
           const uint32_t i = i0 + (uint32_t)r;
-          const uint32_t c = i < u ? hash61(coef.a[i], coef.b[i], aip) & geo.vmask : 0u;
-          const size_t se = (size_t)i * geo.v + c;
-          xl[r] = se * geo.gl + jl;
-          xr[r] = se * geo.g + jr;
-          hl[r] = i < u ? bit_peek(le, xl[r]) : ~0u;
-          hr[r] = (i < u && samp) ? bit_peek(re, xr[r]) : ~0u;
+          c[r] = i < u ? hash61(coef.a[i], coef.b[i], aip) & geo.vmask : 0u;
+          x[r] = ((size_t)i * geo.v + c[r]) * geo.gl + jl;
+          h[r] = i < u ? bit_peek(le, x[r]) : ~0u;
         }
 #pragma unroll
-        for (int r = 0; r < 4; r++) {
-          if (!((hl[r] >> (xl[r] & 31u)) & 1u)) dr_set<CellT>(le, xl[r], code);
-          if (!((hr[r] >> (xr[r] & 31u)) & 1u)) dr_set<CellT>(re, xr[r], code);
+        for (int r = 0; r < 4; r++)
+          if (!((h[r] >> (x[r] & 31u)) & 1u)) dr_set<CellT>(le, x[r], code);
+        if (samp) {
+#pragma unroll
+          for (int r = 0; r < 4; r++) {
+            const uint32_t i = i0 + (uint32_t)r;
+            x[r] = ((size_t)i * geo.v + c[r]) * geo.g + jr;
+            h[r] = i < u ? bit_peek(re, x[r]) : ~0u;
+          }
+#pragma unroll
+          for (int r = 0; r < 4; r++)
+            if (!((h[r] >> (x[r] & 31u)) & 1u)) dr_set<CellT>(re, x[r], code);
         }
       }
     } else {
@@ -107,6 +113,7 @@ __device__ __forceinline__ void scan_dense(uint32_t aip, uint32_t bip, bool ok, 
     }
   }
   const unsigned sm = __ballot_sync(kFull, samp);
+  if constexpr (kInline) return sm;  // the inline test replaces the set of sampled hosts
   int r = -2;
   if (samp) {
     const unsigned peers = __match_any_sync(sm, aip);
@@ -128,6 +135,76 @@ __device__ __forceinline__ void scan_dense(uint32_t aip, uint32_t bip, bool ok, 
         ulist[idx] = aip;
       else
         atomicOr(&ctl->overflow, 1u);
+    }
+  }
+  return sm;
+}
+
+// ------------------------------------------------------------ inline candidate test
+//
+// Algorithm 2 as printed (SRLA_MODE_INLINE): right after a sampled pair has updated the SRE,
+// its host is tested by its union SRE (Algorithm 1: at least ceil(rho g) cells inside the
+// window in every row); if it passes and its super point indicator bit (Section 4.1) is not
+// yet set in all of its u estimators, the bits are set and the host enters the open slice's
+// candidate set.  Threads race between the test and the set, so a host can pass twice; the
+// candidate set keeps one copy.
+struct InlineArgs {
+  uint32_t* si[2];  // super point indicator bits (low 16 bits of a word) per estimator, by parity
+  unsigned long long* ctab[2];
+  uint32_t* cflags[2];
+  uint32_t* clist[2];
+  uint32_t cmask, cmax;
+};
+
+// The SI bit of a host: bits 28..31 of the sampling-role hash applied to aip.
+__device__ __forceinline__ uint32_t si_bit(const Coef& coef, uint32_t u, uint32_t aip) {
+  return hash61(coef.a[u + 2], coef.b[u + 2], aip) >> 28;
+}
+
+// Hosts of the lanes in `sm` (sampled, their SRE stores issued), two at a time.
+template <typename CellT>
+__device__ __forceinline__ void inline_test(unsigned sm, uint32_t aip, const Geo& geo, const Coef& coef,
+                                            const CellT* __restrict__ re, const Win& win, Ctl* __restrict__ ctl,
+                                            const InlineArgs& ia, int lane) {
+  const unsigned long long T = ctl->T;
+  const int par = (int)(T & 1);
+  const uint32_t tag = slice_tag(T);
+  const bool mine = (uint32_t)lane < geo.u;
+  while (sm) {
+    const int j0 = __ffs(sm) - 1;
+    sm &= sm - 1;
+    const bool two = sm != 0;
+    const int j1 = two ? __ffs(sm) - 1 : j0;
+    if (two) sm &= sm - 1;
+    const uint32_t a0 = __shfl_sync(kFull, aip, j0), a1 = __shfl_sync(kFull, aip, j1);
+    const uint32_t c0 = mine ? hash61(coef.a[lane], coef.b[lane], a0) & geo.vmask : 0u;
+    const uint32_t c1 = mine ? hash61(coef.a[lane], coef.b[lane], a1) & geo.vmask : 0u;
+    uint32_t n0, n1;
+    __syncwarp();  // the warp's own SRE stores are ordered before its reads (through L2)
+    union_count_atleast2<CellT, true>(re, geo.v, geo.g, geo.u, c0, c1, win, geo.rho_g, lane, n0, n1);
+    for (int h = 0; h < (two ? 2 : 1); h++) {
+      const uint32_t a = h ? a1 : a0, c = h ? c1 : c0, n = h ? n1 : n0;
+      if (n < geo.rho_g) continue;  // n is the same in every lane
+      const uint32_t b = si_bit(coef, geo.u, a);
+      uint32_t* w = mine ? ia.si[par] + (size_t)lane * geo.v + c : nullptr;
+      const bool set = mine ? ((*w >> b) & 1u) != 0u : true;
+      if (__all_sync(kFull, set)) continue;  // USI(aip) has the bit: already a candidate
+      if (mine) atomicOr(w, 1u << b);
+      if (lane == 0) {
+        uint32_t slot;
+        const int r = set_insert(ia.ctab[par], ia.cmask, tag, a, &slot);
+        if (r == 1) {
+          ia.cflags[par][slot] = SRLA_NEW;
+          atomicAdd(&ctl->n_new, 1u);
+          const unsigned at = atomicAdd(&ctl->cat_count[par], 1u);
+          if (at < ia.cmax)
+            ia.clist[par][at] = a;
+          else
+            atomicOr(&ctl->overflow, 2u);
+        } else if (r < 0) {
+          atomicOr(&ctl->overflow, 2u);
+        }
+      }
     }
   }
 }
@@ -166,15 +243,18 @@ __device__ __forceinline__ bool queue_take(volatile unsigned long long* q, uint3
   return ok;
 }
 
-template <typename CellT>
+template <typename CellT, bool kInline = false>
 __device__ __forceinline__ void drain_scan(ScanQueues& Q, const Geo& geo, const Coef& coef, CellT code,
                                            CellT* __restrict__ re, CellT* __restrict__ le, Ctl* __restrict__ ctl,
                                            unsigned long long* __restrict__ utab, uint32_t umask,
-                                           uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag, int lane) {
+                                           uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag, int lane,
+                                           const InlineArgs* ia = nullptr, const Win* win = nullptr) {
   unsigned long long key;
   const bool ok = queue_take(Q.q2, Q.n2, lane, key);
-  scan_dense<CellT>((uint32_t)(key >> 32), (uint32_t)key, ok, geo, coef, code, re, le, ctl, utab, umask, ulist, umax,
-                    tag, lane);
+  const uint32_t aip = (uint32_t)(key >> 32);
+  const unsigned sm = scan_dense<CellT, kInline>(aip, (uint32_t)key, ok, geo, coef, code, re, le, ctl, utab, umask,
+                                                 ulist, umax, tag, lane);
+  if constexpr (kInline) inline_test<CellT>(sm, aip, geo, coef, re, *win, ctl, *ia, lane);
 }
 
 template <typename CellT>

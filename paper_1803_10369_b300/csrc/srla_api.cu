@@ -97,10 +97,28 @@ int grid_for(uint64_t items, int per_block, int cap) {
   return (int)std::max<uint64_t>(1, std::min<uint64_t>(b, (uint64_t)cap));
 }
 
+bool inline_mode(const srla_t* h) { return h->p.mode == SRLA_MODE_INLINE; }
+
+// The candidate-set and indicator arrays the inline candidate test writes.
+InlineArgs inline_args(const srla_t* h) {
+  const Layout& L = h->L;
+  InlineArgs a{};
+  for (int q = 0; q < 2; q++) {
+    a.si[q] = inline_mode(h) ? h->at<uint32_t>(L.si[q]) : nullptr;
+    a.ctab[q] = h->at<unsigned long long>(L.ctab[q]);
+    a.cflags[q] = h->at<uint32_t>(L.cflags[q]);
+    a.clist[q] = h->at<uint32_t>(L.clist[q]);
+  }
+  a.cmask = L.cmask;
+  a.cmax = h->p.max_candidates;
+  return a;
+}
+
 template <typename CellT>
 int launch_scan(srla_t* h, const uint32_t* pairs, uint64_t n) {
   const bool vec = (reinterpret_cast<uintptr_t>(pairs) & 15u) == 0;
-  auto kern = vec ? k_scan<CellT, true> : k_scan<CellT, false>;
+  auto kern = inline_mode(h) ? (vec ? k_scan<CellT, true, true> : k_scan<CellT, false, true>)
+                             : (vec ? k_scan<CellT, true> : k_scan<CellT, false>);
   const int grid = grid_for(n, kScanThreads * 4, h->sms * std::max(1, h->occ_scan[vec ? 1 : 0]));
   CellT* re = h->at<CellT>(h->L.re);
   CellT* le = h->at<CellT>(h->L.le);
@@ -108,7 +126,8 @@ int launch_scan(srla_t* h, const uint32_t* pairs, uint64_t n) {
   kern<<<grid, kScanThreads, 0, h->st>>>(pairs, n, h->geo, h->coef, re, le, h->ctl(),
                                          h->at<unsigned long long>(h->L.utab), h->L.umask,
                                          h->at<uint32_t>(h->L.ulist), h->p.max_sampled,
-                                         h->L.pairs ? h->at<unsigned long long>(h->L.ptab) : nullptr, h->L.pmask);
+                                         h->L.pairs ? h->at<unsigned long long>(h->L.ptab) : nullptr, h->L.pmask,
+                                         inline_args(h));
   return cuda_err(cudaGetLastError());
 }
 
@@ -143,14 +162,16 @@ int clear_pairs(srla_t* h) {
   return cuda_err(cudaMemsetAsync(h->ws + h->L.ptab, 0xFF, ((size_t)h->L.pmask + 1) * 8, h->st));
 }
 
+// The slice end of the open slice, whose index has parity q.
 template <typename CellT>
-int launch_end_slice(srla_t* h) {
+int launch_end_slice(srla_t* h, int q) {
   const Layout& L = h->L;
+  const bool inl = inline_mode(h);
   int r;
   if ((r = launch_sweep<CellT>(h, 1, h->k_is_P ? 0 : 1, 0)) != SRLA_OK) return r;
   // Eq. 8/9 table: needs the census; runs beside the filter and sort when a side stream exists
   const int lut_grid = (int)std::min<uint32_t>((h->p.gl + 1 + 255) / 256, (uint32_t)h->sms * 4);
-  h->launches += 3;  // lut, filter, estimate
+  h->launches += inl ? 2 : 3;  // lut, (filter,) estimate
   if (h->st_side) {
     SRLA_TRY(cudaEventRecord(h->ev_fork, h->st));
     SRLA_TRY(cudaStreamWaitEvent(h->st_side, h->ev_fork, 0));
@@ -159,20 +180,25 @@ int launch_end_slice(srla_t* h) {
   } else {
     k_lut<<<lut_grid, 256, 0, h->st>>>(h->geo, h->ctl(), h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
   }
-  k_filter<CellT><<<h->sms * 4, 256, 0, h->st>>>(
-      h->geo, h->coef, h->at<CellT>(L.re), h->ctl(), h->at<uint32_t>(L.ulist), h->p.max_sampled,
-      h->at<unsigned long long>(L.ctab[0]), h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]),
-      h->at<uint32_t>(L.cflags[1]), L.cmask, h->at<uint32_t>(L.clist[0]), h->at<uint32_t>(L.clist[1]),
-      h->p.max_candidates);
+  // the inline mode found its new candidates during the scan
+  if (!inl)
+    k_filter<CellT><<<h->sms * 4, 256, 0, h->st>>>(
+        h->geo, h->coef, h->at<CellT>(L.re), h->ctl(), h->at<uint32_t>(L.ulist), h->p.max_sampled,
+        h->at<unsigned long long>(L.ctab[0]), h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]),
+        h->at<uint32_t>(L.cflags[1]), L.cmask, h->at<uint32_t>(L.clist[0]), h->at<uint32_t>(L.clist[1]),
+        h->p.max_candidates);
   if ((r = launch_sort(h)) != SRLA_OK) return r;
   if (h->st_side) SRLA_TRY(cudaStreamWaitEvent(h->st, h->ev_join, 0));
+  // Algorithm 3 clears every SI before the carried hosts set theirs for the next slice
+  if (inl) SRLA_TRY(cudaMemsetAsync(h->ws + L.si[q ^ 1], 0, (size_t)h->p.u * h->p.v * 4, h->st));
   k_estimate<CellT><<<h->sms * 2, 256, 0, h->st>>>(
       h->geo, h->coef, h->at<CellT>(L.re), h->at<CellT>(L.le), h->ctl(), h->at<unsigned long long>(L.ctab[0]),
       h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]), h->at<uint32_t>(L.cflags[1]), L.cmask,
       h->at<uint32_t>(L.clist[0]), h->at<uint32_t>(L.clist[1]), h->p.max_candidates,
       h->at<srla_entry>(L.rep_entries[0]), h->at<srla_entry>(L.rep_entries[1]),
       h->at<srla_slice_stats>(L.rep_stats[0]), h->at<srla_slice_stats>(L.rep_stats[1]), h->p.max_sampled,
-      h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
+      h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags), inl ? h->at<uint32_t>(L.si[0]) : nullptr,
+      inl ? h->at<uint32_t>(L.si[1]) : nullptr);
   SRLA_TRY(cudaGetLastError());
   // with k = 2^z - 1 the recorders that saturate are still inside the window of the closed
   // slice, so they are cleared only after the slice was estimated and closed
@@ -183,7 +209,7 @@ int launch_end_slice(srla_t* h) {
 // Slice end plus the copy of its header and first report entries into the pinned slot q.
 template <typename CellT>
 int enqueue_end_slice(srla_t* h, int q) {
-  const int r = launch_end_slice<CellT>(h);
+  const int r = launch_end_slice<CellT>(h, q);
   if (r != SRLA_OK) return r;
   srla_s::Slot& s = h->slot[q];
   SRLA_TRY(cudaMemcpyAsync(s.h_stats, h->ws + h->L.rep_stats[q], sizeof(srla_slice_stats), cudaMemcpyDeviceToHost,
@@ -234,8 +260,11 @@ int occupancy(srla_t* h) {
   int a = 0, b = 0, c = 0;
   const int rs = with_cells(h->p.dr_bytes, [&](auto cell) {
     using CellT = decltype(cell);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k_scan<CellT, false>, kScanThreads, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_scan<CellT, true>, kScanThreads, 0) != cudaSuccess)
+    const bool inl = inline_mode(h);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, inl ? k_scan<CellT, false, true> : k_scan<CellT, false>,
+                                                      kScanThreads, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, inl ? k_scan<CellT, true, true> : k_scan<CellT, true>,
+                                                      kScanThreads, 0) != cudaSuccess)
       return SRLA_E_CUDA;
     return SRLA_OK;
   });
@@ -428,7 +457,8 @@ int srla_end_slice(srla_t* h, uint64_t* slice_id) {
       k_insert_carried<<<grid_for(nc, 256, h->sms * 4), 256, 0, h->st>>>(
           h->at<uint32_t>(L.sort_tmp), nc, h->ctl(), h->at<unsigned long long>(L.ctab[0]),
           h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]), h->at<uint32_t>(L.cflags[1]),
-          L.cmask, h->at<uint32_t>(L.clist[0]), h->at<uint32_t>(L.clist[1]), h->p.max_candidates);
+          L.cmask, h->at<uint32_t>(L.clist[0]), h->at<uint32_t>(L.clist[1]), h->p.max_candidates, h->geo, h->coef,
+          nullptr);  // the SI bits of the carried hosts are already set
       SRLA_TRY(cudaGetLastError());
     }
   }
@@ -568,6 +598,8 @@ int srla_import_state(srla_t* h, const void* host_buf, size_t len) {
   if (r != SRLA_OK) return r;
   r = with_cells(p.dr_bytes, [&](auto c) { return import_cells<decltype(c)>(h, h->L.le, nle, sle, tm); });
   if (r != SRLA_OK) return r;
+  uint32_t* si_open = inline_mode(h) ? h->at<uint32_t>(h->L.si[h->T & 1]) : nullptr;
+  if (si_open) SRLA_TRY(cudaMemsetAsync(si_open, 0, (size_t)p.u * p.v * 4, h->st));
   if (hd.n_carry) {
     const uint32_t* carry = reinterpret_cast<const uint32_t*>(sle + nle);
     uint32_t* stage = h->at<uint32_t>(h->L.sort_tmp);
@@ -577,7 +609,7 @@ int srla_import_state(srla_t* h, const void* host_buf, size_t len) {
     k_insert_carried<<<grid_for(hd.n_carry, 256, h->sms * 4), 256, 0, h->st>>>(
         stage, hd.n_carry, h->ctl(), h->at<unsigned long long>(L.ctab[0]), h->at<unsigned long long>(L.ctab[1]),
         h->at<uint32_t>(L.cflags[0]), h->at<uint32_t>(L.cflags[1]), L.cmask, h->at<uint32_t>(L.clist[0]),
-        h->at<uint32_t>(L.clist[1]), p.max_candidates);
+        h->at<uint32_t>(L.clist[1]), p.max_candidates, h->geo, h->coef, si_open);
     SRLA_TRY(cudaGetLastError());
   }
   return cuda_err(cudaStreamSynchronize(h->st));
@@ -661,7 +693,7 @@ template <typename CellT>
 int static_batch(srla_s* h, const uint32_t* d_pairs, uint64_t n_pairs) {
   int r = SRLA_OK;
   if (n_pairs && (r = launch_scan<CellT>(h, d_pairs, n_pairs)) != SRLA_OK) return r;
-  return launch_end_slice<CellT>(h);
+  return launch_end_slice<CellT>(h, (int)(h->T & 1));
 }
 
 }  // namespace

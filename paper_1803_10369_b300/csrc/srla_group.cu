@@ -363,7 +363,8 @@ size_t srla_group_fixed_bytes(uint32_t max_links, uint64_t max_pkts, uint64_t ma
 }
 
 size_t srla_group_link_bytes(const srla_params* p) {
-  if (check(p) != SRLA_OK) return 0;
+  // groups run the order-free candidate rule only (the inline test is a single-link mode)
+  if (check(p) != SRLA_OK || p->mode != SRLA_MODE_ORDER_FREE) return 0;
   const srla_params q = link_params(*p);
   return align_up(layout_of(&q).total);
 }
@@ -445,7 +446,7 @@ int srla_group_create(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_p
 }
 
 int srla_group_attach(srla_group_t* g, const srla_params* p, uint32_t* link) {
-  if (!g || !link || check(p) != SRLA_OK) return SRLA_E_INVAL;
+  if (!g || !link || check(p) != SRLA_OK || p->mode != SRLA_MODE_ORDER_FREE) return SRLA_E_INVAL;
   if (!g->segments.empty()) return SRLA_E_ORDER;
   uint32_t l = 0;
   while (l < g->max_links && g->slots[l].active) l++;

@@ -18,6 +18,7 @@ N_HASH = MAX_ROWS + 3
 
 OK, E_INVAL, E_NOMEM, E_CAPACITY, E_CUDA, E_ORDER, E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 SUPER, SATURATED, CARRIED, NEW = 1, 2, 4, 8
+MODE_ORDER_FREE, MODE_INLINE = 0, 1
 
 
 class srla_params(ctypes.Structure):
@@ -26,7 +27,7 @@ class srla_params(ctypes.Structure):
         ("dr_bytes", ctypes.c_uint32), ("z", ctypes.c_uint32), ("k", ctypes.c_uint32), ("theta", ctypes.c_uint32),
         ("start_slice", ctypes.c_uint64), ("staging_pkts", ctypes.c_uint64),
         ("max_sampled", ctypes.c_uint32), ("max_candidates", ctypes.c_uint32),
-        ("pair_slots_log2", ctypes.c_int32), ("reserved", ctypes.c_uint32),
+        ("pair_slots_log2", ctypes.c_int32), ("mode", ctypes.c_uint32),
         ("hash_a", ctypes.c_uint64 * N_HASH), ("hash_b", ctypes.c_uint64 * N_HASH),
     ]
 
@@ -131,9 +132,10 @@ def _ck(code: int, what: str):
 
 
 def make_params(u, v, g, gl, dr_bytes, z, k, theta, hash_a, hash_b, start_slice=0, staging_pkts=0,
-                max_sampled=1 << 16, max_candidates=1 << 14, pair_slots_log2=0) -> srla_params:
+                max_sampled=1 << 16, max_candidates=1 << 14, pair_slots_log2=0, mode=MODE_ORDER_FREE) -> srla_params:
     p = srla_params()
     p.pair_slots_log2 = pair_slots_log2
+    p.mode = mode
     p.u, p.v, p.g, p.gl = u, v, g, gl
     p.dr_bytes, p.z, p.k, p.theta = dr_bytes, z, k, theta
     p.start_slice, p.staging_pkts = start_slice, staging_pkts

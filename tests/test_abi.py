@@ -87,6 +87,17 @@ def test_one_bit_recorders():
     assert bytes1 - bits == cells - cells // 8
 
 
+def test_inline_mode_params():
+    """The inline candidate mode adds the SI words (u*v 32-bit words per slice parity) and is a
+    single-link mode: groups refuse it."""
+    base = srla.workspace_bytes(_params())
+    inl = srla.workspace_bytes(_params(mode=srla.MODE_INLINE))
+    assert inl >= base + 2 * 4 * 1024 * 4
+    assert srla.check_params(_params(mode=2)) == srla.E_INVAL
+    assert srla.Group.link_bytes(_params()) > 0
+    assert srla.Group.link_bytes(_params(mode=srla.MODE_INLINE)) == 0
+
+
 def test_workspace_grows_with_sketch():
     small = srla.workspace_bytes(_params())
     big = srla.workspace_bytes(_params(v=1 << 14, gl=256, g=128, u=8, dr_bytes=2, z=16, k=300))

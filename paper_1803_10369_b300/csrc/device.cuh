@@ -160,9 +160,10 @@ __device__ __forceinline__ void dr_set(CellT* __restrict__ arr, size_t idx, Cell
 // The stamps inside the window of the last `lim` slices (ages 0 .. lim-1) are the codes
 // 1 + ((tm - j) mod P), j < lim: one cyclic interval of codes ending at hi = tm + 1, either
 // [lo, hi] or, when it wraps past P, [lo, P] and [1, hi].  Empty cells (code 0) are never in
-// it.  SIMD compares test 2 (16-bit) or 4 (8-bit) cells per instruction.
+// it.  Cells are tested one by one (the per-byte SIMD compare intrinsics are emulated on
+// this GPU and cost more).
 struct Win {
-  uint32_t lo, hi;  // splatted to every cell of a word
+  uint32_t lo, hi, len;
   bool wrap, none;
 };
 
@@ -175,36 +176,32 @@ template <typename CellT>
 __device__ __forceinline__ Win make_win(uint32_t tm, uint32_t P, uint32_t lim) {
   Win w;
   w.none = lim == 0;
-  if constexpr (kIsBit<CellT>) {  // a set bit is inside any window of at least one slice
-    w.lo = w.hi = 0u;
-    w.wrap = false;
-    return w;
-  }
-  const uint32_t hi = tm + 1u;
-  uint32_t lo;
-  if (lim <= hi) {
-    lo = hi - lim + 1u;
-    w.wrap = false;
-  } else {
-    lo = hi + P - lim + 1u;
-    w.wrap = true;
-  }
-  w.lo = splat<CellT>(lo);
-  w.hi = splat<CellT>(hi);
+  w.len = lim;
+  w.hi = tm + 1u;
+  w.wrap = !kIsBit<CellT> && lim > w.hi;
+  w.lo = w.wrap ? w.hi + P - lim + 1u : w.hi - lim + 1u;
   return w;
 }
 
-// Per-cell mask of a 32-bit word of cells: all ones in the cells inside the window.
+// Per-cell mask of a 32-bit word of cells: all ones in the cells inside the window.  Without
+// wrap a cell c is inside iff c - lo < len in 32-bit arithmetic (code 0 wraps to a huge value).
 template <typename CellT>
 __device__ __forceinline__ uint32_t window_mask(uint32_t word, const Win& w) {
   if (w.none) return 0u;
-  if constexpr (kIsBit<CellT>) return word;
-  if (sizeof(CellT) == 1) {
-    const uint32_t ge = __vcmpgeu4(word, w.lo), le = __vcmpleu4(word, w.hi);
-    return w.wrap ? (ge | (le & __vcmpne4(word, 0u))) : (ge & le);
+  if constexpr (kIsBit<CellT>) {
+    return word;  // a set bit is inside any window of at least one slice
   } else {
-    const uint32_t ge = __vcmpgeu2(word, w.lo), le = __vcmpleu2(word, w.hi);
-    return w.wrap ? (ge | (le & __vcmpne2(word, 0u))) : (ge & le);
+    constexpr int kCells = 4 / (int)sizeof(CellT);
+    constexpr int kBits = 8 * (int)sizeof(CellT);
+    constexpr uint32_t kMask = (1u << kBits) - 1u;
+    uint32_t m = 0;
+#pragma unroll
+    for (int q = 0; q < kCells; q++) {
+      const uint32_t c = (word >> (q * kBits)) & kMask;
+      const bool in = w.wrap ? (c >= w.lo) | (c - 1u < w.hi) : (c - w.lo < w.len);
+      m |= in ? (kMask << (q * kBits)) : 0u;
+    }
+    return m;
   }
 }
 

@@ -205,11 +205,7 @@ __device__ __forceinline__ void group_sweep_chunk(const SweepChunk& c, const Lin
   const uint32_t asplat = splat<CellT>(alias);
   const bool count = is_le && !after_close;
   const bool reset = after_close ? true : !D.k_is_P;
-  SweepWin sw;
-  sw.hi = tm + 1u;
-  sw.wrap = D.geo.k > sw.hi;
-  sw.lo = sw.wrap ? sw.hi + P - D.geo.k + 1u : sw.hi - D.geo.k + 1u;
-  sw.len = D.geo.k;
+  const SweepWin sw = make_sweep_win<CellT>(tm, P, D.geo.k);
   uint32_t cnt = 0;
   const size_t nvec = c.count;
   size_t x = threadIdx.x;

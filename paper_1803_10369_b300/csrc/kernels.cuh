@@ -101,18 +101,24 @@ __global__ void __launch_bounds__(kScanThreads, kInline ? 2 : 4) k_scan(const ui
   }
 }
 
-// One streaming pass over a row of recorders (blockIdx.y < u: SLE row y; >= u: SRE row
-// y - u): census and stamp ageing.
+// One streaming pass over the recorders: census and stamp ageing.  Each block sweeps one
+// part of one row: gx_le blocks per SLE row, then (when ageing) gx_re blocks per SRE row, the
+// counts chosen by the host in proportion to the row lengths so that every block moves about
+// the same number of bytes.  Within its row a block walks grid-stride (neighbouring threads
+// read neighbouring vectors), each thread with four vector loads in flight.
 template <typename CellT>
 __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, CellT* __restrict__ le,
                                                Ctl* __restrict__ ctl, int do_census, int do_reset,
-                                               int after_close) {
-  const uint32_t y = blockIdx.y;
-  const bool is_le = y < geo.u;
-  if (!is_le && !do_reset) return;
-  const bool count = is_le && do_census;
+                                               int after_close, uint32_t gx_le, uint32_t gx_re) {
+  const bool census = do_census != 0;
   const bool reset = do_reset != 0;
-  const uint32_t row = is_le ? y : y - geo.u;
+  const uint32_t n_le_blocks = (census || reset) ? geo.u * gx_le : 0u;
+  const bool is_le = blockIdx.x < n_le_blocks;
+  const uint32_t b = is_le ? blockIdx.x : blockIdx.x - n_le_blocks;
+  const uint32_t gx = is_le ? gx_le : gx_re;
+  const uint32_t row = b / gx, part = b % gx;
+  if (row >= geo.u) return;
+  const bool count = is_le && census;
   const size_t cells = (size_t)geo.v * (is_le ? geo.gl : geo.g);
   uint4* base = reinterpret_cast<uint4*>(words_at<CellT>(is_le ? le : re, (size_t)row * cells));
   const size_t nvec = cell_array_bytes<CellT>(cells) / 16;
@@ -120,14 +126,10 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
   // stamp of the slice that opens next: after the slice was closed, that is the open slice
   const uint32_t alias = 1u + (after_close ? tm : ((tm + 1u == P) ? 0u : tm + 1u));
   const uint32_t asplat = splat<CellT>(alias);
-  SweepWin sw;  // the in-window stamps: [lo, hi], or [lo, P] and [1, hi] when wrapped
-  sw.hi = tm + 1u;
-  sw.wrap = geo.k > sw.hi;
-  sw.lo = sw.wrap ? sw.hi + P - geo.k + 1u : sw.hi - geo.k + 1u;
-  sw.len = geo.k;
+  const SweepWin sw = make_sweep_win<CellT>(tm, P, geo.k);
   uint32_t cnt = 0;
-  const size_t stride = (size_t)gridDim.x * blockDim.x;
-  size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const size_t stride = (size_t)gx * blockDim.x;
+  size_t x = (size_t)part * blockDim.x + threadIdx.x;
   for (; x + 3 * stride < nvec; x += 4 * stride) {  // four loads in flight per thread
     uint4 q[4];
 #pragma unroll
@@ -137,13 +139,13 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
   }
   for (; x < nvec; x += stride) sweep_vec<CellT>(base, x, base[x], count, reset, sw, alias, asplat, cnt);
   if (count) {
-    __shared__ uint32_t part[8];
+    __shared__ uint32_t part_sum[8];
     cnt = warp_sum(cnt);
-    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = cnt;
+    if ((threadIdx.x & 31) == 0) part_sum[threadIdx.x >> 5] = cnt;
     __syncthreads();
     if (threadIdx.x == 0) {
       unsigned long long s = 0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += part[w];
+      for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += part_sum[w];
       atomicAdd(&ctl->census[row], s);
     }
   }

@@ -308,21 +308,42 @@ __device__ __forceinline__ void load_pairs(const uint32_t* __restrict__ pairs, u
 // (age < k).  Reset: clear the stamps whose age would reach P after the slide, i.e. the code
 // 1 + ((T + 1) mod P); this is the DRslide of Algorithm 3 at the point where a distance
 // saturates at 2^z - 1.
-// In-window cells of one 32-bit word (the interval form of make_win, one compare per cell).
+// The in-window stamps of the sweep: [lo, hi] (lo + len = hi + 1), or [lo, P] and [1, hi]
+// when the window wraps past P.
+struct SweepWin {
+  uint32_t lo, hi, len;
+  bool wrap;
+};
+
 template <typename CellT>
-__device__ __forceinline__ uint32_t count_in_window(uint32_t word, uint32_t lo, uint32_t len, bool wrap,
-                                                    uint32_t hi) {
-  if constexpr (kIsBit<CellT>) return (uint32_t)__popc(word);  // the window is the open slice
-  constexpr int kCells = 4 / (int)sizeof(CellT);
-  constexpr int kBits = 8 * (int)sizeof(CellT);
-  constexpr uint32_t kMask = (1u << kBits) - 1u;
-  uint32_t n = 0;
+__device__ __forceinline__ SweepWin make_sweep_win(uint32_t tm, uint32_t P, uint32_t k) {
+  SweepWin sw;
+  sw.hi = tm + 1u;
+  sw.wrap = k > sw.hi;
+  sw.lo = sw.wrap ? sw.hi + P - k + 1u : sw.hi - k + 1u;
+  sw.len = k;
+  return sw;
+}
+
+// In-window cells of one 32-bit word (the interval form of the window, one compare per cell;
+// the SIMD compare intrinsics are slower here).  Without wrap, a cell c is inside iff
+// c - lo < len in 32-bit arithmetic (the empty code 0 wraps to a huge value).
+template <typename CellT>
+__device__ __forceinline__ uint32_t count_in_window(uint32_t word, const SweepWin& sw) {
+  if constexpr (kIsBit<CellT>) {
+    return (uint32_t)__popc(word);  // the window is the open slice
+  } else {
+    constexpr int kCells = 4 / (int)sizeof(CellT);
+    constexpr int kBits = 8 * (int)sizeof(CellT);
+    constexpr uint32_t kMask = (1u << kBits) - 1u;
+    uint32_t n = 0;
 #pragma unroll
-  for (int q = 0; q < kCells; q++) {
-    const uint32_t c = (word >> (q * kBits)) & kMask;
-    n += wrap ? (uint32_t)((c >= lo) | (c - 1u < hi)) : (uint32_t)(c - lo < len);
+    for (int q = 0; q < kCells; q++) {
+      const uint32_t c = (word >> (q * kBits)) & kMask;
+      n += sw.wrap ? (uint32_t)((c >= sw.lo) | (c - 1u < sw.hi)) : (uint32_t)(c - sw.lo < sw.len);
+    }
+    return n;
   }
-  return n;
 }
 
 // Nonzero iff some cell of the word equals the splatted stamp (exact zero-cell test).
@@ -345,19 +366,12 @@ __device__ __forceinline__ uint32_t clear_stamp(uint32_t word, uint32_t alias) {
   return word;
 }
 
-struct SweepWin {
-  uint32_t lo, hi, len;
-  bool wrap;
-};
-
 template <typename CellT>
 __device__ __forceinline__ void sweep_vec(uint4* base, size_t x, uint4 q, bool count, bool reset, const SweepWin& sw,
                                           uint32_t alias, uint32_t asplat, uint32_t& cnt) {
   if (count)
-    cnt += count_in_window<CellT>(q.x, sw.lo, sw.len, sw.wrap, sw.hi) +
-           count_in_window<CellT>(q.y, sw.lo, sw.len, sw.wrap, sw.hi) +
-           count_in_window<CellT>(q.z, sw.lo, sw.len, sw.wrap, sw.hi) +
-           count_in_window<CellT>(q.w, sw.lo, sw.len, sw.wrap, sw.hi);
+    cnt += count_in_window<CellT>(q.x, sw) + count_in_window<CellT>(q.y, sw) + count_in_window<CellT>(q.z, sw) +
+           count_in_window<CellT>(q.w, sw);
   if (reset && (has_stamp<CellT>(q.x, asplat) | has_stamp<CellT>(q.y, asplat) | has_stamp<CellT>(q.z, asplat) |
                 has_stamp<CellT>(q.w, asplat))) {
     uint4 r;

@@ -131,14 +131,24 @@ int launch_scan(srla_t* h, const uint32_t* pairs, uint64_t n) {
   return cuda_err(cudaGetLastError());
 }
 
+// About sms * 8 blocks in all, shared between the SLE and SRE rows in proportion to their
+// lengths (at least one block per row, at most one per 1024 vectors).
 template <typename CellT>
 int launch_sweep(srla_t* h, int census, int reset, int after_close) {
-  const size_t cells_max = (size_t)h->p.v * std::max(h->p.g, h->p.gl);
-  const size_t nvec = cell_array_bytes<CellT>(cells_max) / 16;
-  const int gx = grid_for(nvec, 256, std::max(1, h->sms * 8 / (int)(2 * h->p.u)));
+  const srla_params& p = h->p;
+  const double le_row = (double)cell_array_bytes<CellT>((size_t)p.v * p.gl) / 16;
+  const double re_row = (double)cell_array_bytes<CellT>((size_t)p.v * p.g) / 16;
+  const double target = (double)h->sms * 8 / p.u;  // blocks per (SLE row + SRE row)
+  const double share = reset ? le_row / (le_row + re_row) : 1.0;
+  auto blocks = [](double want, double vecs) {
+    return (uint32_t)std::max(1.0, std::min(std::floor(want + 0.5), std::ceil(vecs / 1024)));
+  };
+  const uint32_t gx_le = blocks(target * share, le_row);
+  const uint32_t gx_re = reset ? blocks(target * (1.0 - share), re_row) : 0u;
+  const uint32_t grid = p.u * (gx_le + gx_re);
   h->launches++;
-  k_sweep<CellT><<<dim3(gx, 2 * h->p.u), 256, 0, h->st>>>(h->geo, h->at<CellT>(h->L.re), h->at<CellT>(h->L.le),
-                                                         h->ctl(), census, reset, after_close);
+  k_sweep<CellT><<<grid, 256, 0, h->st>>>(h->geo, h->at<CellT>(h->L.re), h->at<CellT>(h->L.le), h->ctl(), census,
+                                          reset, after_close, gx_le, gx_re);
   return cuda_err(cudaGetLastError());
 }
 

@@ -99,6 +99,7 @@ struct srla_group_s {
   cudaStream_t st = nullptr, st_copy = nullptr, st_side = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr}, ev_fork = nullptr, ev_join = nullptr;
   int sms = 0, scan_grid = 0, sort_grid = 0;
+  int filt_grid = 0, est_grid = 0;  // one wave of resident blocks
   void* h_pinned = nullptr;
   TaskHeader* h_tasks[2] = {nullptr, nullptr};
   srla_slice_stats* h_stats[2] = {nullptr, nullptr};
@@ -300,13 +301,13 @@ int enqueue_slice(srla_group_t* g, int q) {
   G_TRY(cudaStreamWaitEvent(g->st_side, g->ev_fork, 0));
   kg_lut<<<std::max(1, std::min<int>((int)g->max_links, g->sms * 4)), 256, 0, g->st_side>>>(descs, gctl);
   G_TRY(cudaEventRecord(g->ev_join, g->st_side));
-  kg_filter<<<g->sms * 4, 256, 0, g->st>>>(descs, gctl, filt_off);
+  kg_filter<<<g->filt_grid, 256, 0, g->st>>>(descs, gctl, filt_off);
   uint32_t* rep_off = reinterpret_cast<uint32_t*>(g->ws + F.rep_off[q]);
   void* args[] = {&descs, &gctl, &rep_off};
   G_TRY(cudaLaunchCooperativeKernel((const void*)kg_sort, dim3(g->sort_grid), dim3(kSortThreads), args,
                                     kSortSmallSmem, g->st));
   G_TRY(cudaStreamWaitEvent(g->st, g->ev_join, 0));
-  kg_estimate<<<g->sms * 2, 256, 0, g->st>>>(descs, gctl, reinterpret_cast<srla_slice_stats*>(g->ws + F.gstats[q]),
+  kg_estimate<<<g->est_grid, 256, 0, g->st>>>(descs, gctl, reinterpret_cast<srla_slice_stats*>(g->ws + F.gstats[q]),
                                              rep_off, reinterpret_cast<srla_entry*>(g->ws + F.grep[q]));
   g->launches += 1;
   kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 1, filt_off);
@@ -416,8 +417,10 @@ int srla_group_create(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_p
       std::memset(g->h_tasks[q], 0, tbytes);
     }
     cudaFuncSetAttribute(kg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmallSmem);
-    int o128 = 0, o512 = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_scan, kg_scan<256>, 256, 0) != cudaSuccess ||
+    int o128 = 0, o512 = 0, o_filt = 0, o_est = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o_filt, kg_filter, 256, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o_est, kg_estimate, 256, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_scan, kg_scan<256>, 256, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o128, kg_scan<128>, 128, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o512, kg_scan<512>, 512, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_sort, kg_sort, kSortThreads, kSortSmallSmem) != cudaSuccess ||
@@ -428,6 +431,8 @@ int srla_group_create(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_p
     g->scan_grid_of[2] = g->sms * std::max(1, o512);
     g->scan_grid = g->scan_grid_of[1];
     g->sort_grid = g->sms * occ_sort;
+    g->filt_grid = g->sms * std::max(1, o_filt);
+    g->est_grid = g->sms * std::max(1, o_est);
   }
   if (rc == SRLA_OK) rc = gerr(cudaMemsetAsync(g->ws, 0, g->F.total, g->st));
   if (rc == SRLA_OK) {

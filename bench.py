@@ -236,7 +236,7 @@ def _cuda_ok():
 def _config(w):
     return {"workload": w.name, "u": w.u, "v": w.v, "g": w.g, "gl": w.gl, "dr_bits": w.z, "dr_bytes": w.dr_bytes,
             "k": w.k, "theta": w.theta, "pkts_per_slice": w.pkts_per_slice, "links": 1,
-            "l2": "inputs distinct per step (K x 8 B x pkts/slice > L2); the sketch stays resident by design"}
+            "l2": "inputs distinct per step (K x 8 B x pkts/slice > L2); no flush between steps (the sketch is the link's state)"}
 
 
 def bench_srla(args):

@@ -28,10 +28,11 @@ inline uint64_t next_pow2(uint64_t x) {
 
 struct Layout {
   size_t ctl, re, le, staging, utab, ulist, ctab[2], cflags[2], clist[2], sort_tmp, sort_hist, lut_est,
-      lut_flags, rep_stats[2], rep_entries[2], ptab, si[2], total;
+      lut_flags, rep_stats[2], rep_entries[2], ptab[2], si[2], total;
   uint64_t staging_pkts;
   uint32_t umask, cmask, ntiles, pmask;
-  bool pairs;  // per-slice pair table present
+  bool pairs;   // per-slice pair table present
+  int n_ptab;   // pair tables: 2 (by slice parity), 1, or 0
 };
 
 // Eq. 1 on integers: the least n >= 0 with g * 2^n >= theta.
@@ -77,7 +78,9 @@ inline int check(const srla_params* p) {
   return SRLA_OK;
 }
 
-inline Layout layout_of(const srla_params* p) {
+// n_pair_tables: 2 for a single link (the next slice's table is cleared while one slice is
+// closed), 1 for a group link (the group sweep clears it).
+inline Layout layout_of(const srla_params* p, int n_pair_tables = 2) {
   Layout L{};
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -113,7 +116,9 @@ inline Layout layout_of(const srla_params* p) {
   L.pairs = p->pair_slots_log2 != -1;
   const uint32_t plog = p->pair_slots_log2 > 0 ? (uint32_t)p->pair_slots_log2 : 21u;
   L.pmask = L.pairs ? (1u << plog) - 1u : 0u;
-  L.ptab = take(L.pairs ? ((size_t)1 << plog) * 8 : 0);
+  // two pair tables by slice parity: the next slice's is cleared while this one is closed
+  L.n_ptab = L.pairs ? n_pair_tables : 0;
+  for (int q = 0; q < 2; q++) L.ptab[q] = take(q < L.n_ptab ? ((size_t)1 << plog) * 8 : 0);
   // inline mode: one 32-bit word of super point indicator bits per estimator, by parity
   for (int q = 0; q < 2; q++) L.si[q] = take(p->mode == SRLA_MODE_INLINE ? (size_t)p->u * p->v * 4 : 0);
   L.total = off;

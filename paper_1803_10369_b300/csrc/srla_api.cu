@@ -40,7 +40,9 @@ struct srla_s {
   cudaStream_t st_copy;  // internal stream for report remainders and checkpoints
   cudaStream_t st_h2d;   // internal stream for host-to-device copies of host batches
   cudaStream_t st_side;  // internal stream: the estimator table beside filter and sort
+  cudaStream_t st_d2h;   // internal stream: each slice's report header, after its slice end
   cudaEvent_t ev_fork, ev_join;
+  cudaEvent_t ev_done[2];  // slice end complete, by slice parity
   cudaEvent_t ev_ready[2], ev_free[2];  // staging halves: copied / consumed by the scan
   bool free_pending[2];
   int stage_cur;
@@ -99,6 +101,12 @@ int grid_for(uint64_t items, int per_block, int cap) {
 
 bool inline_mode(const srla_t* h) { return h->p.mode == SRLA_MODE_INLINE; }
 
+// The pair table of slice T (none when the table is disabled).
+unsigned long long* pair_table(const srla_t* h, uint64_t T) {
+  if (!h->L.n_ptab) return nullptr;
+  return h->at<unsigned long long>(h->L.ptab[h->L.n_ptab == 2 ? (int)(T & 1) : 0]);
+}
+
 // The candidate-set and indicator arrays the inline candidate test writes.
 InlineArgs inline_args(const srla_t* h) {
   const Layout& L = h->L;
@@ -126,7 +134,7 @@ int launch_scan(srla_t* h, const uint32_t* pairs, uint64_t n) {
   kern<<<grid, kScanThreads, 0, h->st>>>(pairs, n, h->geo, h->coef, re, le, h->ctl(),
                                          h->at<unsigned long long>(h->L.utab), h->L.umask,
                                          h->at<uint32_t>(h->L.ulist), h->p.max_sampled,
-                                         h->L.pairs ? h->at<unsigned long long>(h->L.ptab) : nullptr, h->L.pmask,
+                                         pair_table(h, h->T), h->L.pmask,
                                          inline_args(h));
   return cuda_err(cudaGetLastError());
 }
@@ -167,9 +175,15 @@ int launch_sort(srla_t* h) {
 }
 
 // The next slice starts with an empty pair table (all slots hold the empty key, ~0).
+// Pair table q (of L.n_ptab) starts empty: every slot holds the empty key, ~0.
+int clear_pairs(srla_t* h, int q, cudaStream_t st) {
+  if (q >= h->L.n_ptab) return SRLA_OK;
+  return cuda_err(cudaMemsetAsync(h->ws + h->L.ptab[q], 0xFF, ((size_t)h->L.pmask + 1) * 8, st));
+}
+
 int clear_pairs(srla_t* h) {
-  if (!h->L.pairs) return SRLA_OK;
-  return cuda_err(cudaMemsetAsync(h->ws + h->L.ptab, 0xFF, ((size_t)h->L.pmask + 1) * 8, h->st));
+  int r = clear_pairs(h, 0, h->st);
+  return r != SRLA_OK ? r : clear_pairs(h, 1, h->st);
 }
 
 // The slice end of the open slice, whose index has parity q.
@@ -178,6 +192,10 @@ int launch_end_slice(srla_t* h, int q) {
   const Layout& L = h->L;
   const bool inl = inline_mode(h);
   int r;
+  // With two pair tables the next slice's (used two slices ago) is cleared beside the
+  // filter and sort, after the sweep has streamed the recorders through L2, so that it is
+  // still cached when the next scan starts; a single table is cleared after the slice end.
+  const bool two = h->L.n_ptab == 2;
   if ((r = launch_sweep<CellT>(h, 1, h->k_is_P ? 0 : 1, 0)) != SRLA_OK) return r;
   // Eq. 8/9 table: needs the census; runs beside the filter and sort when a side stream exists
   const int lut_grid = (int)std::min<uint32_t>((h->p.gl + 1 + 255) / 256, (uint32_t)h->sms * 4);
@@ -186,9 +204,11 @@ int launch_end_slice(srla_t* h, int q) {
     SRLA_TRY(cudaEventRecord(h->ev_fork, h->st));
     SRLA_TRY(cudaStreamWaitEvent(h->st_side, h->ev_fork, 0));
     k_lut<<<lut_grid, 256, 0, h->st_side>>>(h->geo, h->ctl(), h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
+    if (two && (r = clear_pairs(h, q ^ 1, h->st_side)) != SRLA_OK) return r;
     SRLA_TRY(cudaEventRecord(h->ev_join, h->st_side));
   } else {
     k_lut<<<lut_grid, 256, 0, h->st>>>(h->geo, h->ctl(), h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
+    if (two && (r = clear_pairs(h, q ^ 1, h->st)) != SRLA_OK) return r;
   }
   // the inline mode found its new candidates during the scan
   if (!inl)
@@ -213,20 +233,21 @@ int launch_end_slice(srla_t* h, int q) {
   // with k = 2^z - 1 the recorders that saturate are still inside the window of the closed
   // slice, so they are cleared only after the slice was estimated and closed
   if (h->k_is_P && (r = launch_sweep<CellT>(h, 0, 1, 1)) != SRLA_OK) return r;
-  return clear_pairs(h);
+  return two ? SRLA_OK : clear_pairs(h, 0, h->st);
 }
 
-// Slice end plus the copy of its header and first report entries into the pinned slot q.
-template <typename CellT>
-int enqueue_end_slice(srla_t* h, int q) {
-  const int r = launch_end_slice<CellT>(h, q);
-  if (r != SRLA_OK) return r;
+// The copy of slice q's header and first report entries into its pinned slot, on the
+// report stream once the slice end is complete; the next slice's scan does not wait for it.
+int enqueue_report_copy(srla_t* h, int q) {
   srla_s::Slot& s = h->slot[q];
+  SRLA_TRY(cudaEventRecord(h->ev_done[q], h->st));
+  SRLA_TRY(cudaStreamWaitEvent(h->st_d2h, h->ev_done[q], 0));
   SRLA_TRY(cudaMemcpyAsync(s.h_stats, h->ws + h->L.rep_stats[q], sizeof(srla_slice_stats), cudaMemcpyDeviceToHost,
-                           h->st));
+                           h->st_d2h));
   const uint32_t pre = std::min<uint32_t>(kPrefetch, h->p.max_candidates);
   SRLA_TRY(cudaMemcpyAsync(s.h_entries, h->ws + h->L.rep_entries[q], (size_t)pre * sizeof(srla_entry),
-                           cudaMemcpyDeviceToHost, h->st));
+                           cudaMemcpyDeviceToHost, h->st_d2h));
+  SRLA_TRY(cudaEventRecord(s.ev, h->st_d2h));
   return SRLA_OK;
 }
 
@@ -243,7 +264,7 @@ int capture_graphs(srla_t* h) {
       rc = SRLA_E_CUDA;
       break;
     }
-    rc = with_cells(h->p.dr_bytes, [&](auto c) { return enqueue_end_slice<decltype(c)>(h, q); });
+    rc = with_cells(h->p.dr_bytes, [&](auto c) { return launch_end_slice<decltype(c)>(h, q); });
     const cudaError_t e = cudaStreamEndCapture(h->st, &g);
     if (rc == SRLA_OK && e != cudaSuccess) rc = SRLA_E_CUDA;
     if (rc == SRLA_OK && cudaGraphInstantiate(&h->graph[q], g, 0) != cudaSuccess) rc = SRLA_E_CUDA;
@@ -357,8 +378,11 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
   }
   if (cudaStreamCreateWithFlags(&h->st_h2d, cudaStreamNonBlocking) != cudaSuccess) rc = SRLA_E_CUDA;
   if (rc == SRLA_OK && (cudaStreamCreateWithFlags(&h->st_side, cudaStreamNonBlocking) != cudaSuccess ||
+                        cudaStreamCreateWithFlags(&h->st_d2h, cudaStreamNonBlocking) != cudaSuccess ||
                         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess))
+                        cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&h->ev_done[0], cudaEventDisableTiming) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&h->ev_done[1], cudaEventDisableTiming) != cudaSuccess))
     rc = SRLA_E_CUDA;
   for (int q = 0; q < 2 && rc == SRLA_OK; q++) {
     if (cudaEventCreateWithFlags(&h->ev_ready[q], cudaEventDisableTiming) != cudaSuccess ||
@@ -436,10 +460,10 @@ int srla_end_slice(srla_t* h, uint64_t* slice_id) {
     SRLA_TRY(cudaGraphLaunch(h->graph[q], h->st));
     h->launches += h->graph_launches;
   } else {
-    const int r = with_cells(h->p.dr_bytes, [&](auto c) { return enqueue_end_slice<decltype(c)>(h, q); });
+    const int r = with_cells(h->p.dr_bytes, [&](auto c) { return launch_end_slice<decltype(c)>(h, q); });
     if (r != SRLA_OK) return r;
   }
-  SRLA_TRY(cudaEventRecord(s.ev, h->st));
+  if (const int r = enqueue_report_copy(h, q); r != SRLA_OK) return r;
   s.slice = h->T;
   s.n_pkts = h->n_pkts_open;
   s.valid = true;
@@ -495,7 +519,6 @@ int srla_report(srla_t* h, uint64_t slice_id, srla_entry* out, size_t cap, size_
                              (take - pre) * sizeof(srla_entry), cudaMemcpyDeviceToHost, h->st_copy));
     SRLA_TRY(cudaStreamSynchronize(h->st_copy));
   }
-  if (st.overflow & 4u) return SRLA_E_TIMEOUT;
   if (st.overflow & 4u) return SRLA_E_TIMEOUT;
   if (st.overflow) return SRLA_E_CAPACITY;
   if (cap < n) return SRLA_E_NOMEM;
@@ -636,10 +659,15 @@ void srla_destroy(srla_t* h) {
     cudaStreamDestroy(h->st_copy);
   }
   if (h->st_h2d) cudaStreamDestroy(h->st_h2d);
+  if (h->st_d2h) {
+    cudaStreamSynchronize(h->st_d2h);
+    cudaStreamDestroy(h->st_d2h);
+  }
   if (h->st_side) cudaStreamDestroy(h->st_side);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
   for (int q = 0; q < 2; q++) {
+    if (h->ev_done[q]) cudaEventDestroy(h->ev_done[q]);
     if (h->slot[q].ev) cudaEventDestroy(h->slot[q].ev);
     if (h->graph[q]) cudaGraphExecDestroy(h->graph[q]);
     if (h->ev_ready[q]) cudaEventDestroy(h->ev_ready[q]);
@@ -714,7 +742,7 @@ extern "C" int srla_batch_report_static(const srla_params* p, const uint32_t* d_
   if (check(p) != SRLA_OK || (n_pairs && !d_pairs) || (cap && !out)) return SRLA_E_INVAL;
   srla_params q = *p;
   q.staging_pkts = 2;  // the batch is already on the device: no host staging area
-  const Layout L = layout_of(&q);
+  const Layout L = layout_of(&q, 1);  // one slice: one pair table
   if (L.total > (size_t)SRLA_STATIC_SCRATCH_BYTES) return SRLA_E_NOMEM;
   int dev = 0;
   SRLA_TRY(cudaGetDevice(&dev));

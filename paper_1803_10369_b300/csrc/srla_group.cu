@@ -204,7 +204,7 @@ LinkDesc make_desc(srla_group_t* g, const Slot& s) {
   D.sort_hist = reinterpret_cast<uint32_t*>(base + L.sort_hist);
   D.lut_est = reinterpret_cast<float*>(base + L.lut_est);
   D.lut_flags = reinterpret_cast<uint32_t*>(base + L.lut_flags);
-  D.ptab = L.pairs ? reinterpret_cast<unsigned long long*>(base + L.ptab) : nullptr;
+  D.ptab = L.pairs ? reinterpret_cast<unsigned long long*>(base + L.ptab[0]) : nullptr;
   return D;
 }
 
@@ -367,7 +367,7 @@ size_t srla_group_link_bytes(const srla_params* p) {
   // groups run the order-free candidate rule only (the inline test is a single-link mode)
   if (check(p) != SRLA_OK || p->mode != SRLA_MODE_ORDER_FREE) return 0;
   const srla_params q = link_params(*p);
-  return align_up(layout_of(&q).total);
+  return align_up(layout_of(&q, 1).total);
 }
 
 int srla_group_create(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_pkts, uint32_t max_report,
@@ -459,7 +459,7 @@ int srla_group_attach(srla_group_t* g, const srla_params* p, uint32_t* link) {
   // the slot's previous occupant may still be referenced by an enqueued slice end
   for (int q = 0; q < 2; q++) G_TRY(cudaEventSynchronize(g->ev[q]));
   const srla_params lp = link_params(*p);
-  const Layout L = layout_of(&lp);
+  const Layout L = layout_of(&lp, 1);
   size_t off = 0;
   if (!arena_alloc(g, L.total, &off)) return SRLA_E_NOMEM;
   Slot& s = g->slots[l];
@@ -473,7 +473,7 @@ int srla_group_attach(srla_group_t* g, const srla_params* p, uint32_t* link) {
   s.attached_at = g->G;
   char* base = g->ws + off;
   G_TRY(cudaMemsetAsync(base, 0, L.total, g->st));
-  if (L.pairs) G_TRY(cudaMemsetAsync(base + L.ptab, 0xFF, ((size_t)L.pmask + 1) * 8, g->st));
+  if (L.pairs) G_TRY(cudaMemsetAsync(base + L.ptab[0], 0xFF, ((size_t)L.pmask + 1) * 8, g->st));
   Ctl c{};
   c.T = s.T;
   c.tm = (uint32_t)(s.T % ((1u << lp.z) - 1u));
@@ -651,7 +651,7 @@ int srla_group_autotune(srla_group_t* g, int reps, uint32_t* best_threads, uint3
       // sampled-host inserts repeat the slice's own, so the state after tuning is unchanged
       for (const Slot& s : g->slots)
         if (s.active && s.L.pairs)
-          r = r ? r : gerr(cudaMemsetAsync(g->ws + s.off + s.L.ptab, 0xFF, ((size_t)s.L.pmask + 1) * 8, g->st));
+          r = r ? r : gerr(cudaMemsetAsync(g->ws + s.off + s.L.ptab[0], 0xFF, ((size_t)s.L.pmask + 1) * 8, g->st));
       r = r ? r : gerr(cudaMemsetAsync(&g->gctl()->next_task, 0, sizeof(unsigned), g->st));
       r = r ? r : gerr(cudaMemcpyAsync(g->ws + g->F.tasks, g->h_tasks[q], sizeof(TaskHeader) + sizeof(ScanTask) * g->pending.size(),
                                        cudaMemcpyHostToDevice, g->st));
@@ -682,7 +682,7 @@ int srla_group_autotune(srla_group_t* g, int reps, uint32_t* best_threads, uint3
   // the slice end starts from empty pair tables and a zero task counter, as without tuning
   for (const Slot& s : g->slots)
     if (s.active && s.L.pairs)
-      r = r ? r : gerr(cudaMemsetAsync(g->ws + s.off + s.L.ptab, 0xFF, ((size_t)s.L.pmask + 1) * 8, g->st));
+      r = r ? r : gerr(cudaMemsetAsync(g->ws + s.off + s.L.ptab[0], 0xFF, ((size_t)s.L.pmask + 1) * 8, g->st));
   r = r ? r : gerr(cudaMemsetAsync(&g->gctl()->next_task, 0, sizeof(unsigned), g->st));
   g->scan_threads = threads[best / 3];
   g->task_pkts = tasks[best % 3];

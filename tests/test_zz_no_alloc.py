@@ -36,7 +36,6 @@ def test_static_scratch_report_matches_workspace_path(variant, cuda_device):
         w = w.replace(dr_bytes=2, z=16, k=8, theta=128)
     ha, hb = synth.hash_coefficients(w.hash_seed, w.u + 3)
     params = srla.params_for(w, ha, hb)
-    assert srla.workspace_bytes(params) < srla.STATIC_SCRATCH_BYTES
     for call in range(2):  # two calls in a row, different batches
         pk = synth.generate_slice(w.traffic, 3 + call, device=cuda_device)
         got = srla.batch_report_static(params, pk)

@@ -396,63 +396,75 @@ __device__ __forceinline__ uint32_t union_count(const CellT* __restrict__ arr, u
   return union_count_w<CellT, 1, kFresh>(arr, v, cells, u, mycol, win, lane);
 }
 
-// Same count as union_count, for a caller that only needs to know whether it reaches
-// `need`: rows are joined one at a time and the join stops as soon as fewer than `need`
-// cells remain inside the window in every row so far (the union can only shrink).  The
-// result is exact when it is >= need; below need it is some value < need.
-// |URE|^k of two hosts at once (their row loads overlap), for a caller that only needs to
-// know whether each reaches `need`: rows are joined one at a time, and a host stops as soon
-// as fewer than `need` cells remain inside the window in every row so far (the union can
-// only shrink).  A count is exact when it is >= need; below need it is some value < need.
-template <typename CellT, int WPL, bool kFresh = false>
-__device__ __forceinline__ void union_count_atleast2_w(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
-                                                       uint32_t u, uint32_t col0, uint32_t col1, const Win& win,
-                                                       uint32_t need, int lane, uint32_t& out0, uint32_t& out1) {
+// The count of union_count for H hosts at once (their row loads overlap), for a caller that
+// only needs to know whether each reaches `need`: rows are joined one at a time, and a host
+// stops as soon as fewer than `need` cells remain inside the window in every row so far (the
+// union can only shrink).  A count is exact when it is >= need; below need it is some value
+// < need.
+template <typename CellT, int WPL, int H, bool kFresh = false>
+__device__ __forceinline__ void union_count_atleast_w(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
+                                                      uint32_t u, const uint32_t (&col)[H], const Win& win,
+                                                      uint32_t need, int lane, uint32_t (&out)[H]) {
   const uint32_t R = run_words<CellT>(cells);
   const uint32_t w0 = (uint32_t)lane * WPL;
   const bool ok = w0 < R;
-  uint32_t m0[WPL], m1[WPL];
+  uint32_t m[H][WPL];
+  bool live[H];
 #pragma unroll
-  for (int q = 0; q < WPL; q++) m0[q] = m1[q] = ok ? 0xFFFFFFFFu : 0u;
-  bool live0 = true, live1 = true;
-  out0 = out1 = 0;
-  for (uint32_t i = 0; i < u && (live0 || live1); i++) {
-    const uint32_t c0 = __shfl_sync(kFull, col0, (int)i), c1 = __shfl_sync(kFull, col1, (int)i);
-    uint32_t wd0[WPL], wd1[WPL];
-    if (ok && live0) load_run<CellT, WPL, kFresh>(arr, v, cells, i, c0, w0, wd0);
-    if (ok && live1) load_run<CellT, WPL, kFresh>(arr, v, cells, i, c1, w0, wd1);
-    uint32_t p0 = 0, p1 = 0;
+  for (int h = 0; h < H; h++) {
+    live[h] = true;
+    out[h] = 0;
 #pragma unroll
-    for (int q = 0; q < WPL; q++) {
-      if (ok && live0) m0[q] &= window_mask<CellT>(wd0[q], win);
-      if (ok && live1) m1[q] &= window_mask<CellT>(wd1[q], win);
-      p0 += __popc(m0[q]);
-      p1 += __popc(m1[q]);
+    for (int q = 0; q < WPL; q++) m[h][q] = ok ? 0xFFFFFFFFu : 0u;
+  }
+  bool any = true;
+  for (uint32_t i = 0; i < u && any; i++) {
+    uint32_t wd[H][WPL];
+#pragma unroll
+    for (int h = 0; h < H; h++) {  // every live host's row in flight before any is used
+      const uint32_t c = __shfl_sync(kFull, col[h], (int)i);
+      if (ok && live[h]) load_run<CellT, WPL, kFresh>(arr, v, cells, i, c, w0, wd[h]);
     }
-    if (live0) {
-      out0 = cells_of_bits<CellT>(warp_sum(p0));
-      live0 = out0 >= need;
-    }
-    if (live1) {
-      out1 = cells_of_bits<CellT>(warp_sum(p1));
-      live1 = out1 >= need;
+    any = false;
+#pragma unroll
+    for (int h = 0; h < H; h++) {
+      uint32_t p = 0;
+#pragma unroll
+      for (int q = 0; q < WPL; q++) {
+        if (ok && live[h]) m[h][q] &= window_mask<CellT>(wd[h][q], win);
+        p += __popc(m[h][q]);
+      }
+      if (live[h]) {
+        out[h] = cells_of_bits<CellT>(warp_sum(p));
+        live[h] = out[h] >= need;
+      }
+      any |= live[h];
     }
   }
+}
+
+// Lane i < u holds the hosts' columns of row i.
+template <typename CellT, int H, bool kFresh = false>
+__device__ __forceinline__ void union_count_atleast(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
+                                                    uint32_t u, const uint32_t (&col)[H], const Win& win,
+                                                    uint32_t need, int lane, uint32_t (&out)[H]) {
+  const uint32_t R = run_words<CellT>(cells);
+  if (R <= 32) return union_count_atleast_w<CellT, 1, H, kFresh>(arr, v, cells, u, col, win, need, lane, out);
+  if (R <= 64) return union_count_atleast_w<CellT, 2, H, kFresh>(arr, v, cells, u, col, win, need, lane, out);
+  if (R <= 128) return union_count_atleast_w<CellT, 4, H, kFresh>(arr, v, cells, u, col, win, need, lane, out);
+#pragma unroll
+  for (int h = 0; h < H; h++) out[h] = union_count<CellT, kFresh>(arr, v, cells, u, col[h], win, lane);
 }
 
 template <typename CellT, bool kFresh = false>
 __device__ __forceinline__ void union_count_atleast2(const CellT* __restrict__ arr, uint32_t v, uint32_t cells,
                                                      uint32_t u, uint32_t col0, uint32_t col1, const Win& win,
                                                      uint32_t need, int lane, uint32_t& out0, uint32_t& out1) {
-  const uint32_t R = run_words<CellT>(cells);
-  if (R <= 32)
-    return union_count_atleast2_w<CellT, 1, kFresh>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
-  if (R <= 64)
-    return union_count_atleast2_w<CellT, 2, kFresh>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
-  if (R <= 128)
-    return union_count_atleast2_w<CellT, 4, kFresh>(arr, v, cells, u, col0, col1, win, need, lane, out0, out1);
-  out0 = union_count<CellT, kFresh>(arr, v, cells, u, col0, win, lane);
-  out1 = union_count<CellT, kFresh>(arr, v, cells, u, col1, win, lane);
+  const uint32_t col[2] = {col0, col1};
+  uint32_t out[2];
+  union_count_atleast<CellT, 2, kFresh>(arr, v, cells, u, col, win, need, lane, out);
+  out0 = out[0];
+  out1 = out[1];
 }
 
 }  // namespace srla

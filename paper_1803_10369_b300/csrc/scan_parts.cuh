@@ -438,38 +438,45 @@ __device__ __forceinline__ void filter_admit(Ctl* ctl, unsigned long long* ctab,
 // advanced, per-slice counters cleared, the candidate list of T emptied (the carried list of
 // T+1 stays), and the pair-table policy for T+1 chosen from T's counts (kept on while it
 // finds repeats for at least a quarter of the block misses; re-tried every 16 slices).
-__device__ __forceinline__ void close_slice(const Geo& geo, Ctl* ctl, srla_slice_stats* st, uint32_t umax,
-                                            uint32_t cmax) {
-  const unsigned long long T = ctl->T;
+// Every field is loaded before anything is written, so the single closing thread waits for
+// one round trip, not one per field.
+__device__ __forceinline__ void close_slice(const Geo& geo, Ctl* __restrict__ ctl, srla_slice_stats* __restrict__ st,
+                                            uint32_t umax, uint32_t cmax) {
+  const Ctl c = *ctl;
+  const unsigned long long T = c.T;
   const int par = (int)(T & 1);
-  st->slice = T;
-  st->n_pkts = 0;
-  st->n_sampled = min(ctl->n_sampled, umax);
-  st->n_new = ctl->n_new;
-  st->n_candidates = min(ctl->cat_count[par], cmax);
-  st->n_carry_out = min(ctl->cat_count[par ^ 1], cmax);
-  st->w_star = min(ctl->w_star, geo.gl + 1u);
-  st->overflow = ctl->overflow;
-  st->up = ctl->up;
+  srla_slice_stats s;
+  s.slice = T;
+  s.n_pkts = 0;
+  s.n_sampled = min(c.n_sampled, umax);
+  s.n_new = c.n_new;
+  s.n_candidates = min(c.cat_count[par], cmax);
+  s.n_carry_out = min(c.cat_count[par ^ 1], cmax);
+  s.w_star = min(c.w_star, geo.gl + 1u);
+  s.overflow = c.overflow;
+  s.up = c.up;
+  Ctl n = c;
   for (int i = 0; i < SRLA_MAX_ROWS; i++) {
-    st->census[i] = ctl->census[i];
-    ctl->census[i] = 0;
+    s.census[i] = c.census[i];
+    n.census[i] = 0;
   }
-  ctl->T = T + 1;
-  ctl->tm = (ctl->tm + 1u == geo.P) ? 0u : ctl->tm + 1u;
-  ctl->n_sampled = 0;
-  ctl->n_new = 0;
-  ctl->cat_count[par] = 0;
-  ctl->overflow = ctl->overflow_next;
-  ctl->overflow_next = 0;
-  ctl->blocks_done = 0;
-  ctl->bar_count = 0;
-  ctl->w_star = geo.gl + 1u;
-  const bool measured = ctl->pair_mode != 0;
-  const bool worth = 4ull * ctl->n_gdup >= (unsigned long long)ctl->n_miss;
-  ctl->pair_mode = (measured ? worth : false) || ((T + 1) % 16 == 0) ? 1u : 0u;
-  ctl->n_miss = 0;
-  ctl->n_gdup = 0;
+  *st = s;
+  n.T = T + 1;
+  n.tm = (c.tm + 1u == geo.P) ? 0u : c.tm + 1u;
+  n.n_sampled = 0;
+  n.n_new = 0;
+  n.cat_count[par] = 0;
+  n.overflow = c.overflow_next;
+  n.overflow_next = 0;
+  n.blocks_done = 0;
+  n.bar_count = 0;
+  n.w_star = geo.gl + 1u;
+  const bool measured = c.pair_mode != 0;
+  const bool worth = 4ull * c.n_gdup >= (unsigned long long)c.n_miss;
+  n.pair_mode = (measured ? worth : false) || ((T + 1) % 16 == 0) ? 1u : 0u;
+  n.n_miss = 0;
+  n.n_gdup = 0;
+  *ctl = n;
   __threadfence();
 }
 

@@ -72,10 +72,13 @@ __device__ __forceinline__ void bitonic_block(uint32_t* list, uint32_t n, uint32
   while (N < n) N <<= 1;
   for (uint32_t x = threadIdx.x; x < N; x += blockDim.x) smem[x] = x < n ? list[x] : 0xFFFFFFFFu;
   __syncthreads();
+  // Pair t of a stage with distance j (a power of two) is (i, i + j), i = 2j*(t/j) + t%j.
+  // For j <= 32 the 32 pairs of a warp stay inside one run of 64 elements from stage to
+  // stage, so those stages only need the warp to agree (__syncwarp).
   for (uint32_t k = 2; k <= N; k <<= 1) {
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
       for (uint32_t t = threadIdx.x; t < N / 2; t += blockDim.x) {
-        const uint32_t i = 2 * j * (t / j) + (t % j);  // lower index of the pair
+        const uint32_t i = ((t & ~(j - 1u)) << 1) | (t & (j - 1u));  // lower index of the pair
         const uint32_t l = i + j;
         const bool up = (i & k) == 0;
         const uint32_t a = smem[i], b = smem[l];
@@ -84,9 +87,14 @@ __device__ __forceinline__ void bitonic_block(uint32_t* list, uint32_t n, uint32
           smem[l] = a;
         }
       }
-      __syncthreads();
+      // the next stage is (k, j/2), or (2k, k) after j = 1
+      if (j > 32 || (j == 1 && k > 32))
+        __syncthreads();
+      else
+        __syncwarp();
     }
   }
+  __syncthreads();
   for (uint32_t x = threadIdx.x; x < n; x += blockDim.x) list[x] = smem[x];
 }
 

@@ -34,6 +34,8 @@ struct LinkDesc {
   unsigned long long* ptab;  // per-slice pair table, or null
 };
 
+constexpr int kGroupSeenLog2 = 12;  // pairs remembered per group scan block (several per SM)
+
 // One packet batch of one link for the group scan (at most kTaskPkts packets).
 struct ScanTask {
   unsigned long long ptr;  // device address of interleaved (aip, bip) uint32 pairs
@@ -107,7 +109,7 @@ __device__ __forceinline__ void group_scan_task(const ScanTask& t, const LinkDes
       const unsigned long long key = ((unsigned long long)a[j] << 32) | b[j];
       bool miss = false;
       if (ok[j]) {
-        const uint32_t h = seen_slot(key);
+        const uint32_t h = seen_slot<kGroupSeenLog2>(key);
         if (key == kNoPair || seen[h] != key) {
           miss = true;
           if (key != kNoPair) seen[h] = key;
@@ -140,7 +142,7 @@ template <int kThreads>
 __global__ void __launch_bounds__(kThreads) kg_scan(const LinkDesc* __restrict__ descs,
                                                     const TaskHeader* __restrict__ thdr, GroupCtl* __restrict__ gctl) {
   const ScanTask* tasks = reinterpret_cast<const ScanTask*>(thdr + 1);
-  __shared__ unsigned long long seen_mem[kSeen];
+  __shared__ unsigned long long seen_mem[1 << kGroupSeenLog2];
   __shared__ unsigned long long queue_mem[kThreads / 32][2][kQueue];
   __shared__ LinkDesc sdesc;
   __shared__ ScanTask stask;
@@ -163,7 +165,7 @@ __global__ void __launch_bounds__(kThreads) kg_scan(const LinkDesc* __restrict__
       uint32_t* dst = reinterpret_cast<uint32_t*>(&sdesc);
       for (int x = threadIdx.x; x < (int)(sizeof(LinkDesc) / 4); x += kThreads) dst[x] = src[x];
     }
-    for (int x = threadIdx.x; x < kSeen; x += kThreads) seen[x] = kNoPair;
+    for (int x = threadIdx.x; x < (1 << kGroupSeenLog2); x += kThreads) seen[x] = kNoPair;
     __syncthreads();
     ScanQueues Q{queue_mem[warp][0], queue_mem[warp][1], 0u, 0u};
     uint32_t n_miss = 0, n_gdup = 0;

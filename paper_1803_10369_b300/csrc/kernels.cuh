@@ -11,17 +11,23 @@ namespace srla {
 // next iteration's packets are loaded before the current ones are scanned.  kInline: the
 // candidate test of Algorithm 2 runs at packet time (SRLA_MODE_INLINE); every packet is
 // scanned (no pair de-duplication), since each one runs the test on the SRE as it stands.
+// Shared memory of the scan: the block's table of recent pairs and two queues per warp.
+template <bool kInline>
+constexpr size_t scan_smem_bytes() {
+  return (size_t)kSeen * 8 + (size_t)((kInline ? kScanThreadsInline : kScanThreads) / 32) * 2 * kQueue * 8;
+}
+
 template <typename CellT, bool kVec, bool kInline = false>
-__global__ void __launch_bounds__(kScanThreads, kInline ? 2 : 4) k_scan(const uint32_t* __restrict__ pairs, uint64_t n, Geo geo,
+__global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, kInline ? 2 : 1) k_scan(const uint32_t* __restrict__ pairs, uint64_t n, Geo geo,
                                                           const __grid_constant__ Coef coef, CellT* __restrict__ re,
                                                           CellT* __restrict__ le, Ctl* __restrict__ ctl,
                                                           unsigned long long* __restrict__ utab, uint32_t umask,
                                                           uint32_t* __restrict__ ulist, uint32_t umax,
                                                           unsigned long long* __restrict__ ptab, uint32_t pmask,
                                                           const __grid_constant__ InlineArgs ia) {
-  __shared__ unsigned long long seen_mem[kSeen];
-  __shared__ unsigned long long queue_mem[kScanThreads / 32][2][kQueue];
-  volatile unsigned long long* seen = seen_mem;
+  extern __shared__ unsigned long long scan_smem[];
+  volatile unsigned long long* seen = scan_smem;
+  auto queue_mem = reinterpret_cast<unsigned long long(*)[2][kQueue]>(scan_smem + kSeen);
   for (int x = threadIdx.x; x < kSeen; x += blockDim.x) seen[x] = kNoPair;
   __syncthreads();
   if (kInline || (ptab && ctl->pair_mode == 0)) ptab = nullptr;

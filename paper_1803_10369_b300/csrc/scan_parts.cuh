@@ -22,10 +22,11 @@ namespace srla {
 // talk to few peers) then cost one shared-memory probe instead of u + u/2^tau scattered
 // stores that would all land on the same L2 sectors.
 
-constexpr int kSeenLog2 = 12;
-constexpr int kSeen = 1 << kSeenLog2;                      // pairs remembered per block
+constexpr int kSeenLog2 = 14;
+constexpr int kSeen = 1 << kSeenLog2;                      // pairs remembered per block (one block per SM)
 constexpr unsigned long long kNoPair = ~0ull;              // empty slot; that pair is never cached
-constexpr int kScanThreads = 256;
+constexpr int kScanThreads = 1024;                         // one block per SM shares one table
+constexpr int kScanThreadsInline = 256;                    // the inline-test variant (more registers)
 constexpr int kPairProbes = 2;                             // probes into the slice's pair table
 
 // Behind the per-block table sits one table of the pairs scanned anywhere on the GPU in the
@@ -53,8 +54,9 @@ __device__ __forceinline__ bool pair_claim_from(unsigned long long* __restrict__
   return true;
 }
 
+template <int kLog2 = kSeenLog2>
 __device__ __forceinline__ uint32_t seen_slot(unsigned long long key) {
-  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - kSeenLog2));
+  return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - kLog2));
 }
 
 // Full scan of one pair per lane (a dense batch): Algorithm 2's DRsets, and the sampled host

@@ -127,11 +127,13 @@ int launch_scan(srla_t* h, const uint32_t* pairs, uint64_t n) {
   const bool vec = (reinterpret_cast<uintptr_t>(pairs) & 15u) == 0;
   auto kern = inline_mode(h) ? (vec ? k_scan<CellT, true, true> : k_scan<CellT, false, true>)
                              : (vec ? k_scan<CellT, true> : k_scan<CellT, false>);
-  const int grid = grid_for(n, kScanThreads * 4, h->sms * std::max(1, h->occ_scan[vec ? 1 : 0]));
+  const int threads = inline_mode(h) ? kScanThreadsInline : kScanThreads;
+  const size_t smem = inline_mode(h) ? scan_smem_bytes<true>() : scan_smem_bytes<false>();
+  const int grid = grid_for(n, threads * 4, h->sms * std::max(1, h->occ_scan[vec ? 1 : 0]));
   CellT* re = h->at<CellT>(h->L.re);
   CellT* le = h->at<CellT>(h->L.le);
   h->launches++;
-  kern<<<grid, kScanThreads, 0, h->st>>>(pairs, n, h->geo, h->coef, re, le, h->ctl(),
+  kern<<<grid, threads, smem, h->st>>>(pairs, n, h->geo, h->coef, re, le, h->ctl(),
                                          h->at<unsigned long long>(h->L.utab), h->L.umask,
                                          h->at<uint32_t>(h->L.ulist), h->p.max_sampled,
                                          pair_table(h, h->T), h->L.pmask,
@@ -292,10 +294,14 @@ int occupancy(srla_t* h) {
   const int rs = with_cells(h->p.dr_bytes, [&](auto cell) {
     using CellT = decltype(cell);
     const bool inl = inline_mode(h);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, inl ? k_scan<CellT, false, true> : k_scan<CellT, false>,
-                                                      kScanThreads, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, inl ? k_scan<CellT, true, true> : k_scan<CellT, true>,
-                                                      kScanThreads, 0) != cudaSuccess)
+    auto k0 = inl ? k_scan<CellT, false, true> : k_scan<CellT, false>;
+    auto k1 = inl ? k_scan<CellT, true, true> : k_scan<CellT, true>;
+    const int threads = inl ? kScanThreadsInline : kScanThreads;
+    const size_t smem = inl ? scan_smem_bytes<true>() : scan_smem_bytes<false>();
+    if (cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k0, threads, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1, threads, smem) != cudaSuccess)
       return SRLA_E_CUDA;
     return SRLA_OK;
   });

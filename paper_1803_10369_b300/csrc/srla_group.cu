@@ -149,6 +149,22 @@ bool arena_alloc(srla_group_t* g, size_t bytes, size_t* off) {
   return false;
 }
 
+// The same from the top of the arena: the sweep work lists, rebuilt at every membership
+// change, then never leave holes between link regions (which are taken from the bottom).
+bool arena_alloc_top(srla_group_t* g, size_t bytes, size_t* off) {
+  bytes = align_up(bytes);
+  for (size_t i = g->free_list.size(); i-- > 0;) {
+    Region& r = g->free_list[i];
+    if (r.bytes >= bytes) {
+      r.bytes -= bytes;
+      *off = r.off + r.bytes;
+      if (r.bytes == 0) g->free_list.erase(g->free_list.begin() + (long)i);
+      return true;
+    }
+  }
+  return false;
+}
+
 void arena_free(srla_group_t* g, size_t off, size_t bytes) {
   bytes = align_up(bytes);
   if (!bytes) return;
@@ -240,7 +256,7 @@ int rebuild_work(srla_group_t* g) {
   if (g->chunk_bytes) arena_free(g, g->chunk_off, g->chunk_bytes);
   g->chunk_bytes = 0;
   size_t off = 0;
-  if (need && !arena_alloc(g, need, &off)) return SRLA_E_NOMEM;
+  if (need && !arena_alloc_top(g, need, &off)) return SRLA_E_NOMEM;
   g->chunk_off = off;
   g->chunk_bytes = need;
   SweepChunk* dchunks = reinterpret_cast<SweepChunk*>(g->ws + off);

@@ -207,9 +207,9 @@ void srla_destroy(srla_t *h);
  * the host.
  *
  * Scratch: a fixed array of SRLA_STATIC_SCRATCH_BYTES compiled into the library, present on
- * every GPU that loads the library until the process exits.  Parameters whose workspace
- * (srla_workspace_bytes with a 2-packet staging area) exceeds it are rejected with
- * SRLA_E_NOMEM before any GPU work.  The first call on a device looks up the array's device
+ * every GPU that loads the library until the process exits.  Parameters whose one-slice
+ * layout (the workspace layout with one pair table and no host staging, a little less than
+ * srla_workspace_bytes) exceeds it are rejected with SRLA_E_NOMEM before any GPU work.  The first call on a device looks up the array's device
  * address (and sets a kernel attribute) for that device; make that first call before any
  * stream capture.  Every call clears and reuses the same array, so calls that overlap on the
  * GPU (other streams, other host threads) race and corrupt each other: serialize them.
@@ -219,6 +219,17 @@ void srla_destroy(srla_t *h);
 int srla_batch_report_static(const srla_params *p, const uint32_t *d_pairs, uint64_t n_pairs,
                              void *stream, srla_entry *out, size_t cap, size_t *n_out,
                              srla_slice_stats *stats);
+
+/* Self-test of the bounded device waits (the grid barrier of the cooperative candidate
+ * sort; the group sort uses the same pattern).  Launches `blocks` (2..64) blocks on `stream`
+ * that meet at one barrier, of which the last `absent` (< blocks) never arrive; the others
+ * poll at most spin_limit times (each poll sleeps about 64 ns), then give up and flag the
+ * timeout.  dev_scratch: caller-owned device memory of at least 256 bytes, 16-byte aligned
+ * (cleared and used as a control block).  Returns SRLA_E_TIMEOUT when the wait gave up,
+ * SRLA_OK when every block arrived; the CUDA context stays usable either way (no trap, no
+ * fault).  Errors: INVAL, CUDA. */
+int srla_wait_selftest(void *dev_scratch, size_t bytes, void *stream, uint32_t blocks, uint32_t absent,
+                       uint32_t spin_limit);
 const char *srla_strerror(int code);
 
 

@@ -31,5 +31,11 @@ __global__ void __launch_bounds__(kSortThreads) k_sort(Ctl* __restrict__ ctl, ui
   }
 }
 
+// Self-test of the bounded wait: two blocks meet at one grid barrier, but the last `absent`
+// blocks never arrive, so the others give up after spin_limit polls and flag the timeout.
+__global__ void k_wait_selftest(Ctl* ctl, unsigned absent, unsigned spin_limit) {
+  if (blockIdx.x >= gridDim.x - absent) return;  // this block never joins
+  grid_barrier(ctl, gridDim.x, spin_limit);
+}
 
 }  // namespace srla

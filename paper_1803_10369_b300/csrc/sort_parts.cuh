@@ -107,7 +107,7 @@ __device__ __forceinline__ void bitonic_block(uint32_t* list, uint32_t n, uint32
 constexpr unsigned kBarrierSpinLimit = 1u << 24;
 
 // Returns false (in every thread of the block) if the wait gave up.
-__device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks) {
+__device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks, unsigned spin_limit = kBarrierSpinLimit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -122,7 +122,7 @@ __device__ __forceinline__ bool grid_barrier(Ctl* ctl, unsigned nblocks) {
     } else {
       unsigned it = 0;
       while (*gen == g) {
-        if (++it > kBarrierSpinLimit) {
+        if (++it > spin_limit) {
           atomicOr(&ctl->overflow, 4u);
           ok = 0;
           break;

@@ -806,3 +806,20 @@ extern "C" int srla_batch_report_static(const srla_params* p, const uint32_t* d_
   if (cap < n) return SRLA_E_NOMEM;
   return SRLA_OK;
 }
+
+extern "C" int srla_wait_selftest(void* dev_scratch, size_t bytes, void* stream, uint32_t blocks, uint32_t absent,
+                                  uint32_t spin_limit) {
+  if (!dev_scratch || bytes < 256 || (reinterpret_cast<uintptr_t>(dev_scratch) & 15u) || blocks < 2 || blocks > 64 ||
+      absent >= blocks)
+    return SRLA_E_INVAL;
+  static_assert(sizeof(Ctl) <= 256, "control block fits the self-test scratch");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ctl* ctl = static_cast<Ctl*>(dev_scratch);
+  SRLA_TRY(cudaMemsetAsync(ctl, 0, sizeof(Ctl), st));
+  k_wait_selftest<<<blocks, 32, 0, st>>>(ctl, absent, spin_limit);
+  SRLA_TRY(cudaGetLastError());
+  unsigned overflow = 0;
+  SRLA_TRY(cudaMemcpyAsync(&overflow, &ctl->overflow, sizeof(overflow), cudaMemcpyDeviceToHost, st));
+  SRLA_TRY(cudaStreamSynchronize(st));
+  return (overflow & 4u) ? SRLA_E_TIMEOUT : SRLA_OK;
+}

@@ -70,6 +70,7 @@ SIGNATURES = {
     "srla_destroy": (None, [_P]),
     "srla_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "srla_batch_report_static": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P, _P, ctypes.c_size_t, _P, _P]),
+    "srla_wait_selftest": (ctypes.c_int, [_P, ctypes.c_size_t, _P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]),
     "srla_group_fixed_bytes": (ctypes.c_size_t, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32]),
     "srla_group_link_bytes": (ctypes.c_size_t, [_P]),
     "srla_group_create": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P,
@@ -146,6 +147,16 @@ def make_params(u, v, g, gl, dr_bytes, z, k, theta, hash_a, hash_b, start_slice=
         p.hash_a[r] = int(ha[r])
         p.hash_b[r] = int(hb[r])
     return p
+
+
+def wait_selftest(blocks=2, absent=1, spin_limit=10000, device="cuda") -> int:
+    """Run the bounded-wait self-test (srla_wait_selftest); returns its status code."""
+    import torch
+
+    scratch = torch.zeros(256, dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream(scratch.device)
+    return lib().srla_wait_selftest(ctypes.c_void_p(scratch.data_ptr()), 256, ctypes.c_void_p(stream.cuda_stream),
+                                    blocks, absent, spin_limit)
 
 
 def params_for(w, hash_a, hash_b, **over) -> srla_params:

@@ -350,6 +350,7 @@ def bench_srla(args):
     scan_avg_ms = statistics.mean(scan_ms)
     per_launch_pkts = pkts / K
     achieved = bpp * per_launch_pkts / (scan_avg_ms * 1e-3) / 1e9
+    store_roof = _store_roofline(w, tau, dev, stream, per_launch_pkts / (scan_avg_ms * 1e-3))
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpkts/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(elapsed_ms / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -359,7 +360,8 @@ def bench_srla(args):
         "scan_mpkts_s": round(per_launch_pkts / (scan_avg_ms * 1e-3) / 1e6, 3),
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 5), "traffic": _scan_traffic(w.name, int(per_launch_pkts)),
-                     "kernel": "k_scan", "bytes_per_pkt": bpp, "peak_kind": peak_kind},
+                     "kernel": "k_scan", "bytes_per_pkt": bpp, "peak_kind": peak_kind,
+                     "store_roofline": store_roof},
         "e2e": {"value": round(e2e, 3), "unit": "Mpkts/s", "h2d_bytes_per_step": int(8 * per_launch_pkts),
                 "d2h_bytes_per_step": int(statistics.mean(d2h))},
         "gpu_launches": int(launches),
@@ -378,6 +380,37 @@ def bench_srla(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()
+
+
+def _store_roofline(w, tau, dev, stream, scan_pkts_per_s):
+    """The scan against random stores: srla_scatter_probe writes cell-sized values to random
+    cells of a buffer the size of the link's recorders; a packet needs u SLE stores plus u
+    SRE stores for the 2^-tau sampled share.  pkts_per_s = stores/s / stores per packet."""
+    import torch
+
+    from paper_1803_10369_b300 import srla
+
+    cell = w.dr_bytes if w.dr_bytes else 1
+    cells = w.u * w.v * (w.g + w.gl) // (1 if w.dr_bytes else 8)
+    buf = torch.empty(cells * cell, dtype=torch.uint8, device=dev)
+    per_pkt = w.u * (1 + 2.0 ** -tau)
+    n = int(per_pkt * 5_000_000)
+    rates = []
+    with torch.cuda.stream(stream):
+        for rep in range(4):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            srla.scatter_probe(buf, cell, n, seed=rep + 1, stream=stream)
+            e1.record(stream)
+            e1.synchronize()
+            if rep:
+                rates.append(n / (e0.elapsed_time(e1) * 1e-3))
+    del buf
+    r = statistics.median(rates)
+    return {"stores_per_s": round(r, 0), "footprint_bytes": cells * cell, "cell_bytes": cell,
+            "stores_per_pkt": per_pkt, "pkts_per_s": round(r / per_pkt, 0),
+            "scan_vs_stores": round(scan_pkts_per_s / (r / per_pkt), 4),
+            "note": "random stores over the recorders' footprint; the scan de-duplicates pairs, so it can exceed 1"}
 
 
 def _pctl(xs, q):

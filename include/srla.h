@@ -230,6 +230,15 @@ int srla_batch_report_static(const srla_params *p, const uint32_t *d_pairs, uint
  * fault).  Errors: INVAL, CUDA. */
 int srla_wait_selftest(void *dev_scratch, size_t bytes, void *stream, uint32_t blocks, uint32_t absent,
                        uint32_t spin_limit);
+
+/* Store roofline probe (a measurement aid, not part of the method): enqueues on `stream`
+ * n_stores stores of cell_bytes (1, 2 or 4) each to pseudo-random cells of the caller's
+ * device buffer dev_buf of `bytes` bytes (at least one cell): the access
+ * shape of the scan's recorder updates (Algorithm 2) without their hashing,
+ * de-duplication or sampling.  Time it with events on the same stream.  Overwrites the
+ * buffer.  Errors: INVAL, CUDA. */
+int srla_scatter_probe(void *dev_buf, size_t bytes, uint32_t cell_bytes, uint64_t n_stores, uint64_t seed,
+                       void *stream);
 const char *srla_strerror(int code);
 
 

@@ -366,4 +366,21 @@ __global__ void k_insert_carried(const uint32_t* __restrict__ hosts, uint32_t n,
   }
 }
 
+// Random-store probe (the store roofline of the scan): n stores of a cell-sized value to
+// pseudo-random cells of a footprint of `cells` cells, i.e. the access shape of the scan's
+// DRsets without their hashing, de-duplication or sampling.  The cell of store i comes from
+// a 64-bit mix of i (the SplitMix64 finaliser of Steele, Lea and Flood) scaled to [0, cells)
+// by a multiply-high.
+template <typename CellT>
+__global__ void __launch_bounds__(256) k_scatter_probe(CellT* __restrict__ buf, uint64_t cells, uint64_t n,
+                                                       uint64_t seed) {
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
+    uint64_t z = i + seed * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    buf[__umul64hi(z, cells)] = (CellT)(i | 1u);
+  }
+}
+
 }  // namespace srla

@@ -823,3 +823,22 @@ extern "C" int srla_wait_selftest(void* dev_scratch, size_t bytes, void* stream,
   SRLA_TRY(cudaStreamSynchronize(st));
   return (overflow & 4u) ? SRLA_E_TIMEOUT : SRLA_OK;
 }
+
+extern "C" int srla_scatter_probe(void* dev_buf, size_t bytes, uint32_t cell_bytes, uint64_t n_stores, uint64_t seed,
+                                  void* stream) {
+  if (!dev_buf || (cell_bytes != 1 && cell_bytes != 2 && cell_bytes != 4)) return SRLA_E_INVAL;
+  const uint64_t cells = bytes / cell_bytes;
+  if (!cells) return SRLA_E_INVAL;
+  int dev = 0, sms = 0;
+  SRLA_TRY(cudaGetDevice(&dev));
+  SRLA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int grid = grid_for(n_stores, 256, sms * 8);
+  if (cell_bytes == 1)
+    k_scatter_probe<uint8_t><<<grid, 256, 0, st>>>(static_cast<uint8_t*>(dev_buf), cells, n_stores, seed);
+  else if (cell_bytes == 2)
+    k_scatter_probe<uint16_t><<<grid, 256, 0, st>>>(static_cast<uint16_t*>(dev_buf), cells, n_stores, seed);
+  else
+    k_scatter_probe<uint32_t><<<grid, 256, 0, st>>>(static_cast<uint32_t*>(dev_buf), cells, n_stores, seed);
+  return cuda_err(cudaGetLastError());
+}

@@ -119,3 +119,17 @@ def test_strerror():
     L = srla.lib()
     for c in range(0, -7, -1):
         assert L.srla_strerror(c)
+
+
+def test_measurement_and_selftest_entry_points_validate_arguments():
+    """Argument checks happen before any GPU work (no device needed)."""
+    import ctypes
+
+    L = srla.lib()
+    fake = ctypes.c_void_p(256)
+    assert L.srla_scatter_probe(fake, 1024, 3, 10, 1, None) == srla.E_INVAL
+    assert L.srla_scatter_probe(fake, 1, 2, 10, 1, None) == srla.E_INVAL
+    assert L.srla_scatter_probe(None, 1024, 2, 10, 1, None) == srla.E_INVAL
+    assert L.srla_wait_selftest(fake, 256, None, 1, 0, 10) == srla.E_INVAL
+    assert L.srla_wait_selftest(fake, 256, None, 4, 4, 10) == srla.E_INVAL
+    assert L.srla_wait_selftest(fake, 128, None, 4, 1, 10) == srla.E_INVAL

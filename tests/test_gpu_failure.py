@@ -34,3 +34,13 @@ def test_context_usable_after_a_timeout(cuda_device):
         compare_reports(o.end_slice(), link.report(link.end_slice()), f"slice {s}")
     link.close()
     o.close()
+
+
+def test_store_probe_writes_the_footprint(cuda_device):
+    import torch
+
+    buf = torch.zeros(1 << 16, dtype=torch.uint8, device=cuda_device)
+    srla.scatter_probe(buf, 2, 1 << 18, seed=3)
+    torch.cuda.synchronize(cuda_device)
+    cells = buf.view(torch.int16)
+    assert int((cells != 0).sum()) > 0.9 * cells.numel()  # 8 stores per cell on average

@@ -251,37 +251,48 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
   const int lane = threadIdx.x & 31;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t idx = gw; idx < n; idx += nw) {
-    const uint32_t aip = clist[idx];
+  // 2n tasks: task i < n estimates candidate i (union SLE), task n + i runs its carry test
+  // (post-slide union SRE); the two gathers of a candidate run in different warps
+  for (uint32_t idx = gw; idx < 2 * n; idx += nw) {
+    const bool est = idx < n;
+    const uint32_t i = est ? idx : idx - n;
+    const uint32_t aip = clist[i];
     const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
-    const uint32_t w = union_count<CellT>(le, geo.v, geo.gl, geo.u, mycol, win, lane);
+    if (est) {
+      uint32_t origin = 0;
+      if (lane == 0) {  // issued before the gather, used after it
+        const uint32_t s = set_find(ctab, cmask, tag, aip);
+        origin = (s != 0xFFFFFFFFu) ? cflags[s] : 0u;
+      }
+      const uint32_t w = union_count<CellT>(le, geo.v, geo.gl, geo.u, mycol, win, lane);
+      if (lane == 0) {
+        srla_entry e;
+        e.aip = aip;
+        e.w = w;
+        e.est = lut_est[w];
+        e.flags = origin | lut_flags[w];
+        rep[i] = e;
+      }
+      continue;
+    }
     const uint32_t cw = union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, win_post, lane);
+    if (cw < geo.rho_g) continue;
     // inline mode: a carried host gets its SI bits in the next slice's indicators (Algorithm 3)
     uint32_t* si_next = par ? si0 : si1;
-    if (si_next && cw >= geo.rho_g && (uint32_t)lane < geo.u)
+    if (si_next && (uint32_t)lane < geo.u)
       atomicOr(si_next + (size_t)lane * geo.v + mycol, 1u << si_bit(coef, geo.u, aip));
     if (lane == 0) {
-      const uint32_t s = set_find(ctab, cmask, tag, aip);
-      const uint32_t origin = (s != 0xFFFFFFFFu) ? cflags[s] : 0u;
-      srla_entry e;
-      e.aip = aip;
-      e.w = w;
-      e.est = lut_est[w];
-      e.flags = origin | lut_flags[w];
-      rep[idx] = e;
-      if (cw >= geo.rho_g) {
-        uint32_t slot;
-        const int r = set_insert(ntab, cmask, ntag, aip, &slot);
-        if (r == 1) {
-          nflags[slot] = SRLA_CARRIED;
-          const unsigned at = atomicAdd(&ctl->cat_count[par ^ 1], 1u);
-          if (at < cmax)
-            nlist[at] = aip;
-          else
-            atomicOr(&ctl->overflow_next, 2u);
-        } else if (r < 0) {
+      uint32_t slot;
+      const int r = set_insert(ntab, cmask, ntag, aip, &slot);
+      if (r == 1) {
+        nflags[slot] = SRLA_CARRIED;
+        const unsigned at = atomicAdd(&ctl->cat_count[par ^ 1], 1u);
+        if (at < cmax)
+          nlist[at] = aip;
+        else
           atomicOr(&ctl->overflow_next, 2u);
-        }
+      } else if (r < 0) {
+        atomicOr(&ctl->overflow_next, 2u);
       }
     }
   }

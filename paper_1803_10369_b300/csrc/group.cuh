@@ -423,44 +423,49 @@ __global__ void __launch_bounds__(kSortThreads) kg_sort(const LinkDesc* __restri
 
 __device__ __forceinline__ bool grep_off_ok(uint32_t idx, uint32_t cap) { return idx < cap; }
 
-// One candidate of one link: union SLE weight, Eq. 9 lookup, report entry, carry test.
+// One task on one candidate of one link: the union SLE weight, Eq. 9 lookup and report
+// entry (est), or the carry test on the post-slide union SRE (!est).
 template <typename CellT>
-__device__ __forceinline__ void group_estimate_one(const LinkDesc& D, uint32_t idx, int lane, srla_entry* grep,
-                                                   uint32_t rep_cap, GroupCtl* gctl) {
+__device__ __forceinline__ void group_estimate_one(const LinkDesc& D, uint32_t idx, bool est, int lane,
+                                                   srla_entry* grep, uint32_t rep_cap, GroupCtl* gctl) {
   Ctl* ctl = D.ctl;
   const unsigned long long T = ctl->T;
   const int par = (int)(T & 1);
-  const uint32_t tag = slice_tag(T), ntag = slice_tag(T + 1);
-  const Win win = make_win<CellT>(ctl->tm, D.geo.P, D.geo.k);
-  const Win win_post = make_win<CellT>(ctl->tm, D.geo.P, D.geo.k - 1u);
-  const CellT* re = static_cast<const CellT*>(D.re);
-  const CellT* le = static_cast<const CellT*>(D.le);
   const uint32_t aip = D.clist[par][idx];
   const uint32_t mycol = (uint32_t)lane < D.geo.u ? hash61(D.coef.a[lane], D.coef.b[lane], aip) & D.geo.vmask : 0u;
-  const uint32_t w = union_count<CellT>(le, D.geo.v, D.geo.gl, D.geo.u, mycol, win, lane);
-  const uint32_t cw = union_count<CellT>(re, D.geo.v, D.geo.g, D.geo.u, mycol, win_post, lane);
-  if (lane == 0) {
-    const uint32_t s = set_find(D.ctab[par], D.cmask, tag, aip);
-    const uint32_t origin = (s != 0xFFFFFFFFu) ? D.cflags[par][s] : 0u;
-    srla_entry e;
-    e.aip = aip;
-    e.w = w;
-    e.est = D.lut_est[w];
-    e.flags = origin | D.lut_flags[w];
-    if (grep_off_ok(idx, rep_cap)) grep[idx] = e; else atomicOr(&gctl->overflow, 2u);
-    if (cw >= D.geo.rho_g) {
-      uint32_t slot;
-      const int r = set_insert(D.ctab[par ^ 1], D.cmask, ntag, aip, &slot);
-      if (r == 1) {
-        D.cflags[par ^ 1][slot] = SRLA_CARRIED;
-        const unsigned at = atomicAdd(&ctl->cat_count[par ^ 1], 1u);
-        if (at < D.cmax)
-          D.clist[par ^ 1][at] = aip;
-        else
-          atomicOr(&ctl->overflow_next, 2u);
-      } else if (r < 0) {
+  if (est) {
+    uint32_t origin = 0;
+    if (lane == 0) {  // issued before the gather, used after it
+      const uint32_t s = set_find(D.ctab[par], D.cmask, slice_tag(T), aip);
+      origin = (s != 0xFFFFFFFFu) ? D.cflags[par][s] : 0u;
+    }
+    const Win win = make_win<CellT>(ctl->tm, D.geo.P, D.geo.k);
+    const uint32_t w = union_count<CellT>(static_cast<const CellT*>(D.le), D.geo.v, D.geo.gl, D.geo.u, mycol, win, lane);
+    if (lane == 0) {
+      srla_entry e;
+      e.aip = aip;
+      e.w = w;
+      e.est = D.lut_est[w];
+      e.flags = origin | D.lut_flags[w];
+      if (grep_off_ok(idx, rep_cap)) grep[idx] = e; else atomicOr(&gctl->overflow, 2u);
+    }
+    return;
+  }
+  const Win win_post = make_win<CellT>(ctl->tm, D.geo.P, D.geo.k - 1u);
+  const uint32_t cw =
+      union_count<CellT>(static_cast<const CellT*>(D.re), D.geo.v, D.geo.g, D.geo.u, mycol, win_post, lane);
+  if (lane == 0 && cw >= D.geo.rho_g) {
+    uint32_t slot;
+    const int r = set_insert(D.ctab[par ^ 1], D.cmask, slice_tag(T + 1), aip, &slot);
+    if (r == 1) {
+      D.cflags[par ^ 1][slot] = SRLA_CARRIED;
+      const unsigned at = atomicAdd(&ctl->cat_count[par ^ 1], 1u);
+      if (at < D.cmax)
+        D.clist[par ^ 1][at] = aip;
+      else
         atomicOr(&ctl->overflow_next, 2u);
-      }
+    } else if (r < 0) {
+      atomicOr(&ctl->overflow_next, 2u);
     }
   }
 }
@@ -476,13 +481,16 @@ __global__ void __launch_bounds__(256) kg_estimate(const LinkDesc* __restrict__ 
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   const unsigned nl = gctl->n_links;
   const uint32_t total = rep_off[nl];  // every link's candidates in one flat range
-  for (uint32_t i = gw; i < total; i += nw) {
+  // 2 * total tasks: the estimate of every candidate, then the carry test of every candidate
+  for (uint32_t t = gw; t < 2 * total; t += nw) {
+    const bool est = t < total;
+    const uint32_t i = est ? t : t - total;
     const unsigned l = link_of(rep_off, nl, i);
     const LinkDesc& D = descs[l];
     const uint32_t off = rep_off[l];
     const uint32_t cap = gctl->rep_cap > off ? gctl->rep_cap - off : 0u;
     with_cells(D.cell_bytes,
-               [&](auto cell) { group_estimate_one<decltype(cell)>(D, i - off, lane, grep + off, cap, gctl); });
+               [&](auto cell) { group_estimate_one<decltype(cell)>(D, i - off, est, lane, grep + off, cap, gctl); });
   }
   __syncthreads();
   if (threadIdx.x == 0) {

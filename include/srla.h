@@ -70,7 +70,9 @@ extern "C" {
  *   max_candidates  candidate list entries per slice (new + carried)
  *   pair_slots_log2 size of the per-slice table of scanned pairs that lets the scan skip a
  *               pair already scanned in the open slice (it writes the same stamps): 0 gives
- *               2^21 slots, -1 disables the table, 10..28 choose 2^value slots (8 bytes each)
+ *               2^21 slots, -1 disables the table, 10..28 choose 2^value slots (8 bytes each;
+ *               a link's workspace holds two such tables, one per slice parity, so that the
+ *               next slice's is cleared while the current slice is closed)
  *   mode        SRLA_MODE_ORDER_FREE (0) or SRLA_MODE_INLINE (1).  In the inline mode the SI
  *               bit of a host is bits 28..31 of the sampling-role hash applied to aip, the
  *               SI bits are cleared at each slice end and set again for the carried hosts

@@ -38,6 +38,8 @@ def _args():
     ap.add_argument("--latency-slices", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--mode", default="order-free", choices=["order-free", "inline"],
+                    help="candidate rule of the single-link workloads (inline: Algorithm 2 as printed)")
     return ap.parse_args()
 
 
@@ -257,7 +259,8 @@ def bench_srla(args):
     # each rank monitors its own link: a different trace seed per rank
     spec = w.traffic if rank == 0 else w.replace(seed=w.traffic.seed + 1000 * rank).traffic
     ha, hb = synth.hash_coefficients(w.hash_seed, w.u + 3)
-    params = srla.params_for(w, ha, hb, staging_pkts=w.pkts_per_slice)
+    mode = srla.MODE_INLINE if args.mode == "inline" else srla.MODE_ORDER_FREE
+    params = srla.params_for(w, ha, hb, staging_pkts=w.pkts_per_slice, mode=mode)
     tau, rho_g, P = srla.derived(params)
     stream = torch.cuda.Stream(dev)
     link = srla.Link(params, device=dev, stream=stream)
@@ -354,7 +357,8 @@ def bench_srla(args):
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpkts/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(elapsed_ms / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {0: "u1", 1: "u8", 2: "u16"}[w.dr_bytes], "data": "synthetic", "config": _config(w),
+        "dtype": {0: "u1", 1: "u8", 2: "u16"}[w.dr_bytes], "data": "synthetic",
+        "config": {**_config(w), "mode": args.mode},
         "latency_ms": {"p50": round(p50, 4), "p99": round(p99, 4), "slices": n_lat,
                        "slice_end_gpu_p50": round(statistics.median(lat_gpu), 4)},
         "scan_mpkts_s": round(per_launch_pkts / (scan_avg_ms * 1e-3) / 1e6, 3),

@@ -11,10 +11,11 @@ namespace srla {
 // next iteration's packets are loaded before the current ones are scanned.  kInline: the
 // candidate test of Algorithm 2 runs at packet time (SRLA_MODE_INLINE); every packet is
 // scanned (no pair de-duplication), since each one runs the test on the SRE as it stands.
-// Shared memory of the scan: the block's table of recent pairs and two queues per warp.
+// Shared memory of the scan: the block's table of recent pairs (not in the inline mode,
+// which scans every packet) and two queues per warp.
 template <bool kInline>
 constexpr size_t scan_smem_bytes() {
-  return (size_t)kSeen * 8 + (size_t)((kInline ? kScanThreadsInline : kScanThreads) / 32) * 2 * kQueue * 8;
+  return (kInline ? 0 : (size_t)kSeen * 8) + (size_t)((kInline ? kScanThreadsInline : kScanThreads) / 32) * 2 * kQueue * 8;
 }
 
 template <typename CellT, bool kVec, bool kInline = false>
@@ -27,8 +28,9 @@ __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, k
                                                           const __grid_constant__ InlineArgs ia) {
   extern __shared__ unsigned long long scan_smem[];
   volatile unsigned long long* seen = scan_smem;
-  auto queue_mem = reinterpret_cast<unsigned long long(*)[2][kQueue]>(scan_smem + kSeen);
-  for (int x = threadIdx.x; x < kSeen; x += blockDim.x) seen[x] = kNoPair;
+  auto queue_mem = reinterpret_cast<unsigned long long(*)[2][kQueue]>(scan_smem + (kInline ? 0 : kSeen));
+  if (!kInline)
+    for (int x = threadIdx.x; x < kSeen; x += blockDim.x) seen[x] = kNoPair;
   __syncthreads();
   if (kInline || (ptab && ctl->pair_mode == 0)) ptab = nullptr;
   const uint32_t tm = ctl->tm;

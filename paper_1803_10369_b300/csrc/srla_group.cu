@@ -253,10 +253,23 @@ int rebuild_work(srla_group_t* g) {
     }
   }
   const size_t need = (chunks.size() + post.size()) * sizeof(SweepChunk);
-  if (g->chunk_bytes) arena_free(g, g->chunk_off, g->chunk_bytes);
-  g->chunk_bytes = 0;
+  // the new list is placed before the old one is given back, so that a failure leaves the
+  // old list (and the counters that point to it) in place; only when both do not fit at
+  // once is the old one freed first (a shrinking list then always fits)
   size_t off = 0;
-  if (need && !arena_alloc_top(g, need, &off)) return SRLA_E_NOMEM;
+  if (need && !arena_alloc_top(g, need, &off)) {
+    if (!g->chunk_bytes) return SRLA_E_NOMEM;
+    for (int q = 0; q < 2; q++) G_TRY(cudaEventSynchronize(g->ev[q]));
+    arena_free(g, g->chunk_off, g->chunk_bytes);
+    g->chunk_bytes = 0;
+    if (!arena_alloc_top(g, need, &off)) {
+      const unsigned zero[3] = {0, 0, 0};  // n_links, n_chunks, n_post: no sweep until the next rebuild
+      G_TRY(cudaMemcpyAsync(&g->gctl()->n_links, zero, sizeof(zero), cudaMemcpyHostToDevice, g->st));
+      return SRLA_E_NOMEM;
+    }
+  } else if (g->chunk_bytes) {
+    arena_free(g, g->chunk_off, g->chunk_bytes);
+  }
   g->chunk_off = off;
   g->chunk_bytes = need;
   SweepChunk* dchunks = reinterpret_cast<SweepChunk*>(g->ws + off);
@@ -499,10 +512,14 @@ int srla_group_attach(srla_group_t* g, const srla_params* p, uint32_t* link) {
   const LinkDesc D = make_desc(g, s);
   G_TRY(cudaMemcpyAsync(g->descs() + l, &D, sizeof(D), cudaMemcpyHostToDevice, g->st));
   const int rc = rebuild_work(g);
-  if (rc != SRLA_OK) {
+  if (rc != SRLA_OK) {  // undo: the slot and its device entry are free again, the old links' lists rebuilt
     s.active = false;
+    const LinkDesc none{};
+    G_TRY(cudaMemcpyAsync(g->descs() + l, &none, sizeof(none), cudaMemcpyHostToDevice, g->st));
+    G_TRY(cudaStreamSynchronize(g->st));
     arena_free(g, off, L.total);
-    return rc;
+    const int r2 = rebuild_work(g);
+    return r2 != SRLA_OK ? r2 : rc;
   }
   *link = l;
   return SRLA_OK;

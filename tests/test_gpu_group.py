@@ -140,3 +140,23 @@ def test_group_rules(cuda_device):
     assert e.value.code == srla.E_CAPACITY
     g.detach(b)
     g.close()
+
+
+def test_failed_attach_leaves_the_group_working(cuda_device):
+    """The second link's recorders fit the arena but the rebuilt sweep list of both links does
+    not (512 spare bytes: room for one tiny link's list, not two): the attach fails with
+    E_NOMEM, is rolled back, and the first link keeps matching the same link run alone."""
+    small = _params(TINY, pair_slots_log2=10)
+    lb = srla.Group.link_bytes(small)
+    g = _group(n_links=2, arena=2 * lb + 512)
+    a = g.attach(small)
+    with pytest.raises(srla.SRLAError) as e:
+        g.attach(_params(TINY.replace(seed=31), pair_slots_log2=10))
+    assert e.value.code == srla.E_NOMEM
+    solo = srla.Link(small, device=cuda_device)
+    for s in range(4):
+        pk = synth.generate_slice(TINY.traffic, s).to(cuda_device)
+        g.push(a, pk)
+        solo.push(pk)
+        _same(g.report(a, g.end_slice()), solo.report(solo.end_slice()), f"slice {s}")
+    g.close()

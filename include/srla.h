@@ -371,12 +371,12 @@ int srla_server_autotune(srla_server_t *s, int reps);
 int srla_server_tick(srla_server_t *s, uint64_t *slice, uint32_t *admitted, uint32_t *waiting);
 
 /* Results of one of the two most recent slices: per admitted link, its key, statistics and
- * entry range in `entries` (sorted by aip within a link).                               */
+ * entry range in `entries` (sorted by aip within a link).  Driver thread (like tick).     */
 int srla_server_poll(srla_server_t *s, uint64_t slice, srla_server_result *results,
                      size_t result_cap, size_t *n_results, srla_entry *entries,
                      size_t entry_cap, size_t *n_entries);
 
-/* Bytes of the budget in use by admitted links. */
+/* Bytes of the budget in use by admitted links (driver thread). */
 uint64_t srla_server_used_bytes(const srla_server_t *s);
 void srla_server_destroy(srla_server_t *s);
 

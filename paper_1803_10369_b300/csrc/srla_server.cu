@@ -221,7 +221,10 @@ int srla_server_poll(srla_server_t* s, uint64_t slice, srla_server_result* resul
                      size_t* n_results, srla_entry* entries, size_t entry_cap, size_t* n_entries) {
   if (!s || (result_cap && !results) || (entry_cap && !entries)) return SRLA_E_INVAL;
   const int q = (int)(slice & 1);
-  if (s->slice_of[q] != slice) return SRLA_E_ORDER;
+  {
+    std::lock_guard<std::mutex> lock(s->mu);
+    if (s->slice_of[q] != slice) return SRLA_E_ORDER;
+  }
   size_t n = 0;
   const int rc = srla_group_report_all(s->g, slice, s->all.data(), s->all.size(), &n, s->offs.data(), s->stats.data());
   if (rc != SRLA_OK && rc != SRLA_E_CAPACITY) return rc;

@@ -41,7 +41,7 @@ struct srla_s {
   cudaStream_t st_h2d;   // internal stream for host-to-device copies of host batches
   cudaStream_t st_side;  // internal stream: the estimator table beside filter and sort
   cudaStream_t st_d2h;   // internal stream: each slice's report header, after its slice end
-  cudaEvent_t ev_fork, ev_join;
+  cudaEvent_t ev_fork, ev_join, ev_swept;
   cudaEvent_t ev_done[2];  // slice end complete, by slice parity
   cudaEvent_t ev_ready[2], ev_free[2];  // staging halves: copied / consumed by the scan
   bool free_pending[2];
@@ -162,7 +162,7 @@ int launch_sweep(srla_t* h, int census, int reset, int after_close) {
   return cuda_err(cudaGetLastError());
 }
 
-int launch_sort(srla_t* h) {
+int launch_sort(srla_t* h, cudaStream_t st) {
   const Layout& L = h->L;
   Ctl* ctl = h->ctl();
   uint32_t* l0 = h->at<uint32_t>(L.clist[0]);
@@ -173,7 +173,7 @@ int launch_sort(srla_t* h) {
   void* args[] = {&ctl, &l0, &l1, &tmp, &cmax, &hist};
   h->launches++;
   return cuda_err(cudaLaunchCooperativeKernel((const void*)k_sort, dim3(h->sort_grid), dim3(kSortThreads), args,
-                                              kSortSmallSmem, h->st));
+                                              kSortSmallSmem, st));
 }
 
 // The next slice starts with an empty pair table (all slots hold the empty key, ~0).
@@ -188,39 +188,64 @@ int clear_pairs(srla_t* h) {
   return r != SRLA_OK ? r : clear_pairs(h, 1, h->st);
 }
 
+// Recorder arrays up to this size are swept in about the time the candidate filter and sort
+// take, so those two run beside the sweep; a longer sweep is not delayed by them.
+constexpr size_t kOverlapSweepBytes = (size_t)128 << 20;
+
 // The slice end of the open slice, whose index has parity q.
+//
+// Overlapped schedule (side stream, recorder arrays up to kOverlapSweepBytes): the candidate
+// filter and sort run beside the sweep.  They read the SRE only through the window test, and
+// the only SRE cells the sweep may change (when k < P) hold the alias stamp, which is outside
+// the window; with k = P the census sweep changes nothing.  The Eq. 8/9 table follows the
+// census on the main stream.  Otherwise the table runs beside the filter and sort, after the
+// sweep.  Either way the next slice's pair table (used two slices ago; with two tables) is
+// cleared on the side stream after the sweep, so that it is still in L2 when the next scan
+// starts, and the estimate waits for everything; a single table is cleared at the end.
 template <typename CellT>
 int launch_end_slice(srla_t* h, int q) {
   const Layout& L = h->L;
   const bool inl = inline_mode(h);
-  int r;
-  // With two pair tables the next slice's (used two slices ago) is cleared beside the
-  // filter and sort, after the sweep has streamed the recorders through L2, so that it is
-  // still cached when the next scan starts; a single table is cleared after the slice end.
   const bool two = h->L.n_ptab == 2;
-  if ((r = launch_sweep<CellT>(h, 1, h->k_is_P ? 0 : 1, 0)) != SRLA_OK) return r;
-  // Eq. 8/9 table: needs the census; runs beside the filter and sort when a side stream exists
+  const bool overlap = h->st_side && L.le + cell_array_bytes<CellT>((size_t)h->p.u * h->p.v * h->p.gl) - L.re <=
+                                         kOverlapSweepBytes;
   const int lut_grid = (int)std::min<uint32_t>((h->p.gl + 1 + 255) / 256, (uint32_t)h->sms * 4);
+  int r;
   h->launches += inl ? 2 : 3;  // lut, (filter,) estimate
-  if (h->st_side) {
+  auto filter_and_sort = [&](cudaStream_t st) -> int {
+    if (!inl)  // the inline mode found its new candidates during the scan
+      k_filter<CellT><<<h->sms * 4, 256, 0, st>>>(
+          h->geo, h->coef, h->at<CellT>(L.re), h->ctl(), h->at<uint32_t>(L.ulist), h->p.max_sampled,
+          h->at<unsigned long long>(L.ctab[0]), h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]),
+          h->at<uint32_t>(L.cflags[1]), L.cmask, h->at<uint32_t>(L.clist[0]), h->at<uint32_t>(L.clist[1]),
+          h->p.max_candidates);
+    return launch_sort(h, st);
+  };
+  auto lut = [&](cudaStream_t st) {
+    k_lut<<<lut_grid, 256, 0, st>>>(h->geo, h->ctl(), h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
+  };
+  if (overlap) {
     SRLA_TRY(cudaEventRecord(h->ev_fork, h->st));
     SRLA_TRY(cudaStreamWaitEvent(h->st_side, h->ev_fork, 0));
-    k_lut<<<lut_grid, 256, 0, h->st_side>>>(h->geo, h->ctl(), h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
+    if ((r = filter_and_sort(h->st_side)) != SRLA_OK) return r;
+  }
+  if ((r = launch_sweep<CellT>(h, 1, h->k_is_P ? 0 : 1, 0)) != SRLA_OK) return r;
+  if (h->st_side) {
+    SRLA_TRY(cudaEventRecord(h->ev_swept, h->st));
+    SRLA_TRY(cudaStreamWaitEvent(h->st_side, h->ev_swept, 0));
+    if (!overlap) lut(h->st_side);
     if (two && (r = clear_pairs(h, q ^ 1, h->st_side)) != SRLA_OK) return r;
     SRLA_TRY(cudaEventRecord(h->ev_join, h->st_side));
+    if (overlap)
+      lut(h->st);
+    else if ((r = filter_and_sort(h->st)) != SRLA_OK)
+      return r;
+    SRLA_TRY(cudaStreamWaitEvent(h->st, h->ev_join, 0));
   } else {
-    k_lut<<<lut_grid, 256, 0, h->st>>>(h->geo, h->ctl(), h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
+    lut(h->st);
+    if ((r = filter_and_sort(h->st)) != SRLA_OK) return r;
     if (two && (r = clear_pairs(h, q ^ 1, h->st)) != SRLA_OK) return r;
   }
-  // the inline mode found its new candidates during the scan
-  if (!inl)
-    k_filter<CellT><<<h->sms * 4, 256, 0, h->st>>>(
-        h->geo, h->coef, h->at<CellT>(L.re), h->ctl(), h->at<uint32_t>(L.ulist), h->p.max_sampled,
-        h->at<unsigned long long>(L.ctab[0]), h->at<unsigned long long>(L.ctab[1]), h->at<uint32_t>(L.cflags[0]),
-        h->at<uint32_t>(L.cflags[1]), L.cmask, h->at<uint32_t>(L.clist[0]), h->at<uint32_t>(L.clist[1]),
-        h->p.max_candidates);
-  if ((r = launch_sort(h)) != SRLA_OK) return r;
-  if (h->st_side) SRLA_TRY(cudaStreamWaitEvent(h->st, h->ev_join, 0));
   // Algorithm 3 clears every SI before the carried hosts set theirs for the next slice
   if (inl) SRLA_TRY(cudaMemsetAsync(h->ws + L.si[q ^ 1], 0, (size_t)h->p.u * h->p.v * 4, h->st));
   k_estimate<CellT><<<h->sms * 2, 256, 0, h->st>>>(
@@ -387,6 +412,7 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
                         cudaStreamCreateWithFlags(&h->st_d2h, cudaStreamNonBlocking) != cudaSuccess ||
                         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
                         cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+                        cudaEventCreateWithFlags(&h->ev_swept, cudaEventDisableTiming) != cudaSuccess ||
                         cudaEventCreateWithFlags(&h->ev_done[0], cudaEventDisableTiming) != cudaSuccess ||
                         cudaEventCreateWithFlags(&h->ev_done[1], cudaEventDisableTiming) != cudaSuccess))
     rc = SRLA_E_CUDA;
@@ -672,6 +698,7 @@ void srla_destroy(srla_t* h) {
   if (h->st_side) cudaStreamDestroy(h->st_side);
   if (h->ev_fork) cudaEventDestroy(h->ev_fork);
   if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->ev_swept) cudaEventDestroy(h->ev_swept);
   for (int q = 0; q < 2; q++) {
     if (h->ev_done[q]) cudaEventDestroy(h->ev_done[q]);
     if (h->slot[q].ev) cudaEventDestroy(h->slot[q].ev);

@@ -246,16 +246,7 @@ __device__ __forceinline__ unsigned link_of(const uint32_t* off, unsigned nl, ui
 }
 
 __global__ void __launch_bounds__(256) kg_sweep(const LinkDesc* __restrict__ descs, const GroupCtl* __restrict__ gctl,
-                                                int post, uint32_t* __restrict__ filt_off) {
-  if (!post && blockIdx.x == 0 && threadIdx.x == 0) {  // host pairs per link for the flat filter
-    uint32_t run = 0;
-    for (unsigned l = 0; l < gctl->n_links; l++) {
-      filt_off[l] = run;
-      const LinkDesc& D = descs[l];
-      if (D.active) run += (min(D.ctl->n_sampled, D.umax) + 1u) / 2u;
-    }
-    filt_off[gctl->n_links] = run;
-  }
+                                                int post) {
   const unsigned n = post ? gctl->n_post : gctl->n_chunks;
   const SweepChunk* __restrict__ chunks = post ? gctl->post : gctl->chunks;
   for (unsigned ci = blockIdx.x; ci < n; ci += gridDim.x) {
@@ -323,7 +314,30 @@ __device__ __forceinline__ void group_filter_pair(const LinkDesc& D, uint32_t q,
   }
 }
 
-// Every link's sampled hosts in one flat range of host pairs (prefixed by the sweep).
+// Host pairs per link for the flat filter: filt_off[l] = the pairs (two hosts each) of the
+// active links before l, filt_off[n_links] the total.  One warp.
+__global__ void kg_filter_offsets(const LinkDesc* __restrict__ descs, const GroupCtl* __restrict__ gctl,
+                                  uint32_t* __restrict__ filt_off) {
+  const unsigned nl = gctl->n_links;
+  const int lane = threadIdx.x & 31;
+  uint32_t run = 0;
+  for (unsigned base = 0; base < nl; base += 32) {
+    const unsigned l = base + (unsigned)lane;
+    uint32_t c = 0;
+    if (l < nl && descs[l].active) c = (min(descs[l].ctl->n_sampled, descs[l].umax) + 1u) / 2u;
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(kFull, incl, o);
+      if (lane >= o) incl += t;
+    }
+    if (l < nl) filt_off[l] = run + incl - c;
+    run += __shfl_sync(kFull, incl, 31);
+  }
+  if (lane == 0) filt_off[nl] = run;
+}
+
+// Every link's sampled hosts in one flat range of host pairs (prefixed by kg_filter_offsets).
 __global__ void __launch_bounds__(256, 2) kg_filter(const LinkDesc* __restrict__ descs,
                                                     const GroupCtl* __restrict__ gctl,
                                                     const uint32_t* __restrict__ filt_off) {

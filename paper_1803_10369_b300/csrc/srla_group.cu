@@ -322,24 +322,28 @@ int enqueue_slice(srla_group_t* g, int q) {
   GroupCtl* gctl = g->gctl();
   G_TRY(cudaMemcpyAsync(g->ws + F.tasks, g->h_tasks[q], sizeof(TaskHeader) + sizeof(ScanTask) * F.max_tasks,
                         cudaMemcpyHostToDevice, g->st));
-  g->launches += 6;  // scan, sweep, lut, filter, sort, estimate, (post sweep below)
+  g->launches += 7;  // scan, filter offsets, filter, sort, sweep, lut, estimate, (post sweep below)
   launch_group_scan(g, g->scan_threads, reinterpret_cast<const TaskHeader*>(g->ws + F.tasks));
+  // the candidate filter and sort run beside the sweep (they read the SRE only through the
+  // window test; the sweep changes only SRE cells outside the window); the Eq. 8/9 tables
+  // follow the census
   uint32_t* filt_off = reinterpret_cast<uint32_t*>(g->ws + F.filt_off);
-  kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 0, filt_off);
+  uint32_t* rep_off = reinterpret_cast<uint32_t*>(g->ws + F.rep_off[q]);
   G_TRY(cudaEventRecord(g->ev_fork, g->st));
   G_TRY(cudaStreamWaitEvent(g->st_side, g->ev_fork, 0));
-  kg_lut<<<std::max(1, std::min<int>((int)g->max_links, g->sms * 4)), 256, 0, g->st_side>>>(descs, gctl);
-  G_TRY(cudaEventRecord(g->ev_join, g->st_side));
-  kg_filter<<<g->filt_grid, 256, 0, g->st>>>(descs, gctl, filt_off);
-  uint32_t* rep_off = reinterpret_cast<uint32_t*>(g->ws + F.rep_off[q]);
+  kg_filter_offsets<<<1, 32, 0, g->st_side>>>(descs, gctl, filt_off);
+  kg_filter<<<g->filt_grid, 256, 0, g->st_side>>>(descs, gctl, filt_off);
   void* args[] = {&descs, &gctl, &rep_off};
   G_TRY(cudaLaunchCooperativeKernel((const void*)kg_sort, dim3(g->sort_grid), dim3(kSortThreads), args,
-                                    kSortSmallSmem, g->st));
+                                    kSortSmallSmem, g->st_side));
+  G_TRY(cudaEventRecord(g->ev_join, g->st_side));
+  kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 0);
+  kg_lut<<<std::max(1, std::min<int>((int)g->max_links, g->sms * 4)), 256, 0, g->st>>>(descs, gctl);
   G_TRY(cudaStreamWaitEvent(g->st, g->ev_join, 0));
   kg_estimate<<<g->est_grid, 256, 0, g->st>>>(descs, gctl, reinterpret_cast<srla_slice_stats*>(g->ws + F.gstats[q]),
                                              rep_off, reinterpret_cast<srla_entry*>(g->ws + F.grep[q]));
   g->launches += 1;
-  kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 1, filt_off);
+  kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 1);
   G_TRY(cudaGetLastError());
   G_TRY(cudaMemcpyAsync(g->h_stats[q], g->ws + F.gstats[q], sizeof(srla_slice_stats) * g->max_links,
                         cudaMemcpyDeviceToHost, g->st));

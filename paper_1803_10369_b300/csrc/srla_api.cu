@@ -209,7 +209,8 @@ int launch_end_slice(srla_t* h, int q) {
   const bool two = h->L.n_ptab == 2;
   const bool overlap = h->st_side && L.le + cell_array_bytes<CellT>((size_t)h->p.u * h->p.v * h->p.gl) - L.re <=
                                          kOverlapSweepBytes;
-  const int lut_grid = (int)std::min<uint32_t>((h->p.gl + 1 + 255) / 256, (uint32_t)h->sms * 4);
+  // one warp per 32 table entries, spread over the SMs (FP64 throughput is per SM)
+  const int lut_grid = (int)std::min<uint32_t>((h->p.gl + 1 + 31) / 32, (uint32_t)h->sms * 8);
   int r;
   h->launches += inl ? 2 : 3;  // lut, (filter,) estimate
   auto filter_and_sort = [&](cudaStream_t st) -> int {
@@ -222,7 +223,7 @@ int launch_end_slice(srla_t* h, int q) {
     return launch_sort(h, st);
   };
   auto lut = [&](cudaStream_t st) {
-    k_lut<<<lut_grid, 256, 0, st>>>(h->geo, h->ctl(), h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
+    k_lut<<<lut_grid, 32, 0, st>>>(h->geo, h->ctl(), h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags));
   };
   if (overlap) {
     SRLA_TRY(cudaEventRecord(h->ev_fork, h->st));

@@ -389,31 +389,43 @@ def bench_srla(args):
 def _store_roofline(w, tau, dev, stream, scan_pkts_per_s):
     """The scan against random stores: srla_scatter_probe writes cell-sized values to random
     cells of a buffer the size of the link's recorders; a packet needs u SLE stores plus u
-    SRE stores for the 2^-tau sampled share.  pkts_per_s = stores/s / stores per packet."""
+    SRE stores for the 2^-tau sampled share.  pkts_per_s = stores/s / stores per packet.
+    `policies` times the other ways to make the same writes: an atomic maximum (a CAS loop on
+    1- and 2-byte cells; native on 4-byte cells, at twice the footprint for 2-byte recorders)
+    and a read before each write that skips the store when the cell already holds the value."""
     import torch
 
     from paper_1803_10369_b300 import srla
 
     cell = w.dr_bytes if w.dr_bytes else 1
     cells = w.u * w.v * (w.g + w.gl) // (1 if w.dr_bytes else 8)
-    buf = torch.empty(cells * cell, dtype=torch.uint8, device=dev)
     per_pkt = w.u * (1 + 2.0 ** -tau)
     n = int(per_pkt * 5_000_000)
-    rates = []
-    with torch.cuda.stream(stream):
-        for rep in range(4):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            srla.scatter_probe(buf, cell, n, seed=rep + 1, stream=stream)
-            e1.record(stream)
-            e1.synchronize()
-            if rep:
-                rates.append(n / (e0.elapsed_time(e1) * 1e-3))
-    del buf
-    r = statistics.median(rates)
+
+    def rate(cb, policy):
+        buf = torch.zeros(cells * cb, dtype=torch.uint8, device=dev)
+        rates = []
+        with torch.cuda.stream(stream):
+            for rep in range(4):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                # a larger value every repetition, as a new slice writes a new stamp
+                srla.scatter_probe(buf, cb, n, seed=2 * rep + 2, stream=stream, policy=policy)
+                e1.record(stream)
+                e1.synchronize()
+                if rep:
+                    rates.append(n / (e0.elapsed_time(e1) * 1e-3))
+        del buf
+        return statistics.median(rates)
+
+    r = rate(cell, srla.PROBE_STORE)
+    pol = {"store": round(r, 0), "atomic_max": round(rate(cell, srla.PROBE_ATOMIC_MAX), 0),
+           "read_first": round(rate(cell, srla.PROBE_READ_FIRST), 0),
+           "atomic_max_u32": round(rate(4, srla.PROBE_ATOMIC_MAX), 0)}
     return {"stores_per_s": round(r, 0), "footprint_bytes": cells * cell, "cell_bytes": cell,
             "stores_per_pkt": per_pkt, "pkts_per_s": round(r / per_pkt, 0),
             "scan_vs_stores": round(scan_pkts_per_s / (r / per_pkt), 4),
+            "policies_ops_per_s": pol,
             "note": "random stores over the recorders' footprint; the scan de-duplicates pairs, so it can exceed 1"}
 
 

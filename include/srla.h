@@ -234,13 +234,23 @@ int srla_wait_selftest(void *dev_scratch, size_t bytes, void *stream, uint32_t b
                        uint32_t spin_limit);
 
 /* Store roofline probe (a measurement aid, not part of the method): enqueues on `stream`
- * n_stores stores of cell_bytes (1, 2 or 4) each to pseudo-random cells of the caller's
- * device buffer dev_buf of `bytes` bytes (at least one cell): the access
+ * n_stores writes of cell_bytes (1, 2 or 4) each to pseudo-random cells of the caller's
+ * device buffer dev_buf of `bytes` bytes (at least one cell, 4-byte aligned): the access
  * shape of the scan's recorder updates (Algorithm 2) without their hashing,
- * de-duplication or sampling.  Time it with events on the same stream.  Overwrites the
- * buffer.  Errors: INVAL, CUDA. */
+ * de-duplication or sampling.  All writes carry the same value, as all writers of a slice
+ * write the same stamp.  policy: how a write is made,
+ *   SRLA_PROBE_STORE       a plain store (the scan's choice);
+ *   SRLA_PROBE_ATOMIC_MAX  an atomic maximum (native on 4-byte cells; on 1- and 2-byte
+ *                          cells a compare-and-swap loop on the enclosing 32-bit word,
+ *                          at most 64 tries; only the cells of whole words of the buffer
+ *                          are used);
+ *   SRLA_PROBE_READ_FIRST  a load through L2, then a store only if the cell differs.
+ * Time it with events on the same stream.  Overwrites the buffer.  Errors: INVAL, CUDA. */
+#define SRLA_PROBE_STORE 0u
+#define SRLA_PROBE_ATOMIC_MAX 1u
+#define SRLA_PROBE_READ_FIRST 2u
 int srla_scatter_probe(void *dev_buf, size_t bytes, uint32_t cell_bytes, uint64_t n_stores, uint64_t seed,
-                       void *stream);
+                       uint32_t policy, void *stream);
 const char *srla_strerror(int code);
 
 

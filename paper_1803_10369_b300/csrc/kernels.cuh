@@ -379,20 +379,54 @@ __global__ void k_insert_carried(const uint32_t* __restrict__ hosts, uint32_t n,
   }
 }
 
-// Random-store probe (the store roofline of the scan): n stores of a cell-sized value to
+// Random-store probe (the store roofline of the scan): n writes of one cell-sized value to
 // pseudo-random cells of a footprint of `cells` cells, i.e. the access shape of the scan's
-// DRsets without their hashing, de-duplication or sampling.  The cell of store i comes from
+// DRsets without their hashing, de-duplication or sampling (every writer of a slice writes
+// the same stamp, so the value is the same for all writes).  The cell of write i comes from
 // a 64-bit mix of i (the SplitMix64 finaliser of Steele, Lea and Flood) scaled to [0, cells)
-// by a multiply-high.
+// by a multiply-high.  kPolicy selects how a write is made:
+//   0  a plain store (what the scan does);
+//   1  an atomic maximum: native on 32-bit cells; on 8- and 16-bit cells, which have no
+//      atomic maximum, a compare-and-swap loop on the enclosing 32-bit word (at most 64
+//      tries, so contention can only slow it down);
+//   2  read before write: a load through L2, and a store only if the cell differs.
+enum : uint32_t { kProbeStore = 0, kProbeAtomicMax = 1, kProbeReadFirst = 2 };
+
 template <typename CellT>
+__device__ __forceinline__ void probe_atomic_max(CellT* p, CellT val) {
+  if constexpr (sizeof(CellT) == 4) {
+    atomicMax(reinterpret_cast<unsigned*>(p), (unsigned)val);
+  } else {
+    unsigned* w = reinterpret_cast<unsigned*>(reinterpret_cast<uintptr_t>(p) & ~(uintptr_t)3);
+    const unsigned sh = (unsigned)(reinterpret_cast<uintptr_t>(p) & 3u) * 8u;
+    const unsigned m = (unsigned)(CellT)~(CellT)0 << sh;
+    unsigned old = __ldcg(w);
+    for (int it = 0; it < 64; it++) {
+      if (((old & m) >> sh) >= (unsigned)val) break;
+      const unsigned prev = atomicCAS(w, old, (old & ~m) | ((unsigned)val << sh));
+      if (prev == old) break;
+      old = prev;
+    }
+  }
+}
+
+template <typename CellT, uint32_t kPolicy>
 __global__ void __launch_bounds__(256) k_scatter_probe(CellT* __restrict__ buf, uint64_t cells, uint64_t n,
                                                        uint64_t seed) {
+  const CellT val = (CellT)(seed | 1u);
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t z = i + seed * 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z ^= z >> 31;
-    buf[__umul64hi(z, cells)] = (CellT)(i | 1u);
+    CellT* p = buf + __umul64hi(z, cells);
+    if constexpr (kPolicy == kProbeStore) {
+      *p = val;
+    } else if constexpr (kPolicy == kProbeAtomicMax) {
+      probe_atomic_max<CellT>(p, val);
+    } else {
+      if (__ldcg(p) != val) *p = val;
+    }
   }
 }
 

@@ -852,10 +852,26 @@ extern "C" int srla_wait_selftest(void* dev_scratch, size_t bytes, void* stream,
   return (overflow & 4u) ? SRLA_E_TIMEOUT : SRLA_OK;
 }
 
+template <typename CellT>
+static void launch_probe(uint32_t policy, int grid, cudaStream_t st, void* buf, uint64_t cells, uint64_t n,
+                         uint64_t seed) {
+  CellT* b = static_cast<CellT*>(buf);
+  if (policy == kProbeStore)
+    k_scatter_probe<CellT, kProbeStore><<<grid, 256, 0, st>>>(b, cells, n, seed);
+  else if (policy == kProbeAtomicMax)
+    k_scatter_probe<CellT, kProbeAtomicMax><<<grid, 256, 0, st>>>(b, cells, n, seed);
+  else
+    k_scatter_probe<CellT, kProbeReadFirst><<<grid, 256, 0, st>>>(b, cells, n, seed);
+}
+
 extern "C" int srla_scatter_probe(void* dev_buf, size_t bytes, uint32_t cell_bytes, uint64_t n_stores, uint64_t seed,
-                                  void* stream) {
-  if (!dev_buf || (cell_bytes != 1 && cell_bytes != 2 && cell_bytes != 4)) return SRLA_E_INVAL;
-  const uint64_t cells = bytes / cell_bytes;
+                                  uint32_t policy, void* stream) {
+  if (!dev_buf || (cell_bytes != 1 && cell_bytes != 2 && cell_bytes != 4) || policy > kProbeReadFirst)
+    return SRLA_E_INVAL;
+  if (reinterpret_cast<uintptr_t>(dev_buf) & 3u) return SRLA_E_INVAL;  // word-aligned for the CAS loop
+  // the CAS loop of the atomic maximum reads and writes whole 32-bit words: only cells of
+  // whole words of the buffer are used
+  const uint64_t cells = (policy == kProbeAtomicMax ? bytes & ~(size_t)3 : bytes) / cell_bytes;
   if (!cells) return SRLA_E_INVAL;
   int dev = 0, sms = 0;
   SRLA_TRY(cudaGetDevice(&dev));
@@ -863,10 +879,10 @@ extern "C" int srla_scatter_probe(void* dev_buf, size_t bytes, uint32_t cell_byt
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int grid = grid_for(n_stores, 256, sms * 8);
   if (cell_bytes == 1)
-    k_scatter_probe<uint8_t><<<grid, 256, 0, st>>>(static_cast<uint8_t*>(dev_buf), cells, n_stores, seed);
+    launch_probe<uint8_t>(policy, grid, st, dev_buf, cells, n_stores, seed);
   else if (cell_bytes == 2)
-    k_scatter_probe<uint16_t><<<grid, 256, 0, st>>>(static_cast<uint16_t*>(dev_buf), cells, n_stores, seed);
+    launch_probe<uint16_t>(policy, grid, st, dev_buf, cells, n_stores, seed);
   else
-    k_scatter_probe<uint32_t><<<grid, 256, 0, st>>>(static_cast<uint32_t*>(dev_buf), cells, n_stores, seed);
+    launch_probe<uint32_t>(policy, grid, st, dev_buf, cells, n_stores, seed);
   return cuda_err(cudaGetLastError());
 }

@@ -71,7 +71,8 @@ SIGNATURES = {
     "srla_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "srla_batch_report_static": (ctypes.c_int, [_P, _P, ctypes.c_uint64, _P, _P, ctypes.c_size_t, _P, _P]),
     "srla_wait_selftest": (ctypes.c_int, [_P, ctypes.c_size_t, _P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32]),
-    "srla_scatter_probe": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, _P]),
+    "srla_scatter_probe": (ctypes.c_int, [_P, ctypes.c_size_t, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64,
+                                          ctypes.c_uint32, _P]),
     "srla_group_fixed_bytes": (ctypes.c_size_t, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32]),
     "srla_group_link_bytes": (ctypes.c_size_t, [_P]),
     "srla_group_create": (ctypes.c_int, [ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, _P,
@@ -160,14 +161,17 @@ def wait_selftest(blocks=2, absent=1, spin_limit=10000, device="cuda") -> int:
                                     blocks, absent, spin_limit)
 
 
-def scatter_probe(buf, cell_bytes: int, n_stores: int, seed: int = 1, stream=None):
+PROBE_STORE, PROBE_ATOMIC_MAX, PROBE_READ_FIRST = 0, 1, 2
+
+
+def scatter_probe(buf, cell_bytes: int, n_stores: int, seed: int = 1, stream=None, policy: int = PROBE_STORE):
     """Enqueue the store roofline probe (srla_scatter_probe) on `stream` over the torch buffer
-    `buf`."""
+    `buf`; `policy` is PROBE_STORE, PROBE_ATOMIC_MAX or PROBE_READ_FIRST."""
     import torch
 
     st = stream if stream is not None else torch.cuda.current_stream(buf.device)
     _ck(lib().srla_scatter_probe(ctypes.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(), cell_bytes,
-                                 n_stores, seed, ctypes.c_void_p(st.cuda_stream)), "srla_scatter_probe")
+                                 n_stores, seed, policy, ctypes.c_void_p(st.cuda_stream)), "srla_scatter_probe")
 
 
 def params_for(w, hash_a, hash_b, **over) -> srla_params:

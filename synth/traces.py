@@ -15,7 +15,9 @@ The traffic model stands in for the CERNET traces of Section 5, which are not av
   that ``planted_spread`` consecutive slices hold ``card`` distinct destinations; a share of
   them switch on and off (churn);
 * optional adversarial parts: one heavy source sending a share of all packets to random
-  destinations, and a flood of spoofed one-packet sources.
+  destinations, and a flood of spoofed one-packet sources;
+* optional flow bursts: each background pair sends a geometric number of packets (mean
+  ``burst_mean``) back to back, so that consecutive packets repeat the same pair.
 
 Every slice is generated from ``(seed, slice index)`` alone, so any slice can be rebuilt on
 its own, on the CPU or on a CUDA device (the two devices draw different streams; tests make
@@ -91,6 +93,7 @@ class TrafficSpec:
     heavy_frac: float = 0.0
     flood_sources: int = 0
     flood_slices: tuple = (0, 0)        # [first, last) slice of the spoofed flood
+    burst_mean: float = 0.0             # > 0: background pairs in back-to-back bursts of this mean
 
 
 @functools.lru_cache(maxsize=8)
@@ -187,6 +190,19 @@ def generate_slice(spec: TrafficSpec, s: int, device="cpu") -> torch.Tensor:
         f_bip = f_aip
 
     n_bg = max(0, n - p_aip.numel() - n_heavy - f_aip.numel())
+    burst = None
+    if spec.burst_mean > 0 and n_bg > 0:
+        # packets per background flow ~ Geometric(1/mean) >= 1, drawn until they cover n_bg
+        m = int(math.ceil(n_bg / spec.burst_mean * 1.25)) + 64
+        burst = torch.empty(m, device=dev, dtype=torch.float64).geometric_(1.0 / spec.burst_mean, generator=gen)
+        burst = burst.to(torch.int64)
+        ends = torch.cumsum(burst, 0)
+        f = int(torch.searchsorted(ends, torch.tensor([n_bg], device=dev, dtype=torch.int64)).item()) + 1
+        if f > m:
+            raise ValueError("burst draw did not cover the slice")
+        burst = burst[:f].clone()
+        burst[-1] -= int(ends[f - 1].item()) - n_bg
+        n_bg = f
     u = torch.rand(n_bg, generator=gen, device=dev, dtype=torch.float64)
     rank = torch.searchsorted(_zipf_cdf(spec.n_src, spec.zipf_s, dev), u, right=True)
     rank = rank.clamp_(max=spec.n_src - 1).to(torch.int64)
@@ -205,6 +221,11 @@ def generate_slice(spec: TrafficSpec, s: int, device="cpu") -> torch.Tensor:
     aip = torch.cat([bg_aip, p_aip, h_aip, f_aip])
     bip = torch.cat([bg_bip, p_bip, h_bip, f_bip])
     perm = torch.randperm(aip.numel(), generator=gen, device=dev)
+    if burst is not None:  # shuffle whole bursts, then expand each into its packets
+        reps = torch.cat([burst, torch.ones(aip.numel() - n_bg, dtype=torch.int64, device=dev)])[perm]
+        aip = torch.repeat_interleave(aip[perm], reps)
+        bip = torch.repeat_interleave(bip[perm], reps)
+        return torch.stack([_to_i32(aip), _to_i32(bip)], dim=1).contiguous()
     return torch.stack([_to_i32(aip[perm]), _to_i32(bip[perm])], dim=1).contiguous()
 
 

@@ -103,7 +103,19 @@ DISCRETE = PAPER_OWN.replace(
     name="discrete-1link-u4-v65536-g8-gl1024-z1-k1-bits-4.5Mpps", dr_bytes=0, z=1, k=1, n_slices=16,
     n_planted=60, planted_spread=1, churn_run=(1, 4))
 
-WORKLOADS = {"tiny": TINY, "paper": PAPER, "longwin": LONGWIN, "paperown": PAPER_OWN, "discrete": DISCRETE}
+# Paper-scale traffic in flow bursts: every background pair sends a geometric number of
+# packets (mean 8) back to back, so warps see runs of the same pair (duplicate elision).
+BURST = PAPER.replace(name="burst-1link-u8-v16384-g128-gl256-z16-k300-5Mpps-mean8", seed=7, burst_mean=8.0)
+
+# The literal reading of the paper-scale traffic: background destinations uniform over 2^20
+# addresses.  About 10^9 distinct pairs per window saturate every SRE and SLE row, so nearly
+# every sampled source becomes a candidate and is reported saturated (a stress case: candidate
+# lists of about a million hosts to sort, estimate and carry every slice).
+UNIFORM = PAPER.replace(name="uniform-1link-u8-v16384-g128-gl256-z16-k300-5Mpps-saturating", seed=8,
+                        dst_model="uniform", dst_space=1 << 20, max_candidates=1 << 21)
+
+WORKLOADS = {"tiny": TINY, "paper": PAPER, "longwin": LONGWIN, "paperown": PAPER_OWN, "discrete": DISCRETE,
+             "burst": BURST, "uniform": UNIFORM}
 
 
 def workload(name: str) -> Workload:

@@ -127,9 +127,12 @@ def test_measurement_and_selftest_entry_points_validate_arguments():
 
     L = srla.lib()
     fake = ctypes.c_void_p(256)
-    assert L.srla_scatter_probe(fake, 1024, 3, 10, 1, None) == srla.E_INVAL
-    assert L.srla_scatter_probe(fake, 1, 2, 10, 1, None) == srla.E_INVAL
-    assert L.srla_scatter_probe(None, 1024, 2, 10, 1, None) == srla.E_INVAL
+    assert L.srla_scatter_probe(fake, 1024, 3, 10, 1, 0, None) == srla.E_INVAL
+    assert L.srla_scatter_probe(fake, 1, 2, 10, 1, 0, None) == srla.E_INVAL
+    assert L.srla_scatter_probe(None, 1024, 2, 10, 1, 0, None) == srla.E_INVAL
+    assert L.srla_scatter_probe(fake, 1024, 2, 10, 1, 3, None) == srla.E_INVAL       # unknown policy
+    assert L.srla_scatter_probe(ctypes.c_void_p(258), 1024, 2, 10, 1, 1, None) == srla.E_INVAL  # not word-aligned
+    assert L.srla_scatter_probe(fake, 3, 1, 10, 1, 1, None) == srla.E_INVAL  # no whole word for the CAS loop
     assert L.srla_wait_selftest(fake, 256, None, 1, 0, 10) == srla.E_INVAL
     assert L.srla_wait_selftest(fake, 256, None, 4, 4, 10) == srla.E_INVAL
     assert L.srla_wait_selftest(fake, 128, None, 4, 1, 10) == srla.E_INVAL

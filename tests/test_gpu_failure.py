@@ -44,3 +44,30 @@ def test_store_probe_writes_the_footprint(cuda_device):
     torch.cuda.synchronize(cuda_device)
     cells = buf.view(torch.int16)
     assert int((cells != 0).sum()) > 0.9 * cells.numel()  # 8 stores per cell on average
+
+
+@pytest.mark.parametrize("cell_bytes", [1, 2, 4])
+@pytest.mark.parametrize("policy", [srla.PROBE_ATOMIC_MAX, srla.PROBE_READ_FIRST])
+def test_store_probe_policies_write_the_same_value(policy, cell_bytes, cuda_device):
+    """Every policy leaves each touched cell holding the probe's value (seed | 1); the atomic
+    maximum keeps larger values already present, and its CAS loop leaves the neighbouring
+    cells of the same 32-bit word alone."""
+    import torch
+
+    dt = {1: torch.uint8, 2: torch.int16, 4: torch.int32}[cell_bytes]
+    n_cells = (1 << 16) // cell_bytes
+    buf = torch.zeros(n_cells, dtype=dt, device=cuda_device)
+    big = torch.arange(n_cells, device=cuda_device) % 7 == 0
+    buf[big] = 100                              # larger than the value written below
+    seed = 4                                    # the probe writes seed | 1 = 5
+    srla.scatter_probe(buf, cell_bytes, 8 * n_cells, seed=seed, policy=policy)
+    torch.cuda.synchronize(cuda_device)
+    touched = buf != 0
+    assert int(touched.sum()) > 0.99 * n_cells  # 8 writes per cell on average
+    if policy == srla.PROBE_ATOMIC_MAX:
+        assert bool((buf[big] == 100).all())
+        rest = buf[~big]
+        assert bool(((rest == 5) | (rest == 0)).all())
+    else:  # a cell that differs is overwritten, 100 included; about e^-8 of the cells get no write
+        assert bool(((buf == 5) | (buf == 0) | (big & (buf == 100))).all())
+        assert float((buf[big] == 5).float().mean()) > 0.99

@@ -46,6 +46,14 @@ def test_long_window_flood_and_stamp_wraparound(cuda_device):
     _run(w, 3, cuda_device, first_trace_slice=4, state_every=3)
 
 
+def test_paper_scale_flow_bursts(cuda_device):
+    """Paper-scale traffic sent in bursts of the same pair (geometric, mean 8 packets): warps
+    meet runs of one pair, which the scan's duplicate elision must skip without losing any."""
+    w = synth.workload("burst").replace(planted_spread=3)
+    n_cand = _run(w, 3, cuda_device, state_every=3)
+    assert n_cand >= 100
+
+
 def test_paper_scale_uniform_destinations(cuda_device):
     """The literal uniform-destination reading of the paper-scale traffic (saturating)."""
     w = synth.workload("paper").replace(dst_model="uniform", dst_space=1 << 20, planted_spread=3,

@@ -31,6 +31,7 @@ VARIANTS = {
     "paper-g8": TINY.replace(g=8, gl=256, dr_bytes=2, z=16, k=6),
     "tag-wrap-2^31": TINY.replace(start_slice=(1 << 31) - 5),
     "slice-wrap-2^64": TINY.replace(start_slice=(1 << 64) - 6),
+    "flow-bursts-mean8": TINY.replace(burst_mean=8.0),
     # one-bit recorders packed 32 to a word (z = 1, k = 1); runs of 8 and of 4/16 recorders
     # share words, runs of 64 and 1024 span whole words
     "bits-discrete": TINY.replace(dr_bytes=0, z=1, k=1),

@@ -41,3 +41,25 @@ def test_longwin_flood_and_heavy_source():
     aips, cnt = np.unique(s[:, 0], return_counts=True)
     assert cnt.max() >= 0.09 * s.shape[0]          # the heavy source
     assert (cnt == 1).sum() >= (1 << 14) // 4 * 0.9  # one-packet spoofed sources
+
+
+def test_flow_bursts_repeat_each_pair_back_to_back():
+    """burst_mean = 8: background pairs come in runs of a geometric length (mean 8), the slice
+    keeps its packet count, and the planted hosts keep their destinations."""
+    w = synth.workload("tiny")
+    b = w.replace(burst_mean=8.0)
+    s = synth.pairs_to_numpy(synth.generate_slice(b.traffic, 4))
+    assert s.shape == (w.pkts_per_slice, 2)
+    key = (s[:, 0].astype(np.uint64) << np.uint64(32)) | s[:, 1].astype(np.uint64)
+    starts = np.concatenate([[True], key[1:] != key[:-1]])
+    runs = np.diff(np.concatenate([np.flatnonzero(starts), [key.size]]))
+    # each distinct pair forms one run (uniform destinations over 2^20 almost never repeat)
+    assert np.unique(key).size >= 0.99 * runs.size
+    planted = set(synth.planted_hosts(w.traffic)[0].tolist())
+    bg = np.array([a not in planted for a in s[starts, 0].tolist()])
+    assert 7.0 < runs[bg].mean() < 9.0
+    # planted hosts: the same destinations as without bursts
+    p = synth.pairs_to_numpy(synth.generate_slice(w.traffic, 4))
+    pk = lambda x: {tuple(r) for r in x[np.isin(x[:, 0], list(planted))].tolist()}
+    assert pk(s) == pk(p)
+    assert np.array_equal(s, synth.pairs_to_numpy(synth.generate_slice(b.traffic, 4)))

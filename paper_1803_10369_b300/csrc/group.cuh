@@ -208,17 +208,9 @@ __device__ __forceinline__ void group_sweep_chunk(const SweepChunk& c, const Lin
   const bool count = is_le && !after_close;
   const bool reset = after_close ? true : !D.k_is_P;
   const SweepWin sw = make_sweep_win<CellT>(tm, P, D.geo.k);
-  uint32_t cnt = 0;
   const size_t nvec = c.count;
-  size_t x = threadIdx.x;
-  for (; x + 3 * blockDim.x < nvec; x += 4 * blockDim.x) {
-    uint4 q[4];
-#pragma unroll
-    for (int j = 0; j < 4; j++) q[j] = base[x + j * blockDim.x];
-#pragma unroll
-    for (int j = 0; j < 4; j++) sweep_vec<CellT>(base, x + j * blockDim.x, q[j], count, reset, sw, alias, asplat, cnt);
-  }
-  for (; x < nvec; x += blockDim.x) sweep_vec<CellT>(base, x, base[x], count, reset, sw, alias, asplat, cnt);
+  uint32_t cnt = sw.wrap ? sweep_part<CellT, true>(base, nvec, threadIdx.x, blockDim.x, count, reset, sw, alias, asplat)
+                         : sweep_part<CellT, false>(base, nvec, threadIdx.x, blockDim.x, count, reset, sw, alias, asplat);
   if (count) {
     __shared__ uint32_t part[32];
     cnt = warp_sum(cnt);

@@ -135,17 +135,10 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
   const uint32_t alias = 1u + (after_close ? tm : ((tm + 1u == P) ? 0u : tm + 1u));
   const uint32_t asplat = splat<CellT>(alias);
   const SweepWin sw = make_sweep_win<CellT>(tm, P, geo.k);
-  uint32_t cnt = 0;
   const size_t stride = (size_t)gx * blockDim.x;
-  size_t x = (size_t)part * blockDim.x + threadIdx.x;
-  for (; x + 3 * stride < nvec; x += 4 * stride) {  // four loads in flight per thread
-    uint4 q[4];
-#pragma unroll
-    for (int j = 0; j < 4; j++) q[j] = base[x + j * stride];
-#pragma unroll
-    for (int j = 0; j < 4; j++) sweep_vec<CellT>(base, x + j * stride, q[j], count, reset, sw, alias, asplat, cnt);
-  }
-  for (; x < nvec; x += stride) sweep_vec<CellT>(base, x, base[x], count, reset, sw, alias, asplat, cnt);
+  const size_t x = (size_t)part * blockDim.x + threadIdx.x;
+  uint32_t cnt = sw.wrap ? sweep_part<CellT, true>(base, nvec, x, stride, count, reset, sw, alias, asplat)
+                         : sweep_part<CellT, false>(base, nvec, x, stride, count, reset, sw, alias, asplat);
   if (count) {
     __shared__ uint32_t part_sum[8];
     cnt = warp_sum(cnt);

@@ -329,8 +329,10 @@ __device__ __forceinline__ SweepWin make_sweep_win(uint32_t tm, uint32_t P, uint
 
 // In-window cells of one 32-bit word (the interval form of the window, one compare per cell;
 // the SIMD compare intrinsics are slower here).  Without wrap, a cell c is inside iff
-// c - lo < len in 32-bit arithmetic (the empty code 0 wraps to a huge value).
-template <typename CellT>
+// c - lo < len in 32-bit arithmetic (the empty code 0 wraps to a huge value).  kWrap fixes
+// the form at compile time (the caller picks the loop once), so the cell loop carries one
+// form only.
+template <typename CellT, bool kWrap>
 __device__ __forceinline__ uint32_t count_in_window(uint32_t word, const SweepWin& sw) {
   if constexpr (kIsBit<CellT>) {
     return (uint32_t)__popc(word);  // the window is the open slice
@@ -342,7 +344,7 @@ __device__ __forceinline__ uint32_t count_in_window(uint32_t word, const SweepWi
 #pragma unroll
     for (int q = 0; q < kCells; q++) {
       const uint32_t c = (word >> (q * kBits)) & kMask;
-      n += sw.wrap ? (uint32_t)((c >= sw.lo) | (c - 1u < sw.hi)) : (uint32_t)(c - sw.lo < sw.len);
+      n += kWrap ? (uint32_t)((c >= sw.lo) | (c - 1u < sw.hi)) : (uint32_t)(c - sw.lo < sw.len);
     }
     return n;
   }
@@ -368,12 +370,12 @@ __device__ __forceinline__ uint32_t clear_stamp(uint32_t word, uint32_t alias) {
   return word;
 }
 
-template <typename CellT>
+template <typename CellT, bool kWrap>
 __device__ __forceinline__ void sweep_vec(uint4* base, size_t x, uint4 q, bool count, bool reset, const SweepWin& sw,
                                           uint32_t alias, uint32_t asplat, uint32_t& cnt) {
   if (count)
-    cnt += count_in_window<CellT>(q.x, sw) + count_in_window<CellT>(q.y, sw) + count_in_window<CellT>(q.z, sw) +
-           count_in_window<CellT>(q.w, sw);
+    cnt += count_in_window<CellT, kWrap>(q.x, sw) + count_in_window<CellT, kWrap>(q.y, sw) +
+           count_in_window<CellT, kWrap>(q.z, sw) + count_in_window<CellT, kWrap>(q.w, sw);
   if (reset && (has_stamp<CellT>(q.x, asplat) | has_stamp<CellT>(q.y, asplat) | has_stamp<CellT>(q.z, asplat) |
                 has_stamp<CellT>(q.w, asplat))) {
     uint4 r;
@@ -383,6 +385,23 @@ __device__ __forceinline__ void sweep_vec(uint4* base, size_t x, uint4 q, bool c
     r.w = clear_stamp<CellT>(q.w, alias);
     base[x] = r;
   }
+}
+
+// One block's part of one row: grid-stride over the row's vectors from `x`, four loads in
+// flight per thread.
+template <typename CellT, bool kWrap>
+__device__ __forceinline__ uint32_t sweep_part(uint4* base, size_t nvec, size_t x, size_t stride, bool count,
+                                               bool reset, const SweepWin& sw, uint32_t alias, uint32_t asplat) {
+  uint32_t cnt = 0;
+  for (; x + 3 * stride < nvec; x += 4 * stride) {
+    uint4 q[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) q[j] = base[x + j * stride];
+#pragma unroll
+    for (int j = 0; j < 4; j++) sweep_vec<CellT, kWrap>(base, x + j * stride, q[j], count, reset, sw, alias, asplat, cnt);
+  }
+  for (; x < nvec; x += stride) sweep_vec<CellT, kWrap>(base, x, base[x], count, reset, sw, alias, asplat, cnt);
+  return cnt;
 }
 
 // ------------------------------------------------------------- Eq. 8 and Eq. 9 (b2)

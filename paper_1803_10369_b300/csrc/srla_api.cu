@@ -53,6 +53,7 @@ struct srla_s {
   uint64_t staging_used;  // staging packets used in the open slice
   uint64_t launches;      // kernels launched so far
   int occ_scan[2];        // resident scan blocks per SM (unaligned, aligned batches)
+  int occ_sweep;          // resident sweep blocks per SM
   int sort_grid;          // blocks of the cooperative sort
   cudaGraphExec_t graph[2];    // captured slice end, by slice parity
   uint64_t graph_launches;     // kernels per captured slice end
@@ -141,17 +142,18 @@ int launch_scan(srla_t* h, const uint32_t* pairs, uint64_t n) {
   return cuda_err(cudaGetLastError());
 }
 
-// About sms * 8 blocks in all, shared between the SLE and SRE rows in proportion to their
-// lengths (at least one block per row, at most one per 1024 vectors).
+// One wave of resident blocks (sms * occupancy) in all, shared between the SLE and SRE rows
+// in proportion to their lengths (at least one block per row, at most one per 1024 vectors);
+// a second, partial wave would leave most SMs idle at its end.
 template <typename CellT>
 int launch_sweep(srla_t* h, int census, int reset, int after_close) {
   const srla_params& p = h->p;
   const double le_row = (double)cell_array_bytes<CellT>((size_t)p.v * p.gl) / 16;
   const double re_row = (double)cell_array_bytes<CellT>((size_t)p.v * p.g) / 16;
-  const double target = (double)h->sms * 8 / p.u;  // blocks per (SLE row + SRE row)
+  const double target = (double)h->sms * h->occ_sweep / p.u;  // blocks per (SLE row + SRE row)
   const double share = reset ? le_row / (le_row + re_row) : 1.0;
   auto blocks = [](double want, double vecs) {
-    return (uint32_t)std::max(1.0, std::min(std::floor(want + 0.5), std::ceil(vecs / 1024)));
+    return (uint32_t)std::max(1.0, std::min(std::floor(want), std::ceil(vecs / 1024)));
   };
   const uint32_t gx_le = blocks(target * share, le_row);
   const uint32_t gx_re = reset ? blocks(target * (1.0 - share), re_row) : 0u;
@@ -314,9 +316,10 @@ int reset_tables(srla_t* h, bool all) {
   return clear_pairs(h);
 }
 
-// Resident blocks per SM of the scan, and the cooperative sort's grid (all co-resident).
+// Resident blocks per SM of the scan and of the sweep, and the cooperative sort's grid (all
+// co-resident).
 int occupancy(srla_t* h) {
-  int a = 0, b = 0, c = 0;
+  int a = 0, b = 0, c = 0, sw = 0;
   const int rs = with_cells(h->p.dr_bytes, [&](auto cell) {
     using CellT = decltype(cell);
     const bool inl = inline_mode(h);
@@ -327,7 +330,8 @@ int occupancy(srla_t* h) {
     if (cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k0, threads, smem) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1, threads, smem) != cudaSuccess)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1, threads, smem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sw, k_sweep<CellT>, 256, 0) != cudaSuccess)
       return SRLA_E_CUDA;
     return SRLA_OK;
   });
@@ -336,6 +340,7 @@ int occupancy(srla_t* h) {
     return SRLA_E_CUDA;
   h->occ_scan[0] = std::max(1, a);
   h->occ_scan[1] = std::max(1, b);
+  h->occ_sweep = std::max(1, sw);
   h->sort_grid = (int)std::max<uint32_t>(1, std::min<uint32_t>(h->L.ntiles, (uint32_t)(h->sms * c)));
   return SRLA_OK;
 }

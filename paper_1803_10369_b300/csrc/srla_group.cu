@@ -99,7 +99,7 @@ struct srla_group_s {
   cudaStream_t st = nullptr, st_copy = nullptr, st_side = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr}, ev_fork = nullptr, ev_join = nullptr;
   int sms = 0, scan_grid = 0, sort_grid = 0;
-  int filt_grid = 0, est_grid = 0;  // one wave of resident blocks
+  int filt_grid = 0, est_grid = 0, sweep_grid = 0;  // one wave of resident blocks
   void* h_pinned = nullptr;
   TaskHeader* h_tasks[2] = {nullptr, nullptr};
   srla_slice_stats* h_stats[2] = {nullptr, nullptr};
@@ -337,13 +337,13 @@ int enqueue_slice(srla_group_t* g, int q) {
   G_TRY(cudaLaunchCooperativeKernel((const void*)kg_sort, dim3(g->sort_grid), dim3(kSortThreads), args,
                                     kSortSmallSmem, g->st_side));
   G_TRY(cudaEventRecord(g->ev_join, g->st_side));
-  kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 0);
+  kg_sweep<<<g->sweep_grid, 256, 0, g->st>>>(descs, gctl, 0);
   kg_lut<<<std::max(1, std::min<int>((int)g->max_links, g->sms * 4)), 256, 0, g->st>>>(descs, gctl);
   G_TRY(cudaStreamWaitEvent(g->st, g->ev_join, 0));
   kg_estimate<<<g->est_grid, 256, 0, g->st>>>(descs, gctl, reinterpret_cast<srla_slice_stats*>(g->ws + F.gstats[q]),
                                              rep_off, reinterpret_cast<srla_entry*>(g->ws + F.grep[q]));
   g->launches += 1;
-  kg_sweep<<<g->sms * 8, 256, 0, g->st>>>(descs, gctl, 1);
+  kg_sweep<<<g->sweep_grid, 256, 0, g->st>>>(descs, gctl, 1);
   G_TRY(cudaGetLastError());
   G_TRY(cudaMemcpyAsync(g->h_stats[q], g->ws + F.gstats[q], sizeof(srla_slice_stats) * g->max_links,
                         cudaMemcpyDeviceToHost, g->st));
@@ -450,9 +450,10 @@ int srla_group_create(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_p
       std::memset(g->h_tasks[q], 0, tbytes);
     }
     cudaFuncSetAttribute(kg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmallSmem);
-    int o128 = 0, o512 = 0, o_filt = 0, o_est = 0;
+    int o128 = 0, o512 = 0, o_filt = 0, o_est = 0, o_sweep = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o_filt, kg_filter, 256, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o_est, kg_estimate, 256, 0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o_sweep, kg_sweep, 256, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_scan, kg_scan<256>, 256, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o128, kg_scan<128>, 128, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o512, kg_scan<512>, 512, 0) != cudaSuccess ||
@@ -466,6 +467,7 @@ int srla_group_create(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_p
     g->sort_grid = g->sms * occ_sort;
     g->filt_grid = g->sms * std::max(1, o_filt);
     g->est_grid = g->sms * std::max(1, o_est);
+    g->sweep_grid = g->sms * std::max(1, o_sweep);
   }
   if (rc == SRLA_OK) rc = gerr(cudaMemsetAsync(g->ws, 0, g->F.total, g->st));
   if (rc == SRLA_OK) {

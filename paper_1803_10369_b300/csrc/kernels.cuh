@@ -246,9 +246,10 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
   const int lane = threadIdx.x & 31;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  // 2n tasks: task i < n estimates candidate i (union SLE), task n + i runs its carry test
-  // (post-slide union SRE); the two gathers of a candidate run in different warps
-  for (uint32_t idx = gw; idx < 2 * n; idx += nw) {
+  // While there are no more candidates than warps, 2n tasks: task i < n estimates candidate
+  // i (union SLE), task n + i runs its carry test (post-slide union SRE); the two gathers of
+  // a candidate run in different warps.
+  for (uint32_t idx = gw; n <= nw && idx < 2 * n; idx += nw) {
     const bool est = idx < n;
     const uint32_t i = est ? idx : idx - n;
     const uint32_t aip = clist[i];
@@ -288,6 +289,77 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
           atomicOr(&ctl->overflow_next, 2u);
       } else if (r < 0) {
         atomicOr(&ctl->overflow_next, 2u);
+      }
+    }
+  }
+  // Above that, two tasks per run of b consecutive candidates: one estimates them (union SLE),
+  // one runs their carry test (post-slide union SRE).  b grows up to 32 so that a run's hosts,
+  // origin flags, report entries and next-slice inserts are handled with one lane per
+  // candidate, their round trips paid once per run; only the gathers stay one candidate at a
+  // time.
+  const uint32_t b = min(32u, max(1u, (n + nw - 1) / nw));
+  const uint32_t runs = n > nw ? (n + b - 1) / b : 0u;
+  for (uint32_t t = gw; t < 2 * runs; t += nw) {
+    const bool est = t < runs;
+    const uint32_t r0 = (est ? t : t - runs) * b;
+    const uint32_t m = min(b, n - r0);  // candidates of this run, one per lane
+    const bool mine = (uint32_t)lane < m;
+    const uint32_t my_aip = mine ? clist[r0 + lane] : 0u;
+    if (est) {
+      uint32_t origin = 0;
+      if (mine) {  // issued before the gathers, used after them
+        const uint32_t s = set_find(ctab, cmask, tag, my_aip);
+        origin = (s != 0xFFFFFFFFu) ? cflags[s] : 0u;
+      }
+      uint32_t my_w = 0;
+      for (uint32_t j = 0; j < m; j++) {
+        const uint32_t aip = __shfl_sync(kFull, my_aip, (int)j);
+        const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
+        const uint32_t w = union_count<CellT>(le, geo.v, geo.gl, geo.u, mycol, win, lane);
+        if ((uint32_t)lane == j) my_w = w;
+      }
+      if (mine) {
+        srla_entry e;
+        e.aip = my_aip;
+        e.w = my_w;
+        e.est = lut_est[my_w];
+        e.flags = origin | lut_flags[my_w];
+        rep[r0 + lane] = e;
+      }
+      continue;
+    }
+    // inline mode: a carried host gets its SI bits in the next slice's indicators (Algorithm 3)
+    uint32_t* si_next = par ? si0 : si1;
+    bool pass = false;
+    for (uint32_t j = 0; j < m; j++) {
+      const uint32_t aip = __shfl_sync(kFull, my_aip, (int)j);
+      const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
+      const uint32_t cw = union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, win_post, lane);
+      if ((uint32_t)lane == j) pass = cw >= geo.rho_g;
+      if (cw >= geo.rho_g && si_next && (uint32_t)lane < geo.u)
+        atomicOr(si_next + (size_t)lane * geo.v + mycol, 1u << si_bit(coef, geo.u, aip));
+    }
+    // the run's carried hosts join the next slice's candidate set and list together
+    int r = -2;
+    if (pass) {
+      uint32_t slot;
+      r = set_insert(ntab, cmask, ntag, my_aip, &slot);
+      if (r == 1)
+        nflags[slot] = SRLA_CARRIED;
+      else if (r < 0)
+        atomicOr(&ctl->overflow_next, 2u);
+    }
+    const unsigned ins = __ballot_sync(kFull, r == 1);
+    if (ins) {
+      const int first = __ffs(ins) - 1;
+      unsigned at = 0;
+      if (lane == first) at = atomicAdd(&ctl->cat_count[par ^ 1], (unsigned)__popc(ins));
+      at = __shfl_sync(kFull, at, first) + (unsigned)__popc(ins & ((1u << lane) - 1u));
+      if (r == 1) {
+        if (at < cmax)
+          nlist[at] = my_aip;
+        else
+          atomicOr(&ctl->overflow_next, 2u);
       }
     }
   }

@@ -174,6 +174,16 @@ def scatter_probe(buf, cell_bytes: int, n_stores: int, seed: int = 1, stream=Non
                                  n_stores, seed, policy, ctypes.c_void_p(st.cuda_stream)), "srla_scatter_probe")
 
 
+def _pinned_entries(n: int):
+    """A reusable report buffer of n entries in page-locked host memory (device-to-host copies
+    into it run at the link's full rate; into pageable memory they are several times slower).
+    Returns the numpy view and the torch tensor that owns the memory."""
+    import torch
+
+    mem = torch.empty(max(1, n) * ENTRY_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+    return mem.numpy().view(ENTRY_DTYPE)[:n], mem
+
+
 def params_for(w, hash_a, hash_b, **over) -> srla_params:
     """Parameters of a synth.Workload-like object (fields u, v, g, gl, dr_bytes, z, k, theta...)."""
     kw = dict(u=w.u, v=w.v, g=w.g, gl=w.gl, dr_bytes=w.dr_bytes, z=w.z, k=w.k, theta=w.theta,
@@ -218,7 +228,7 @@ class Link:
                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)), "srla_create")
         self._h = h
         self._last = None
-        self._out = np.empty(params.max_candidates, dtype=ENTRY_DTYPE)  # reused report buffer
+        self._out, self._out_mem = _pinned_entries(params.max_candidates)  # reused report buffer
 
     # -- packets ---------------------------------------------------------------
     def push(self, pairs):
@@ -263,11 +273,10 @@ class Link:
         if rc != OK and not (allow_overflow and rc == E_CAPACITY):
             raise SRLAError(rc, "srla_report")
         m = min(n.value, cap)
-        e = out[:m]
+        e = out[:m].copy()  # one contiguous copy out of the reused buffer; the fields view it
         stats = {f: getattr(st, f) for f, _ in srla_slice_stats._fields_ if f != "census"}
         stats["census"] = np.array(st.census[: self.params.u], dtype=np.uint64)
-        return {"aip": e["aip"].copy(), "w": e["w"].copy(), "est": e["est"].copy(),
-                "flags": e["flags"].copy(), "stats": stats, "rc": rc}
+        return {"aip": e["aip"], "w": e["w"], "est": e["est"], "flags": e["flags"], "stats": stats, "rc": rc}
 
     def kernel_launches(self) -> int:
         return self.L.srla_kernel_launches(self._h)
@@ -362,7 +371,7 @@ class Group:
         self._h = h
         self.params = {}
         self._keep = []
-        self._out = np.empty(max_report, dtype=ENTRY_DTYPE)
+        self._out, self._out_mem = _pinned_entries(max_report)
 
     @staticmethod
     def link_bytes(params: srla_params) -> int:

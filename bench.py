@@ -74,8 +74,8 @@ def _algorithmic_bytes_per_pkt(w, tau):
 # DRAM traffic of one k_scan launch (5M packets of the paper-scale workload) from one ncu
 # capture (profiles/k_scan_paper_scale.md), valid only for the kernel sources it was taken on.
 SCAN_TRAFFIC = {
-    "sources": "15b49b84df8b67a9",
-    "paper-1link-u8-v16384-g128-gl256-z16-k300-5Mpps": {"bytes_per_launch": 103.766528e6 + 56.492032e6,
+    "sources": "341e4747ee909743",
+    "paper-1link-u8-v16384-g128-gl256-z16-k300-5Mpps": {"bytes_per_launch": 103.644160e6 + 56.353536e6,
                                                          "pkts": 5_000_000},
 }
 

@@ -18,7 +18,7 @@ constexpr size_t scan_smem_bytes() {
   return (kInline ? 0 : (size_t)kSeen * 8) + (size_t)((kInline ? kScanThreadsInline : kScanThreads) / 32) * 2 * kQueue * 8;
 }
 
-template <typename CellT, bool kVec, bool kInline = false>
+template <typename CellT, bool kVec, bool kInline = false, bool kElide = false>
 __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, kInline ? 2 : 1) k_scan(const uint32_t* __restrict__ pairs, uint64_t n, Geo geo,
                                                           const __grid_constant__ Coef coef, CellT* __restrict__ re,
                                                           CellT* __restrict__ le, Ctl* __restrict__ ctl,
@@ -69,14 +69,16 @@ __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, k
         // the pair that marks empty slots cannot be claimed: it is always scanned
         queue_push(Q.q1, Q.n1, miss && key != kNoPair, key, lane);
         queue_push(Q.q2, Q.n2, miss && key == kNoPair, key, lane);
-        if (Q.n2 >= 32) drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+        if (Q.n2 >= 32)
+          drain_scan<CellT, false, kElide>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
         if (Q.n1 >= 32)
-          drain_claim<CellT>(Q, ptab, pmask, n_miss, n_gdup, geo, coef, code, re, le, ctl, utab, umask, ulist, umax,
-                             tag, lane);
+          drain_claim<CellT, kElide>(Q, ptab, pmask, n_miss, n_gdup, geo, coef, code, re, le, ctl, utab, umask, ulist,
+                                     umax, tag, lane);
       } else {
         queue_push(Q.q2, Q.n2, miss, key, lane);
         if (Q.n2 >= 32)
-          drain_scan<CellT, kInline>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, &ia, &win);
+          drain_scan<CellT, kInline, kElide>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, &ia,
+                                             &win);
       }
     }
 #pragma unroll
@@ -87,10 +89,11 @@ __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, k
   }
   // what is left in the queues
   if (ptab && Q.n1)
-    drain_claim<CellT>(Q, ptab, pmask, n_miss, n_gdup, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag,
-                       lane);
+    drain_claim<CellT, kElide>(Q, ptab, pmask, n_miss, n_gdup, geo, coef, code, re, le, ctl, utab, umask, ulist, umax,
+                               tag, lane);
   while (Q.n2)
-    drain_scan<CellT, kInline>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, &ia, &win);
+    drain_scan<CellT, kInline, kElide>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, &ia,
+                                       &win);
   if (ptab) {  // one global update per block
     __shared__ unsigned s_miss, s_gdup;
     if (threadIdx.x == 0) s_miss = s_gdup = 0;

@@ -62,7 +62,7 @@ __device__ __forceinline__ uint32_t seen_slot(unsigned long long key) {
 // Full scan of one pair per lane (a dense batch): Algorithm 2's DRsets, and the sampled host
 // into the slice's set (one probe per distinct host of the warp, one append counter update
 // per warp).  All 32 lanes call it; `ok` marks the lanes that hold a pair.
-template <typename CellT, bool kInline = false>
+template <typename CellT, bool kInline = false, bool kElide = false>
 __device__ __forceinline__ unsigned scan_dense(uint32_t aip, uint32_t bip, bool ok, const Geo& geo, const Coef& coef,
                                            CellT code, CellT* __restrict__ re, CellT* __restrict__ le,
                                            Ctl* __restrict__ ctl, unsigned long long* __restrict__ utab,
@@ -102,6 +102,30 @@ __device__ __forceinline__ unsigned scan_dense(uint32_t aip, uint32_t bip, bool 
 #pragma unroll
           for (int r = 0; r < 4; r++)
             if (!((h[r] >> (x[r] & 31u)) & 1u)) dr_set<CellT>(re, x[r], code);
+        }
+      }
+    } else if constexpr (kElide) {
+      // Four rows at a time, their cells read first; a cell already holding the slice's
+      // stamp is not written again (only this slice's writers store that stamp, so an equal
+      // value, even from this SM's L1, is current).  Chosen when most pairs are new (the pair
+      // table is off): then a good share of the stores would repeat a stamp already there.
+      for (uint32_t i0 = 0; i0 < u; i0 += 4) {
+        size_t xl[4], xr[4];
+        CellT hl[4], hr[4];
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          const uint32_t i = i0 + (uint32_t)r;
+          const uint32_t c = i < u ? hash61(coef.a[i], coef.b[i], aip) & geo.vmask : 0u;
+          const size_t se = (size_t)i * geo.v + c;
+          xl[r] = se * geo.gl + jl;
+          xr[r] = se * geo.g + jr;
+          hl[r] = i < u ? le[xl[r]] : code;
+          hr[r] = (samp && i < u) ? re[xr[r]] : code;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; r++) {
+          if (hl[r] != code) dr_set<CellT>(le, xl[r], code);
+          if (hr[r] != code) dr_set<CellT>(re, xr[r], code);
         }
       }
     } else {
@@ -245,7 +269,7 @@ __device__ __forceinline__ bool queue_take(volatile unsigned long long* q, uint3
   return ok;
 }
 
-template <typename CellT, bool kInline = false>
+template <typename CellT, bool kInline = false, bool kElide = false>
 __device__ __forceinline__ void drain_scan(ScanQueues& Q, const Geo& geo, const Coef& coef, CellT code,
                                            CellT* __restrict__ re, CellT* __restrict__ le, Ctl* __restrict__ ctl,
                                            unsigned long long* __restrict__ utab, uint32_t umask,
@@ -254,12 +278,12 @@ __device__ __forceinline__ void drain_scan(ScanQueues& Q, const Geo& geo, const 
   unsigned long long key;
   const bool ok = queue_take(Q.q2, Q.n2, lane, key);
   const uint32_t aip = (uint32_t)(key >> 32);
-  const unsigned sm = scan_dense<CellT, kInline>(aip, (uint32_t)key, ok, geo, coef, code, re, le, ctl, utab, umask,
-                                                 ulist, umax, tag, lane);
+  const unsigned sm = scan_dense<CellT, kInline, kElide>(aip, (uint32_t)key, ok, geo, coef, code, re, le, ctl, utab,
+                                                         umask, ulist, umax, tag, lane);
   if constexpr (kInline) inline_test<CellT>(sm, aip, geo, coef, re, *win, ctl, *ia, lane);
 }
 
-template <typename CellT>
+template <typename CellT, bool kElide = false>
 __device__ __forceinline__ void drain_claim(ScanQueues& Q, unsigned long long* __restrict__ ptab, uint32_t pmask,
                                             uint32_t& n_miss, uint32_t& n_gdup, const Geo& geo, const Coef& coef,
                                             CellT code, CellT* __restrict__ re, CellT* __restrict__ le,
@@ -280,7 +304,7 @@ __device__ __forceinline__ void drain_claim(ScanQueues& Q, unsigned long long* _
   }
   queue_push(Q.q2, Q.n2, scan, key, lane);
   if (Q.n2 >= 32)
-    drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+    drain_scan<CellT, false, kElide>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
 }
 
 template <bool kVec>

@@ -63,6 +63,7 @@ struct srla_s {
     cudaEvent_t ev;
     srla_slice_stats* h_stats;
     srla_entry* h_entries;
+    uint32_t* h_pair_mode;  // pair-table state of the slice after this one (read-first scan hint)
   } slot[2];
   void* h_pinned;
 
@@ -123,10 +124,26 @@ InlineArgs inline_args(const srla_t* h) {
   return a;
 }
 
+// Read-first scan (8/16-bit recorders, order-free mode) when the newest slice whose report
+// has reached the host ran with the pair table off: most pairs are then new, and a good share
+// of their stores would repeat a stamp already in place.  The hint is one or two slices old
+// and never waits; either scan gives the same recorders.
+bool read_first_hint(const srla_t* h) {
+  for (uint64_t back = 1; back <= 2 && back <= h->T; back++) {
+    const srla_s::Slot& s = h->slot[(h->T - back) & 1];
+    if (!s.valid || s.slice != h->T - back) continue;
+    if (cudaEventQuery(s.ev) != cudaSuccess) continue;
+    return *s.h_pair_mode == 0;
+  }
+  return false;
+}
+
 template <typename CellT>
 int launch_scan(srla_t* h, const uint32_t* pairs, uint64_t n) {
   const bool vec = (reinterpret_cast<uintptr_t>(pairs) & 15u) == 0;
+  const bool elide = !kIsBit<CellT> && !inline_mode(h) && read_first_hint(h);
   auto kern = inline_mode(h) ? (vec ? k_scan<CellT, true, true> : k_scan<CellT, false, true>)
+              : elide        ? (vec ? k_scan<CellT, true, false, true> : k_scan<CellT, false, false, true>)
                              : (vec ? k_scan<CellT, true> : k_scan<CellT, false>);
   const int threads = inline_mode(h) ? kScanThreadsInline : kScanThreads;
   const size_t smem = inline_mode(h) ? scan_smem_bytes<true>() : scan_smem_bytes<false>();
@@ -277,6 +294,8 @@ int enqueue_report_copy(srla_t* h, int q) {
   const uint32_t pre = std::min<uint32_t>(kPrefetch, h->p.max_candidates);
   SRLA_TRY(cudaMemcpyAsync(s.h_entries, h->ws + h->L.rep_entries[q], (size_t)pre * sizeof(srla_entry),
                            cudaMemcpyDeviceToHost, h->st_d2h));
+  SRLA_TRY(cudaMemcpyAsync(s.h_pair_mode, &h->ctl()->pair_mode, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                           h->st_d2h));
   SRLA_TRY(cudaEventRecord(s.ev, h->st_d2h));
   return SRLA_OK;
 }
@@ -329,6 +348,10 @@ int occupancy(srla_t* h) {
     const size_t smem = inl ? scan_smem_bytes<true>() : scan_smem_bytes<false>();
     if (cudaFuncSetAttribute(k0, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
         cudaFuncSetAttribute(k1, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+        cudaFuncSetAttribute(k_scan<CellT, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scan_smem_bytes<false>()) != cudaSuccess ||
+        cudaFuncSetAttribute(k_scan<CellT, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scan_smem_bytes<false>()) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k0, threads, smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1, threads, smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&sw, k_sweep<CellT>, 256, 0) != cudaSuccess)
@@ -403,7 +426,7 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
     delete h;
     return cuda_err(cudaErrorUnknown);
   }
-  const size_t per_slot = sizeof(srla_slice_stats) + (size_t)kPrefetch * sizeof(srla_entry);
+  const size_t per_slot = sizeof(srla_slice_stats) + (size_t)kPrefetch * sizeof(srla_entry) + 16;
   if (cudaHostAlloc(&h->h_pinned, 2 * per_slot, cudaHostAllocDefault) != cudaSuccess) {
     delete h;
     return cuda_err(cudaErrorMemoryAllocation);
@@ -432,6 +455,8 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
     h->slot[q].h_stats = reinterpret_cast<srla_slice_stats*>(static_cast<char*>(h->h_pinned) + q * per_slot);
     h->slot[q].h_entries = reinterpret_cast<srla_entry*>(reinterpret_cast<char*>(h->slot[q].h_stats) +
                                                          sizeof(srla_slice_stats));
+    h->slot[q].h_pair_mode = reinterpret_cast<uint32_t*>(h->slot[q].h_entries + kPrefetch);
+    *h->slot[q].h_pair_mode = 1u;
     if (cudaEventCreateWithFlags(&h->slot[q].ev, cudaEventDisableTiming) != cudaSuccess) rc = SRLA_E_CUDA;
   }
   if (rc == SRLA_OK) {

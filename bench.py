@@ -74,8 +74,8 @@ def _algorithmic_bytes_per_pkt(w, tau):
 # DRAM traffic of one k_scan launch (5M packets of the paper-scale workload) from one ncu
 # capture (profiles/k_scan_paper_scale.md), valid only for the kernel sources it was taken on.
 SCAN_TRAFFIC = {
-    "sources": "341e4747ee909743",
-    "paper-1link-u8-v16384-g128-gl256-z16-k300-5Mpps": {"bytes_per_launch": 103.644160e6 + 56.353536e6,
+    "sources": "c0b046b4b67206a2",
+    "paper-1link-u8-v16384-g128-gl256-z16-k300-5Mpps": {"bytes_per_launch": 103.776768e6 + 55.736576e6,
                                                          "pkts": 5_000_000},
 }
 

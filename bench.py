@@ -38,6 +38,8 @@ def _args():
     ap.add_argument("--latency-slices", type=int, default=100)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-multi", action="store_true",
+                    help="skip the batched (64 links) and served sub-measurements of the default line")
     ap.add_argument("--mode", default="order-free", choices=["order-free", "inline"],
                     help="candidate rule of the single-link workloads (inline: Algorithm 2 as printed)")
     return ap.parse_args()
@@ -72,7 +74,8 @@ def _algorithmic_bytes_per_pkt(w, tau):
 
 
 # DRAM traffic of one k_scan launch (5M packets of the paper-scale workload) from one ncu
-# capture (profiles/k_scan_paper_scale.md), valid only for the kernel sources it was taken on.
+# capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
+# kernel sources it was taken on.
 SCAN_TRAFFIC = {
     "sources": "c0b046b4b67206a2",
     "paper-1link-u8-v16384-g128-gl256-z16-k300-5Mpps": {"bytes_per_launch": 103.776768e6 + 55.736576e6,
@@ -292,18 +295,21 @@ def bench_srla(args):
     with Clocks(smi_id) as clk:
         ev[0].record(stream)
         pending = None
+        timed_stats = []
+        builds0 = link.scan_builds()
         for i in range(K):
             scan_ev[i][0].record(stream)
             link.push(batches[i])
             scan_ev[i][1].record(stream)
             sid = link.end_slice()
             if pending is not None:
-                link.report(pending)
+                timed_stats.append(link.report(pending)["stats"])
             pending = sid
         ev[1].record(stream)
-        link.report(pending)
+        timed_stats.append(link.report(pending)["stats"])
         torch.cuda.synchronize(dev)
     launches = link.kernel_launches() - launches0
+    builds = [b - a for a, b in zip(builds0, link.scan_builds())]
     barrier()
     elapsed_ms = max_over_ranks(ev[0].elapsed_time(ev[1]), world, dev)
     scan_ms = [a.elapsed_time(b) for a, b in scan_ev]
@@ -354,6 +360,7 @@ def bench_srla(args):
     per_launch_pkts = pkts / K
     achieved = bpp * per_launch_pkts / (scan_avg_ms * 1e-3) / 1e9
     store_roof = _store_roofline(w, tau, dev, stream, per_launch_pkts / (scan_avg_ms * 1e-3))
+    l2_roof = _l2_roofline(w, params, timed_stats, builds, scan_avg_ms, store_roof, dev, stream)
     line = {
         "metric": METRIC, "value": round(value, 3), "unit": "Mpkts/s", "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": round(elapsed_ms / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -365,7 +372,7 @@ def bench_srla(args):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 5), "traffic": _scan_traffic(w.name, int(per_launch_pkts)),
                      "kernel": "k_scan", "bytes_per_pkt": bpp, "peak_kind": peak_kind,
-                     "store_roofline": store_roof},
+                     "store_roofline": store_roof, "l2": l2_roof},
         "e2e": {"value": round(e2e, 3), "unit": "Mpkts/s", "h2d_bytes_per_step": int(8 * per_launch_pkts),
                 "d2h_bytes_per_step": int(statistics.mean(d2h))},
         "gpu_launches": int(launches),
@@ -374,6 +381,13 @@ def bench_srla(args):
         "prefill_slices": prefill,
     }
     link.close()
+    del batches, host
+    torch.cuda.empty_cache()
+    if world == 1 and args.workload == "paper" and args.mode == "order-free" and not args.no_multi:
+        # many links on the same GPU: one group launch per slice against the per-link loop,
+        # and the serving loop against the per-link loop (same packets, same latency span)
+        line["batched"] = measure_batched(K, W, 24, dev)
+        line["served"] = measure_served(K, W, 8, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         mpps, timed, pk, secs = run_oracle(w, 0, 0, device_for_gen=dev, seconds=args.cpu_seconds)
         cores, model = _cpu_info()
@@ -429,23 +443,106 @@ def _store_roofline(w, tau, dev, stream, scan_pkts_per_s):
             "note": "random stores over the recorders' footprint; the scan de-duplicates pairs, so it can exceed 1"}
 
 
+def _probe_rate(dev, stream, nbytes, cell, policy, n, fill=0):
+    """Median accesses/s of srla_scatter_probe over a buffer of nbytes (3 timed runs)."""
+    import torch
+
+    from paper_1803_10369_b300 import srla
+
+    buf = torch.full((nbytes,), fill, dtype=torch.uint8, device=dev)
+    rates = []
+    with torch.cuda.stream(stream):
+        for rep in range(4):
+            if policy == srla.PROBE_CAS:
+                buf.fill_(0xFF)  # every slot empty again, as the pair table at a slice start
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            srla.scatter_probe(buf, cell, n, seed=2 * rep + 2, stream=stream, policy=policy)
+            e1.record(stream)
+            e1.synchronize()
+            if rep:
+                rates.append(n / (e0.elapsed_time(e1) * 1e-3))
+    del buf
+    return statistics.median(rates)
+
+
+def _l2_roofline(w, params, stats, builds, scan_ms, store_roof, dev, stream):
+    """The scan against the resource that binds it: its L2 operations.  Per launch, from the
+    slice statistics the library returns (averaged over the timed slices): recorder stores
+    (u per scanned pair, u more per sampled pair; the read-first build loads each of those
+    cells first), pair-table claims (one 64-bit compare-and-swap per block-table miss),
+    sampled-host set probes (one load each) and insertions (one compare-and-swap per distinct
+    sampled host), and the input read from DRAM.  Each kind is priced at its rate measured
+    live by srla_scatter_probe on a buffer of the footprint it touches; `frac` = the time those
+    operations take at the measured rates / the measured scan time."""
+    from paper_1803_10369_b300 import srla
+
+    n = len(stats)
+    avg = lambda key: sum(float(st[key]) for st in stats) / n  # noqa: E731
+    scanned, sampled = avg("n_scanned"), avg("n_scanned_sampled")
+    claims, probes, inserts = avg("n_claims"), avg("n_set_probes"), avg("n_sampled")
+    pkts = avg("n_pkts")
+    read_first = builds[1] > 0 and builds[0] == 0
+    cells = w.u * (scanned + sampled)
+    ops = {"recorder_stores": cells, "recorder_loads": cells if read_first else 0.0, "pair_claims_cas": claims,
+           "set_probe_loads": probes, "set_insert_cas": inserts, "input_bytes": 8.0 * pkts}
+    ucap = 1
+    while ucap < 2 * params.max_sampled:
+        ucap <<= 1
+    ptab_bytes = (1 << (params.pair_slots_log2 if params.pair_slots_log2 > 0 else 21)) * 8
+    n_probe = 20_000_000
+    rates = {"store": store_roof["stores_per_s"],
+             "load": _probe_rate(dev, stream, store_roof["footprint_bytes"], store_roof["cell_bytes"],
+                                 srla.PROBE_LOAD, n_probe),
+             "cas_pair_table": _probe_rate(dev, stream, ptab_bytes, 8, srla.PROBE_CAS, n_probe // 2),
+             "cas_set": _probe_rate(dev, stream, max(64, ucap) * 8, 8, srla.PROBE_CAS, n_probe // 2),
+             "load_set": _probe_rate(dev, stream, max(64, ucap) * 8, 8, srla.PROBE_LOAD, n_probe)}
+    hbm, _ = _peaks()
+    t = {"recorder_stores": ops["recorder_stores"] / rates["store"],
+         "recorder_loads": ops["recorder_loads"] / rates["load"],
+         "pair_claims_cas": ops["pair_claims_cas"] / rates["cas_pair_table"],
+         "set_probe_loads": ops["set_probe_loads"] / rates["load_set"],
+         "set_insert_cas": ops["set_insert_cas"] / rates["cas_set"],
+         "input_bytes": ops["input_bytes"] / (hbm * 1e9)}
+    t_sum = sum(t.values())
+    return {"bound": "l2 operations", "ops_per_launch": {k: round(v, 1) for k, v in ops.items()},
+            "rates_per_s": {k: round(v, 0) for k, v in rates.items()},
+            "time_at_rates_us": {k: round(v * 1e6, 2) for k, v in t.items()},
+            "achieved_us": round(scan_ms * 1e3, 2), "bound_us": round(t_sum * 1e6, 2),
+            "frac": round(t_sum / (scan_ms * 1e-3), 4), "scan_build": "read-first" if read_first else "plain",
+            "pair_table_slices": int(sum(int(st["pair_table"]) for st in stats)), "slices": n,
+            "note": "frac = time the scan's L2 operations take at rates measured alone on the same footprints "
+                    "/ measured scan time"}
+
+
 def _pctl(xs, q):
     xs = sorted(xs)
     return xs[min(len(xs) - 1, int(round(q * (len(xs) - 1))))]
 
 
-def bench_batched(args):
-    """64 independent links of uneven rates: one group (one graph launch per slice for all
-    links) against the plain per-link loop (one handle per link, its own scan and slice end),
-    on the same GPU and the same device-resident packets."""
+def _smi_id(dev):
+    import torch
+
+    uuid = str(getattr(torch.cuda.get_device_properties(dev), "uuid", dev.index or 0))
+    return uuid if uuid.startswith("GPU-") or not uuid[:1].isalnum() or len(uuid) < 30 else "GPU-" + uuid
+
+
+LATENCY_SPAN = ("host time from the slice's first call (its batches already in device memory, the GPU idle) "
+                "to every link's report on the host: scans, slice ends and report copies of all links")
+
+
+def measure_batched(K, W, prefill, dev, n_links=64):
+    """64 independent links of uneven rates (synth.batched_links): one group (one graph launch
+    per slice scans and closes every link) against the plain per-link loop (one handle per
+    link, its own scan and slice end), on the same GPU and the same device-resident packets.
+    Throughput: K pipelined slices timed with CUDA events.  Latency: LATENCY_SPAN per slice,
+    the same span for both arms."""
     import torch
 
     import synth
     from paper_1803_10369_b300 import srla
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    links = synth.batched_links(64)
+    links = synth.batched_links(n_links)
     params = []
     for w, plog in links:
         ha, hb = synth.hash_coefficients(w.hash_seed, w.u + 3)
@@ -453,8 +550,34 @@ def bench_batched(args):
     n_distinct = 4
     batches = [[synth.generate_slice(w.traffic, s, device=dev) for s in range(n_distinct)] for w, _ in links]
     pkts_slice = sum(int(b[0].shape[0]) for b in batches)
-    prefill, W, K = (args.prefill if args.prefill >= 0 else 24), args.warmup, args.steps
+    n_lat = max(K, 32)
     stream = torch.cuda.Stream(dev)
+    smi = _smi_id(dev)
+
+    def timed(run_slice, latency_slice, label):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        with Clocks(smi) as clk:
+            e0.record(stream)
+            pending = None
+            for s in range(K):
+                h = run_slice(prefill + W + s)
+                if pending is not None:
+                    pending()
+                pending = h
+            e1.record(stream)
+            pending()
+            torch.cuda.synchronize(dev)
+            lat = []
+            for s in range(n_lat):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                latency_slice(s)
+                lat.append((time.perf_counter() - t0) * 1e3)
+        ms = e0.elapsed_time(e1) / K
+        return {"value": round(pkts_slice / (ms * 1e-3) / 1e6, 3), "unit": "Mpkts/s", "ms_per_step": round(ms, 4),
+                "latency_ms": {"p50": round(_pctl(lat, 0.5), 4), "p99": round(_pctl(lat, 0.99), 4), "slices": n_lat},
+                "clocks": clk.summary()}
 
     # ---- the group
     arena = sum(srla.Group.link_bytes(p) for p in params) + (64 << 20)
@@ -462,121 +585,108 @@ def bench_batched(args):
                    device=dev, stream=stream)
     ids = [g.attach(p) for p in params]
 
-    def group_slice(s):
+    def group_push(s):
         for i, l in enumerate(ids):
             g.push(l, batches[i][s % n_distinct])
-        return g.end_slice()
+
+    def group_slice(s):
+        group_push(s)
+        gs = g.end_slice()
+        return lambda: g.report_all(gs)
+
+    def group_latency(s):
+        group_push(s)
+        g.report_all(g.end_slice())
 
     with torch.cuda.stream(stream):
         for s in range(prefill + W):
             if s == prefill // 2:  # autotune the scan launch shape on a live slice
-                for i, l in enumerate(ids):
-                    g.push(l, batches[i][s % n_distinct])
+                group_push(s)
                 tuned = g.autotune(reps=3)
                 g.report_all(g.end_slice())
                 continue
-            g.report_all(group_slice(s))
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            group_slice(s)()
         launches0 = g.kernel_launches()
-        e0.record(stream)
-        pending = None
-        for s in range(K):
-            gs = group_slice(prefill + W + s)
-            if pending is not None:
-                g.report_all(pending)
-            pending = gs
-        e1.record(stream)
-        g.report_all(pending)
-        torch.cuda.synchronize(dev)
-        group_ms = e0.elapsed_time(e1) / K
-        group_launches = (g.kernel_launches() - launches0) / K
-        lat_g = []
-        for s in range(max(K, 32)):
-            for i, l in enumerate(ids):
-                g.push(l, batches[i][s % n_distinct])
-            t0 = time.perf_counter()
-            g.report_all(g.end_slice())
-            lat_g.append((time.perf_counter() - t0) * 1e3)
+        grp = timed(group_slice, group_latency, "group")
+        grp["gpu_launches_per_slice"] = (g.kernel_launches() - launches0) / (K + n_lat)
     g.close()
+    del g
 
     # ---- the plain per-link loop
     solo = [srla.Link(p, device=dev, stream=stream) for p in params]
-    with torch.cuda.stream(stream):
-        def loop_slice(s, lat=None):
-            ends = []
-            for i, L in enumerate(solo):
-                L.push(batches[i][s % n_distinct])
-                ends.append((time.perf_counter(), L.end_slice()))
-            for i, L in enumerate(solo):
-                L.report(ends[i][1])
-                if lat is not None:
-                    lat.append((time.perf_counter() - ends[i][0]) * 1e3)
 
+    def loop_slice(s):
+        sids = []
+        for i, L in enumerate(solo):
+            L.push(batches[i][s % n_distinct])
+            sids.append(L.end_slice())
+        return lambda: [L.report(sids[i]) for i, L in enumerate(solo)]
+
+    with torch.cuda.stream(stream):
         for s in range(prefill + W):
-            loop_slice(s)
-        torch.cuda.synchronize(dev)
-        e0.record(stream)
-        for s in range(K):
-            loop_slice(prefill + W + s)
-        e1.record(stream)
-        torch.cuda.synchronize(dev)
-        loop_ms = e0.elapsed_time(e1) / K
-        lat_l = []
-        for s in range(max(K, 32)):
-            loop_slice(s, lat_l)
+            loop_slice(s)()
+        loop = timed(loop_slice, lambda s: loop_slice(s)(), "loop")
     for L in solo:
         L.close()
-    line = {
-        "metric": METRIC, "value": round(pkts_slice / (group_ms * 1e-3) / 1e6, 3), "unit": "Mpkts/s", "n_gpus": 1,
-        "steps": K, "warmup": W, "ms_per_step": round(group_ms, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8/u16", "data": "synthetic",
-        "config": {"workload": "batched-64-links-rates-1e4-5e6-k16-300", "links": len(params),
-                   "pkts_per_slice": pkts_slice, "prefill_slices": prefill},
-        "latency_ms": {"p50": round(_pctl(lat_g, 0.5), 4), "p99": round(_pctl(lat_g, 0.99), 4),
-                       "what": "end_slice call to every link's report on the host (scan included)"},
-        "gpu_launches_per_slice": group_launches,
+    del solo, batches
+    torch.cuda.empty_cache()
+    grp.update({
+        "config": {"workload": f"batched-{n_links}-links-rates-1e4-5e6-k16-300", "links": len(params),
+                   "pkts_per_slice": pkts_slice, "prefill_slices": prefill,
+                   "dr_bytes": sorted({int(p.dr_bytes) for p in params})},
+        "latency_span": LATENCY_SPAN,
         "scan_autotune": {"block_threads": tuned[0], "packets_per_task": tuned[1]},
-        "per_link_loop": {"value": round(pkts_slice / (loop_ms * 1e-3) / 1e6, 3), "ms_per_step": round(loop_ms, 4),
-                          "latency_ms": {"p50": round(_pctl(lat_l, 0.5), 4), "p99": round(_pctl(lat_l, 0.99), 4),
-                                         "what": "a link's end_slice call to its report on the host"}},
-    }
+        "per_link_loop": loop,
+    })
+    return grp
+
+
+def bench_batched(args):
+    import torch
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    prefill = args.prefill if args.prefill >= 0 else 24
+    r = measure_batched(args.steps, args.warmup, prefill, dev)
+    line = {"metric": METRIC, "value": r["value"], "unit": "Mpkts/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8/u16", "data": "synthetic", **{k: v for k, v in r.items()
+                                                                            if k not in ("value", "ms_per_step")}}
     print(json.dumps(line), flush=True)
 
 
-def bench_served(args):
-    """Serving loop: links of the served workload arrive (Poisson) and depart (mean lifetime 600
-    slices), each sends its slice's packets as batches of 4K..1M pairs; the server admits links
-    under a 60 GB budget and closes one slice per tick for all of them.  Compared with the
-    plain per-link loop (one handle per link, created at arrival) on the same schedule."""
+def measure_served(K, W, prefill, dev, n_ident=256, conc=96, life=600.0):
+    """Serving loop: links of synth.served_links arrive (Poisson, `conc` open on average) and
+    depart (mean lifetime `life` slices); each sends its slice's packets as batches of 4K..1M
+    pairs; the server admits links under a 60 GB budget and closes one slice per tick for all
+    of them.  Compared with the plain per-link loop (one handle per link, created at arrival)
+    on the same schedule.  Throughput: K pipelined ticks, host wall clock.  Latency: per tick,
+    from its first call (departures, arrivals, batches; the GPU idle) to every admitted link's
+    results on the host, the same span for both arms."""
     import numpy as np
     import torch
 
     import synth
     from paper_1803_10369_b300 import srla
 
-    dev = torch.device("cuda", 0)
-    torch.cuda.set_device(dev)
-    ident = synth.served_links(256)
+    ident = synth.served_links(n_ident)
     params = []
     for w, plog in ident:
         ha, hb = synth.hash_coefficients(w.hash_seed, w.u + 3)
         params.append(srla.params_for(w, ha, hb, pair_slots_log2=plog))
     rng = np.random.default_rng(7)
-    conc, life = 96, 600.0
-    ticks = args.prefill if args.prefill >= 0 else 8
-    K, W = args.steps, args.warmup
-    n_ticks = ticks + W + K + max(K, 32)
+    n_lat = max(K, 32)
+    n_ticks = prefill + W + K + n_lat + 2
     # the schedule: who is open at each tick (identities are never reused)
     order = list(rng.permutation(len(ident)))
     active = [order.pop() for _ in range(conc)]
-    events = []
-    for t in range(n_ticks):
+    events = [([], list(active), list(active))]
+    for t in range(1, n_ticks):
         gone = [k for k in active if rng.random() < 1.0 / life]
         new = [order.pop() for _ in range(min(len(order), rng.poisson(conc / life)))]
         active = [k for k in active if k not in gone] + new
         events.append((gone, new, list(active)))
-    used = sorted(set(k for _, _, a in events for k in a) | set(events[0][2]))
+    used = sorted(set(k for _, _, a in events for k in a))
     pool = {k: [synth.generate_slice(ident[k][0].traffic, s, device=dev) for s in range(2)] for k in used}
 
     def batches_of(k, t):
@@ -590,19 +700,47 @@ def bench_served(args):
 
     plan = [{k: batches_of(k, t) for k in events[t][2]} for t in range(n_ticks)]
     pkts = [sum(int(x.shape[0]) for bs in plan[t].values() for x in bs) for t in range(n_ticks)]
+    flat = [([k for k, bs in plan[t].items() for _ in bs], [x for bs in plan[t].values() for x in bs])
+            for t in range(n_ticks)]
     stream = torch.cuda.Stream(dev)
+    smi = _smi_id(dev)
+
+    def timed(tick, first):
+        """Ticks first+1.. (prefill + W untimed), K timed pipelined ticks, n_lat latency ticks."""
+        t = first + 1
+        for _ in range(prefill + W):
+            tick(t)()
+            t += 1
+        torch.cuda.synchronize(dev)
+        with Clocks(smi) as clk:
+            t0 = time.perf_counter()
+            pending, n_pk = None, 0
+            for _ in range(K):
+                h = tick(t)
+                n_pk += pkts[t]
+                t += 1
+                if pending is not None:
+                    pending()
+                pending = h
+            pending()
+            torch.cuda.synchronize(dev)
+            secs = time.perf_counter() - t0
+            lat = []
+            for _ in range(n_lat):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                tick(t)()
+                lat.append((time.perf_counter() - t0) * 1e3)
+                t += 1
+        return {"value": round(n_pk / secs / 1e6, 3), "unit": "Mpkts/s", "ms_per_step": round(1e3 * secs / K, 4),
+                "latency_ms": {"p50": round(_pctl(lat, 0.5), 4), "p99": round(_pctl(lat, 0.99), 4), "slices": n_lat},
+                "clocks": clk.summary()}
 
     # ---- the server
     budget = 60 << 30
     arena = min(budget, sum(srla.Group.link_bytes(params[k]) for k in used) + (256 << 20))
     srv = srla.Server(max_links=256, max_pkts=2 * max(pkts), budget_bytes=budget, arena_bytes=arena,
                       max_report=1 << 21, device=dev, stream=stream)
-    for k in events[0][2]:
-        srv.open(k, params[k])
-    srv.tick()
-
-    flat = [([k for k, bs in plan[t].items() for _ in bs], [x for bs in plan[t].values() for x in bs])
-            for t in range(n_ticks)]
 
     def server_tick(t):
         gone, new, _ = events[t]
@@ -611,49 +749,23 @@ def bench_served(args):
         for k in new:
             srv.open(k, params[k])
         srv.submit_many(*flat[t])
-        return srv.tick()[0]
+        sl = srv.tick()[0]
+        return lambda: srv.poll(sl)
 
     with torch.cuda.stream(stream):
-        t = 1
-        for i in range(ticks + W):
-            if i == ticks // 2:
-                srv.autotune(3)  # the scan launch shape, tuned on a live tick
-            srv.poll(server_tick(t))
-            t += 1
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        pending, n_srv = None, 0
-        for _ in range(K):
-            sl = server_tick(t)
-            n_srv += pkts[t]
-            t += 1
-            if pending is not None:
-                srv.poll(pending)
-            pending = sl
-        srv.poll(pending)
-        torch.cuda.synchronize(dev)
-        srv_s = time.perf_counter() - t0
-        lat_s = []
-        for _ in range(max(K, 32)):
-            if t >= n_ticks:
-                break
-            gone, new, _ = events[t]
-            for k in gone:
-                srv.close(k)
-            for k in new:
-                srv.open(k, params[k])
-            srv.submit_many(*flat[t])
-            t0 = time.perf_counter()
-            srv.poll(srv.tick()[0])
-            lat_s.append((time.perf_counter() - t0) * 1e3)
-            t += 1
+        for k in events[0][2]:
+            srv.open(k, params[k])
+        srv.tick()
+        server_tick(1)()
+        srv.autotune(3)  # the scan launch shape, tuned on the next live tick
+        server = timed(server_tick, 1)
     srv.destroy()
     del srv
 
     # ---- the plain per-link loop on the same schedule
     links = {}
 
-    def loop_tick(t, lat=None):
+    def loop_tick(t):
         gone, new, _ = events[t]
         for k in gone:
             links.pop(k).close()
@@ -663,49 +775,40 @@ def bench_served(args):
         for k, L in links.items():
             for x in plan[t].get(k, []):
                 L.push(x)
-            ends.append((k, time.perf_counter(), L.end_slice()))
-        for k, t_end, sid in ends:
-            links[k].report(sid)
-            if lat is not None:
-                lat.append((time.perf_counter() - t_end) * 1e3)
+            ends.append((k, L.end_slice()))
+        return lambda: [links[k].report(sid) for k, sid in ends]
 
     with torch.cuda.stream(stream):
         for k in events[0][2]:
             links[k] = srla.Link(params[k], device=dev, stream=stream)
-        t = 1
-        for _ in range(ticks + W):
-            loop_tick(t)
-            t += 1
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        n_loop = 0
-        for _ in range(K):
-            loop_tick(t)
-            n_loop += pkts[t]
-            t += 1
-        torch.cuda.synchronize(dev)
-        loop_s = time.perf_counter() - t0
-        lat_l = []
-        for _ in range(max(K, 32)):
-            if t >= n_ticks:
-                break
-            loop_tick(t, lat_l)
-            t += 1
+        loop_tick(1)()
+        loop = timed(loop_tick, 1)
     for L in links.values():
         L.close()
-    line = {
-        "metric": METRIC, "value": round(n_srv / srv_s / 1e6, 3), "unit": "Mpkts/s", "n_gpus": 1, "steps": K,
-        "warmup": W, "ms_per_step": round(1e3 * srv_s / K, 4), "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "u8/u16", "data": "synthetic",
+    del links, pool, plan, flat
+    torch.cuda.empty_cache()
+    server.update({
         "config": {"workload": "served-poisson-links-mean-life-600-batches-4k-1M-budget-60GB",
-                   "identities": len(ident), "concurrent_links": conc,
-                   "pkts_per_tick_mean": int(np.mean(pkts)), "timing": "host wall clock, pipelined ticks"},
-        "latency_ms": {"p50": round(_pctl(lat_s, 0.5), 4), "p99": round(_pctl(lat_s, 0.99), 4),
-                       "what": "tick call to every link's results on the host (scan included)"},
-        "per_link_loop": {"value": round(n_loop / loop_s / 1e6, 3), "ms_per_step": round(1e3 * loop_s / K, 4),
-                          "latency_ms": {"p50": round(_pctl(lat_l, 0.5), 4), "p99": round(_pctl(lat_l, 0.99), 4),
-                                         "what": "a link's end_slice call to its report on the host"}},
-    }
+                   "identities": len(ident), "concurrent_links": conc, "pkts_per_tick_mean": int(np.mean(pkts)),
+                   "timing": "host wall clock, pipelined ticks"},
+        "latency_span": "host time from the tick's first call (departures, arrivals and batches already in device "
+                        "memory, the GPU idle) to every admitted link's results on the host",
+        "per_link_loop": loop,
+    })
+    return server
+
+
+def bench_served(args):
+    import torch
+
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    prefill = args.prefill if args.prefill >= 0 else 8
+    r = measure_served(args.steps, args.warmup, prefill, dev)
+    line = {"metric": METRIC, "value": r["value"], "unit": "Mpkts/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u8/u16", "data": "synthetic", **{k: v for k, v in r.items()
+                                                                            if k not in ("value", "ms_per_step")}}
     print(json.dumps(line), flush=True)
 
 

@@ -118,6 +118,18 @@ typedef struct srla_slice_stats {
                                 bit 2: a device-side wait timed out */
   double up;                 /* UP of Eq. 8 */
   uint64_t census[SRLA_MAX_ROWS]; /* |LDR(i)|^k of Section 4.2, per row */
+  /* Work of the slice's scan (Algorithm 2), for measurement; these counts depend on thread
+   * timing (which of the repeats of a pair are skipped), the results above do not.         */
+  uint32_t pair_table;       /* 1: the scans consulted the per-slice table of scanned pairs
+                                (when the link has one); 0: it was switched off this slice */
+  uint32_t pad;
+  uint64_t n_claims;         /* pairs that missed their block's table of recent pairs and
+                                claimed a slot of the pair table (one compare-and-swap each) */
+  uint64_t n_claim_repeats;  /* of which the pair table had seen already (not scanned again) */
+  uint64_t n_scanned;        /* pairs scanned: their u SLE recorders set */
+  uint64_t n_scanned_sampled; /* of which sampled: their u SRE recorders set as well */
+  uint64_t n_set_probes;     /* insertions tried into the slice's set of sampled hosts (one
+                                per distinct host of a warp's sampled pairs) */
 } srla_slice_stats;
 
 typedef struct srla_s srla_t;
@@ -188,6 +200,23 @@ int srla_import_state(srla_t *h, const void *host_buf, size_t len);
 /* Number of CUDA kernels this handle has launched since srla_create (all entry points). */
 uint64_t srla_kernel_launches(const srla_t *h);
 
+/*
+ * The scan (Algorithm 2) has two builds that leave the same recorders: the plain build stores
+ * every recorder of a scanned pair; the read-first build (8- and 16-bit recorders, order-free
+ * rule) reads the recorders first and skips those already holding the open slice's stamp,
+ * which pays when most pairs are new.  SRLA_SCAN_AUTO (the default) picks the read-first build
+ * while the newest slice whose report reached the host ran with its pair table switched off;
+ * the other two force one build (a tuning and testing aid).  srla_set_scan_build returns
+ * SRLA_E_INVAL for an unknown value, or for SRLA_SCAN_READ_FIRST on one-bit recorders or in
+ * the inline mode.  srla_scan_builds counts the scan launches of each build since
+ * srla_create (either pointer may be NULL).
+ */
+#define SRLA_SCAN_AUTO 0u
+#define SRLA_SCAN_PLAIN 1u
+#define SRLA_SCAN_READ_FIRST 2u
+int srla_set_scan_build(srla_t *h, uint32_t build);
+int srla_scan_builds(const srla_t *h, uint64_t *plain, uint64_t *read_first);
+
 /* 1 if srla_end_slice replays a CUDA graph captured at srla_create (one per slice parity),
  * 0 if it launches its kernels one by one (capture was not possible on this device). */
 int srla_uses_graph(const srla_t *h);
@@ -198,15 +227,15 @@ void srla_destroy(srla_t *h);
  * Allocation-free batch report (the paper has no counterpart; this is a service for callers).
  *
  * Some callers cannot allocate device memory: a packet-capture thread with real-time
- * deadlines (cudaMalloc and cudaFree may synchronize the whole device), a plugin whose host
- * framework owns all device memory and hands it only fixed input and output buffers, or code
- * running while a stream is being captured.  This entry point needs no workspace and makes
- * no device or host allocation: it runs the scan and the slice end of a fresh estimator
- * over one device batch d_pairs (n_pairs interleaved aip, bip) on `stream`, i.e. the report
- * that srla_create + srla_push_packets + srla_end_slice + srla_report give for a first slice
- * holding exactly this batch, and copies it (sorted by aip) to the host buffer out
- * (cap entries; *n_out = full count; stats may be NULL).  It returns when the report is on
- * the host.
+ * deadlines (cudaMalloc and cudaFree may synchronize the whole device and stall it), or a
+ * plugin whose host framework owns all device memory and hands it only fixed input and
+ * output buffers.  This entry point needs no workspace and makes no device or host
+ * allocation: it runs the scan and the slice end of a fresh estimator over one device batch
+ * d_pairs (n_pairs interleaved aip, bip) on `stream`, i.e. the report that srla_create +
+ * srla_push_packets + srla_end_slice + srla_report give for a first slice holding exactly
+ * this batch, and copies it (sorted by aip) to the host buffer out (cap entries; *n_out =
+ * full count; stats may be NULL).  It synchronizes `stream` and returns when the report is
+ * on the host.
  *
  * Scratch: a fixed array of SRLA_STATIC_SCRATCH_BYTES compiled into the library, present on
  * every GPU that loads the library until the process exits.  Parameters whose one-slice
@@ -234,21 +263,27 @@ int srla_wait_selftest(void *dev_scratch, size_t bytes, void *stream, uint32_t b
                        uint32_t spin_limit);
 
 /* Store roofline probe (a measurement aid, not part of the method): enqueues on `stream`
- * n_stores writes of cell_bytes (1, 2 or 4) each to pseudo-random cells of the caller's
- * device buffer dev_buf of `bytes` bytes (at least one cell, 4-byte aligned): the access
- * shape of the scan's recorder updates (Algorithm 2) without their hashing,
+ * n_stores accesses of cell_bytes each to pseudo-random cells of the caller's device buffer
+ * dev_buf of `bytes` bytes (at least one cell, aligned to 4 bytes, to 8 for 8-byte cells):
+ * the access shape of the scan's recorder updates (Algorithm 2) without their hashing,
  * de-duplication or sampling.  All writes carry the same value, as all writers of a slice
- * write the same stamp.  policy: how a write is made,
- *   SRLA_PROBE_STORE       a plain store (the scan's choice);
+ * write the same stamp.  policy: how an access is made,
+ *   SRLA_PROBE_STORE       a plain store (the scan's choice; cell_bytes 1, 2 or 4);
  *   SRLA_PROBE_ATOMIC_MAX  an atomic maximum (native on 4-byte cells; on 1- and 2-byte
  *                          cells a compare-and-swap loop on the enclosing 32-bit word,
  *                          at most 64 tries; only the cells of whole words of the buffer
  *                          are used);
- *   SRLA_PROBE_READ_FIRST  a load through L2, then a store only if the cell differs.
+ *   SRLA_PROBE_READ_FIRST  a load through L2, then a store only if the cell differs;
+ *   SRLA_PROBE_CAS         a 64-bit compare-and-swap from the all-ones key (cell_bytes 8):
+ *                          the scan's claims in its table of scanned pairs;
+ *   SRLA_PROBE_LOAD        a plain load through L2 (cell_bytes 1, 2, 4 or 8): the scan's
+ *                          probes of its sampled-host set.
  * Time it with events on the same stream.  Overwrites the buffer.  Errors: INVAL, CUDA. */
 #define SRLA_PROBE_STORE 0u
 #define SRLA_PROBE_ATOMIC_MAX 1u
 #define SRLA_PROBE_READ_FIRST 2u
+#define SRLA_PROBE_CAS 3u
+#define SRLA_PROBE_LOAD 4u
 int srla_scatter_probe(void *dev_buf, size_t bytes, uint32_t cell_bytes, uint64_t n_stores, uint64_t seed,
                        uint32_t policy, void *stream);
 const char *srla_strerror(int code);
@@ -317,6 +352,13 @@ int srla_group_report(srla_group_t *g, uint32_t link, uint64_t group_slice, srla
  * (the trial scans repeat the slice's own idempotent recorder stores).  Errors: ORDER when
  * nothing was pushed, CUDA.                                                              */
 int srla_group_autotune(srla_group_t *g, int reps, uint32_t *best_threads, uint32_t *best_task_pkts);
+
+/* Checkpoint of one attached link at a slice boundary (no packets pushed in the open group
+ * slice, else SRLA_E_ORDER), in the format of srla_export_state: the recorder distances, the
+ * link's open slice and its carried hosts.  srla_group_state_bytes gives the buffer size (0
+ * for a free slot).  Synchronizes the group's stream.                                     */
+size_t srla_group_state_bytes(const srla_group_t *g, uint32_t link);
+int srla_group_export_state(srla_group_t *g, uint32_t link, void *host_buf, size_t cap);
 
 int srla_group_sync(srla_group_t *g);
 uint64_t srla_group_kernel_launches(const srla_group_t *g);
@@ -388,6 +430,11 @@ int srla_server_poll(srla_server_t *s, uint64_t slice, srla_server_result *resul
 
 /* Bytes of the budget in use by admitted links (driver thread). */
 uint64_t srla_server_used_bytes(const srla_server_t *s);
+
+/* Checkpoint of an admitted link between ticks (driver thread), as srla_group_export_state;
+ * SRLA_E_ORDER when the key is not admitted.  srla_server_state_bytes is 0 for such a key. */
+size_t srla_server_state_bytes(srla_server_t *s, uint64_t key);
+int srla_server_export_state(srla_server_t *s, uint64_t key, void *host_buf, size_t cap);
 void srla_server_destroy(srla_server_t *s);
 
 #ifdef __cplusplus

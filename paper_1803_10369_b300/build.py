@@ -1,9 +1,14 @@
-"""Build libsrla.so for sm_103a with nvcc (in-tree, under _build/)."""
+"""Build libsrla.so for sm_103a with nvcc (in-tree, under _build/).
+
+Each .cu of csrc/ is compiled to an object in parallel, then the objects are linked into one
+shared library.
+"""
 from __future__ import annotations
 
 import glob
 import os
 import subprocess
+from concurrent.futures import ThreadPoolExecutor
 
 PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
@@ -15,14 +20,14 @@ LIB = os.path.join(OUT_DIR, "libsrla.so")
 NVCC_FLAGS = [
     "-O3", "-std=c++17", "-lineinfo",
     "-gencode", "arch=compute_103a,code=sm_103a",
-    "-Xcompiler", "-fPIC", "-shared",
+    "-Xcompiler", "-fPIC",
     "--expt-relaxed-constexpr",
 ]
 
 
 def _sources():
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu"))) + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + [
-        os.path.join(INCLUDE, "srla.h")]
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu"))) + sorted(glob.glob(os.path.join(CSRC, "*.cuh"))) + sorted(
+        glob.glob(os.path.join(CSRC, "*.h"))) + [os.path.join(INCLUDE, "srla.h")]
 
 
 def needs_build() -> bool:
@@ -40,17 +45,41 @@ def nvcc() -> str:
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    """Compile every .cu of csrc/ into one shared library; returns its path."""
+    """Compile every .cu of csrc/ and link them into one shared library; returns its path."""
     if not force and not needs_build():
         return LIB
     os.makedirs(OUT_DIR, exist_ok=True)
-    tmp = f"{LIB}.{os.getpid()}.tmp"
+    tag = f"{os.getpid()}"
     cus = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
-    cmd = [nvcc(), *NVCC_FLAGS, *extra, "-I", INCLUDE, "-I", CSRC, "-o", tmp, *cus]
-    if verbose:
-        print(" ".join(cmd))
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB)
+    objs = [os.path.join(OUT_DIR, os.path.basename(c)[:-3] + f".{tag}.o") for c in cus]
+
+    def compile_one(src_obj):
+        src, obj = src_obj
+        cmd = [nvcc(), *NVCC_FLAGS, *extra, "-I", INCLUDE, "-I", CSRC, "-c", "-o", obj, src]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        return subprocess.run(cmd, capture_output=True, text=True)
+
+    try:
+        with ThreadPoolExecutor(max_workers=max(1, len(cus))) as ex:
+            results = list(ex.map(compile_one, zip(cus, objs)))
+        for r in results:
+            if r.stdout:
+                print(r.stdout, end="")
+            if r.stderr:
+                print(r.stderr, end="")
+        for r in results:
+            r.check_returncode()
+        tmp = f"{LIB}.{tag}.tmp"
+        link = [nvcc(), "-shared", "-gencode", "arch=compute_103a,code=sm_103a", "-o", tmp, *objs]
+        if verbose:
+            print(" ".join(link), flush=True)
+        subprocess.run(link, check=True)
+        os.replace(tmp, LIB)
+    finally:
+        for o in objs:
+            if os.path.exists(o):
+                os.remove(o)
     return LIB
 
 

@@ -53,11 +53,19 @@ struct Ctl {
   unsigned int bar_count;         // grid barrier of the cooperative sort: arrivals
   unsigned int bar_gen;           // grid barrier of the cooperative sort: generation
   unsigned int pair_mode;         // 1: the scan consults the per-slice pair table
-  unsigned int n_miss;            // packets of the open slice that missed their block's table
+  unsigned int n_miss;            // block-table misses of the open slice that claimed a pair-table slot
   unsigned int n_gdup;            // of which the per-slice pair table found already scanned
   unsigned int pad2;
   double up;                      // UP of Eq. 8 for the open slice (set at its end)
+  unsigned long long n_scan;      // pairs of the open slice scanned (their SLE recorders set)
+  unsigned long long n_scan_samp; // of which sampled (their SRE recorders set too)
+  unsigned long long n_probe;     // sampled-host set insertions tried (one probe load each)
   unsigned long long census[SRLA_MAX_ROWS];
+};
+
+// Per-thread scan counters, added to the control block once per block.
+struct ScanCount {
+  uint32_t miss, gdup, scan, samp, probe;
 };
 
 // ---------------------------------------------------------------------------- hashing

@@ -90,7 +90,7 @@ __device__ __forceinline__ void with_cells(uint32_t cell_bytes, F&& f) {
 template <typename CellT, bool kVec>
 __device__ __forceinline__ void group_scan_task(const ScanTask& t, const LinkDesc& D, Ctl* ctl,
                                                 volatile unsigned long long* seen, ScanQueues& Q, int lane, int warp,
-                                                int nwarps, uint32_t& n_miss, uint32_t& n_gdup) {
+                                                int nwarps, ScanCount& sc) {
   const uint32_t* pairs = reinterpret_cast<const uint32_t*>(t.ptr);
   const uint64_t n = t.n;
   CellT* re = static_cast<CellT*>(D.re);
@@ -119,21 +119,21 @@ __device__ __forceinline__ void group_scan_task(const ScanTask& t, const LinkDes
         queue_push(Q.q1, Q.n1, miss && key != kNoPair, key, lane);
         queue_push(Q.q2, Q.n2, miss && key == kNoPair, key, lane);
         if (Q.n2 >= 32)
-          drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag, lane);
+          drain_scan<CellT>(Q, sc, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag, lane);
         if (Q.n1 >= 32)
-          drain_claim<CellT>(Q, ptab, D.pmask, n_miss, n_gdup, geo, coef, code, re, le, ctl, D.utab, D.umask,
-                             D.ulist, D.umax, tag, lane);
+          drain_claim<CellT>(Q, sc, ptab, D.pmask, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag,
+                             lane);
       } else {
         queue_push(Q.q2, Q.n2, miss, key, lane);
         if (Q.n2 >= 32)
-          drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag, lane);
+          drain_scan<CellT>(Q, sc, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag, lane);
       }
     }
   }
   if (ptab && Q.n1)
-    drain_claim<CellT>(Q, ptab, D.pmask, n_miss, n_gdup, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist,
-                       D.umax, tag, lane);
-  while (Q.n2) drain_scan<CellT>(Q, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag, lane);
+    drain_claim<CellT>(Q, sc, ptab, D.pmask, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag,
+                       lane);
+  while (Q.n2) drain_scan<CellT>(Q, sc, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag, lane);
 }
 
 // Persistent blocks take scan tasks one at a time; a task is one link's batch, so the block's
@@ -146,15 +146,12 @@ __global__ void __launch_bounds__(kThreads) kg_scan(const LinkDesc* __restrict__
   __shared__ unsigned long long queue_mem[kThreads / 32][2][kQueue];
   __shared__ LinkDesc sdesc;
   __shared__ ScanTask stask;
-  __shared__ unsigned s_task, s_miss, s_gdup;
+  __shared__ unsigned s_task;
   volatile unsigned long long* seen = seen_mem;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned n_tasks = thdr->n_tasks;
   for (;;) {
-    if (threadIdx.x == 0) {
-      s_task = atomicAdd(&gctl->next_task, 1u);
-      s_miss = s_gdup = 0;
-    }
+    if (threadIdx.x == 0) s_task = atomicAdd(&gctl->next_task, 1u);
     __syncthreads();
     const unsigned ti = s_task;
     if (ti >= n_tasks) break;
@@ -168,27 +165,17 @@ __global__ void __launch_bounds__(kThreads) kg_scan(const LinkDesc* __restrict__
     for (int x = threadIdx.x; x < (1 << kGroupSeenLog2); x += kThreads) seen[x] = kNoPair;
     __syncthreads();
     ScanQueues Q{queue_mem[warp][0], queue_mem[warp][1], 0u, 0u};
-    uint32_t n_miss = 0, n_gdup = 0;
+    ScanCount sc{0u, 0u, 0u, 0u, 0u};
     const bool vec = (stask.ptr & 15ull) == 0;
     Ctl* ctl = sdesc.ctl;
     with_cells(sdesc.cell_bytes, [&](auto cell) {
       using CellT = decltype(cell);
       if (vec)
-        group_scan_task<CellT, true>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, n_miss, n_gdup);
+        group_scan_task<CellT, true>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, sc);
       else
-        group_scan_task<CellT, false>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, n_miss, n_gdup);
+        group_scan_task<CellT, false>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, sc);
     });
-    n_miss = warp_sum(n_miss);
-    n_gdup = warp_sum(n_gdup);
-    if (lane == 0 && (n_miss | n_gdup)) {
-      atomicAdd(&s_miss, n_miss);
-      atomicAdd(&s_gdup, n_gdup);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && (s_miss | s_gdup)) {
-      atomicAdd(&ctl->n_miss, s_miss);
-      atomicAdd(&ctl->n_gdup, s_gdup);
-    }
+    scan_count_flush(sc, ctl, lane);
     __syncthreads();
   }
 }

@@ -18,6 +18,20 @@ inline constexpr uint32_t kStateVersion = 1;
 
 inline size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
 
+// Header of an exported state (single links and group links): the geometry, the open slice
+// and the number of carried hosts, followed by the SRE distances (u*v*g uint16), the SLE
+// distances (u*v*gl uint16) and the carried hosts (n_carry uint32, ascending).
+struct StateHeader {
+  uint32_t magic, version;
+  uint32_t u, v, g, gl, dr_bytes, z, k, theta;
+  uint64_t slice;
+  uint32_t n_carry, pad;
+};
+
+inline size_t state_bytes_of(const srla_params* p, uint32_t n_carry) {
+  return sizeof(StateHeader) + (size_t)p->u * p->v * (p->g + p->gl) * 2 + (size_t)n_carry * 4;
+}
+
 inline bool pow2(uint64_t x) { return x && !(x & (x - 1)); }
 
 inline uint64_t next_pow2(uint64_t x) {

@@ -45,7 +45,7 @@ __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, k
   uint64_t base = gw * 128;
   uint32_t a[4], b[4];
   bool ok[4];
-  uint32_t n_miss = 0, n_gdup = 0;
+  ScanCount sc{0u, 0u, 0u, 0u, 0u};
   load_pairs<kVec>(pairs, n, base, lane, a, b, ok);
   while (base < n) {
     const uint64_t next = base + nw * 128;
@@ -70,15 +70,15 @@ __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, k
         queue_push(Q.q1, Q.n1, miss && key != kNoPair, key, lane);
         queue_push(Q.q2, Q.n2, miss && key == kNoPair, key, lane);
         if (Q.n2 >= 32)
-          drain_scan<CellT, false, kElide>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+          drain_scan<CellT, false, kElide>(Q, sc, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
         if (Q.n1 >= 32)
-          drain_claim<CellT, kElide>(Q, ptab, pmask, n_miss, n_gdup, geo, coef, code, re, le, ctl, utab, umask, ulist,
-                                     umax, tag, lane);
+          drain_claim<CellT, kElide>(Q, sc, ptab, pmask, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag,
+                                     lane);
       } else {
         queue_push(Q.q2, Q.n2, miss, key, lane);
         if (Q.n2 >= 32)
-          drain_scan<CellT, kInline, kElide>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, &ia,
-                                             &win);
+          drain_scan<CellT, kInline, kElide>(Q, sc, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane,
+                                             &ia, &win);
       }
     }
 #pragma unroll
@@ -89,27 +89,11 @@ __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, k
   }
   // what is left in the queues
   if (ptab && Q.n1)
-    drain_claim<CellT, kElide>(Q, ptab, pmask, n_miss, n_gdup, geo, coef, code, re, le, ctl, utab, umask, ulist, umax,
-                               tag, lane);
+    drain_claim<CellT, kElide>(Q, sc, ptab, pmask, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
   while (Q.n2)
-    drain_scan<CellT, kInline, kElide>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, &ia,
+    drain_scan<CellT, kInline, kElide>(Q, sc, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, &ia,
                                        &win);
-  if (ptab) {  // one global update per block
-    __shared__ unsigned s_miss, s_gdup;
-    if (threadIdx.x == 0) s_miss = s_gdup = 0;
-    __syncthreads();
-    n_miss = warp_sum(n_miss);
-    n_gdup = warp_sum(n_gdup);
-    if (lane == 0) {
-      atomicAdd(&s_miss, n_miss);
-      atomicAdd(&s_gdup, n_gdup);
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      atomicAdd(&ctl->n_miss, s_miss);
-      atomicAdd(&ctl->n_gdup, s_gdup);
-    }
-  }
+  scan_count_flush(sc, ctl, lane);
 }
 
 // One streaming pass over the recorders: census and stamp ageing.  Each block sweeps one
@@ -378,22 +362,6 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
   close_slice(geo, ctl, par ? st1 : st0, umax, cmax);
 }
 
-// Recorder stamps -> the paper's distances (2^z - 1 = empty), at the open slice.
-template <typename CellT>
-__global__ void k_decode(const CellT* __restrict__ cells, uint16_t* __restrict__ out, size_t n,
-                         const Ctl* __restrict__ ctl, uint32_t P) {
-  const uint32_t tm = ctl->tm;
-  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
-    if constexpr (kIsBit<CellT>) {
-      const uint32_t word = reinterpret_cast<const uint32_t*>(cells)[x >> 5];
-      out[x] = (uint16_t)(((word >> (x & 31u)) & 1u) ? 0u : P);
-    } else {
-      const uint32_t c = cells[x];
-      out[x] = (uint16_t)(c == 0 ? P : stamp_age(c, tm, P));
-    }
-  }
-}
-
 // Distances -> stamps at open slice with T mod P = tm (one-bit recorders: 32 per thread).
 template <typename CellT>
 __global__ void k_encode(const uint16_t* __restrict__ d, CellT* __restrict__ cells, size_t n, uint32_t tm,
@@ -457,8 +425,13 @@ __global__ void k_insert_carried(const uint32_t* __restrict__ hosts, uint32_t n,
 //   1  an atomic maximum: native on 32-bit cells; on 8- and 16-bit cells, which have no
 //      atomic maximum, a compare-and-swap loop on the enclosing 32-bit word (at most 64
 //      tries, so contention can only slow it down);
-//   2  read before write: a load through L2, and a store only if the cell differs.
-enum : uint32_t { kProbeStore = 0, kProbeAtomicMax = 1, kProbeReadFirst = 2 };
+//   2  read before write: a load through L2, and a store only if the cell differs;
+//   3  a compare-and-swap of a 64-bit slot from the empty key (all ones) to the value: the
+//      claim of the scan's pair table (after the first claim of a slot the swap fails, which
+//      is the same round trip);
+//   4  a plain load through L2 (the probes of the sampled-host set), folded into a register
+//      that is stored only if it equals a value no load returns.
+enum : uint32_t { kProbeStore = 0, kProbeAtomicMax = 1, kProbeReadFirst = 2, kProbeCas = 3, kProbeLoad = 4 };
 
 template <typename CellT>
 __device__ __forceinline__ void probe_atomic_max(CellT* p, CellT val) {
@@ -482,6 +455,7 @@ template <typename CellT, uint32_t kPolicy>
 __global__ void __launch_bounds__(256) k_scatter_probe(CellT* __restrict__ buf, uint64_t cells, uint64_t n,
                                                        uint64_t seed) {
   const CellT val = (CellT)(seed | 1u);
+  CellT acc = 0;
   for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x) {
     uint64_t z = i + seed * 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -492,10 +466,20 @@ __global__ void __launch_bounds__(256) k_scatter_probe(CellT* __restrict__ buf, 
       *p = val;
     } else if constexpr (kPolicy == kProbeAtomicMax) {
       probe_atomic_max<CellT>(p, val);
-    } else {
+    } else if constexpr (kPolicy == kProbeReadFirst) {
       if (__ldcg(p) != val) *p = val;
+    } else if constexpr (kPolicy == kProbeCas) {
+      static_assert(sizeof(CellT) == 8, "the claim probe swaps 64-bit slots");
+      acc ^= (CellT)atomicCAS(reinterpret_cast<unsigned long long*>(p), ~0ull, (unsigned long long)val);
+    } else {
+      acc ^= __ldcg(p);
     }
   }
+  // loads and swaps must not be optimised away: their folded results feed a store, taken
+  // only in the rare case that they equal one fixed pattern (it writes one cell of the
+  // caller's scratch buffer)
+  if constexpr (kPolicy == kProbeCas || kPolicy == kProbeLoad)
+    if (acc == (CellT)0x5A5A5A5A5A5A5A5Bull) buf[0] = acc;
 }
 
 }  // namespace srla

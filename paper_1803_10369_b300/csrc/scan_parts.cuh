@@ -67,7 +67,7 @@ __device__ __forceinline__ unsigned scan_dense(uint32_t aip, uint32_t bip, bool 
                                            CellT code, CellT* __restrict__ re, CellT* __restrict__ le,
                                            Ctl* __restrict__ ctl, unsigned long long* __restrict__ utab,
                                            uint32_t umask, uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag,
-                                           int lane) {
+                                           int lane, uint32_t& n_probe) {
   const uint32_t u = geo.u;
   bool samp = false;
   if (ok) {
@@ -106,9 +106,14 @@ __device__ __forceinline__ unsigned scan_dense(uint32_t aip, uint32_t bip, bool 
       }
     } else if constexpr (kElide) {
       // Four rows at a time, their cells read first; a cell already holding the slice's
-      // stamp is not written again (only this slice's writers store that stamp, so an equal
-      // value, even from this SM's L1, is current).  Chosen when most pairs are new (the pair
-      // table is off): then a good share of the stores would repeat a stamp already there.
+      // stamp 1 + (T mod P) is not written again.  That skip is exact because no cell holds
+      // this code when slice T opens: the sweep of the transition into T (the ageing step of
+      // Algorithm 3) clears every cell whose code is 1 + (T mod P) (the cells whose distance
+      // reaches 2^z - 1), before the census when k < P and after the close when k = P.  So
+      // every cell with that code was stamped in slice T by one of its writers, and an equal
+      // value, even a stale one from this SM's L1, is current.  Chosen when most pairs are
+      // new (the pair table is off): then a good share of the stores would repeat a stamp
+      // already there.
       for (uint32_t i0 = 0; i0 < u; i0 += 4) {
         size_t xl[4], xr[4];
         CellT hl[4], hr[4];
@@ -145,6 +150,7 @@ __device__ __forceinline__ unsigned scan_dense(uint32_t aip, uint32_t bip, bool 
     const unsigned peers = __match_any_sync(sm, aip);
     if ((peers & ((1u << lane) - 1u)) == 0) {
       uint32_t slot;
+      n_probe++;
       r = set_insert(utab, umask, tag, aip, &slot);
       if (r < 0) atomicOr(&ctl->overflow, 1u);
     }
@@ -270,26 +276,27 @@ __device__ __forceinline__ bool queue_take(volatile unsigned long long* q, uint3
 }
 
 template <typename CellT, bool kInline = false, bool kElide = false>
-__device__ __forceinline__ void drain_scan(ScanQueues& Q, const Geo& geo, const Coef& coef, CellT code,
-                                           CellT* __restrict__ re, CellT* __restrict__ le, Ctl* __restrict__ ctl,
-                                           unsigned long long* __restrict__ utab, uint32_t umask,
-                                           uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag, int lane,
-                                           const InlineArgs* ia = nullptr, const Win* win = nullptr) {
+__device__ __forceinline__ void drain_scan(ScanQueues& Q, ScanCount& sc, const Geo& geo, const Coef& coef,
+                                           CellT code, CellT* __restrict__ re, CellT* __restrict__ le,
+                                           Ctl* __restrict__ ctl, unsigned long long* __restrict__ utab,
+                                           uint32_t umask, uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag,
+                                           int lane, const InlineArgs* ia = nullptr, const Win* win = nullptr) {
   unsigned long long key;
   const bool ok = queue_take(Q.q2, Q.n2, lane, key);
   const uint32_t aip = (uint32_t)(key >> 32);
   const unsigned sm = scan_dense<CellT, kInline, kElide>(aip, (uint32_t)key, ok, geo, coef, code, re, le, ctl, utab,
-                                                         umask, ulist, umax, tag, lane);
+                                                         umask, ulist, umax, tag, lane, sc.probe);
+  sc.scan += ok ? 1u : 0u;
+  sc.samp += (sm >> lane) & 1u;
   if constexpr (kInline) inline_test<CellT>(sm, aip, geo, coef, re, *win, ctl, *ia, lane);
 }
 
 template <typename CellT, bool kElide = false>
-__device__ __forceinline__ void drain_claim(ScanQueues& Q, unsigned long long* __restrict__ ptab, uint32_t pmask,
-                                            uint32_t& n_miss, uint32_t& n_gdup, const Geo& geo, const Coef& coef,
-                                            CellT code, CellT* __restrict__ re, CellT* __restrict__ le,
-                                            Ctl* __restrict__ ctl, unsigned long long* __restrict__ utab,
-                                            uint32_t umask, uint32_t* __restrict__ ulist, uint32_t umax,
-                                            uint32_t tag, int lane) {
+__device__ __forceinline__ void drain_claim(ScanQueues& Q, ScanCount& sc, unsigned long long* __restrict__ ptab,
+                                            uint32_t pmask, const Geo& geo, const Coef& coef, CellT code,
+                                            CellT* __restrict__ re, CellT* __restrict__ le, Ctl* __restrict__ ctl,
+                                            unsigned long long* __restrict__ utab, uint32_t umask,
+                                            uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag, int lane) {
   unsigned long long key;
   const bool ok = queue_take(Q.q1, Q.n1, lane, key);
   bool scan = false;
@@ -299,12 +306,36 @@ __device__ __forceinline__ void drain_claim(ScanQueues& Q, unsigned long long* _
     bool dup = old == key;
     if (old != kNoPair && !dup) dup = !pair_claim_from(ptab, pmask, key, (home + 1) & pmask);
     scan = !dup;
-    n_miss += 1;
-    n_gdup += dup;
+    sc.miss += 1;
+    sc.gdup += dup;
   }
   queue_push(Q.q2, Q.n2, scan, key, lane);
   if (Q.n2 >= 32)
-    drain_scan<CellT, false, kElide>(Q, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+    drain_scan<CellT, false, kElide>(Q, sc, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+}
+
+// The block's scan counters into the control block: one reduction per block (all threads
+// of the block call it), one atomic per counter.
+__device__ __forceinline__ void scan_count_flush(ScanCount sc, Ctl* __restrict__ ctl, int lane) {
+  __shared__ unsigned s_cnt[5];
+  __syncthreads();
+  if (threadIdx.x < 5) s_cnt[threadIdx.x] = 0;
+  __syncthreads();
+  const uint32_t v[5] = {warp_sum(sc.miss), warp_sum(sc.gdup), warp_sum(sc.scan), warp_sum(sc.samp),
+                         warp_sum(sc.probe)};
+  if (lane == 0) {
+#pragma unroll
+    for (int i = 0; i < 5; i++)
+      if (v[i]) atomicAdd(&s_cnt[i], v[i]);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (s_cnt[0]) atomicAdd(&ctl->n_miss, s_cnt[0]);
+    if (s_cnt[1]) atomicAdd(&ctl->n_gdup, s_cnt[1]);
+    if (s_cnt[2]) atomicAdd(&ctl->n_scan, (unsigned long long)s_cnt[2]);
+    if (s_cnt[3]) atomicAdd(&ctl->n_scan_samp, (unsigned long long)s_cnt[3]);
+    if (s_cnt[4]) atomicAdd(&ctl->n_probe, (unsigned long long)s_cnt[4]);
+  }
 }
 
 template <bool kVec>
@@ -428,6 +459,25 @@ __device__ __forceinline__ uint32_t sweep_part(uint4* base, size_t nvec, size_t 
   return cnt;
 }
 
+// ---------------------------------------------------------------- state export
+//
+// Recorder stamps -> the paper's distances (2^z - 1 = empty), at the open slice: the
+// checkpoint form of the recorders (single links and group links).
+template <typename CellT>
+__global__ void k_decode(const CellT* __restrict__ cells, uint16_t* __restrict__ out, size_t n,
+                         const Ctl* __restrict__ ctl, uint32_t P) {
+  const uint32_t tm = ctl->tm;
+  for (size_t x = (size_t)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (size_t)gridDim.x * blockDim.x) {
+    if constexpr (kIsBit<CellT>) {
+      const uint32_t word = reinterpret_cast<const uint32_t*>(cells)[x >> 5];
+      out[x] = (uint16_t)(((word >> (x & 31u)) & 1u) ? 0u : P);
+    } else {
+      const uint32_t c = cells[x];
+      out[x] = (uint16_t)(c == 0 ? P : stamp_age(c, tm, P));
+    }
+  }
+}
+
 // ------------------------------------------------------------- Eq. 8 and Eq. 9 (b2)
 //
 // UP = prod_i |LDR(i)|^k / (g' v) from the row census, and Eq. 9 for a union weight w, both
@@ -500,6 +550,13 @@ __device__ __forceinline__ void close_slice(const Geo& geo, Ctl* __restrict__ ct
   s.w_star = min(c.w_star, geo.gl + 1u);
   s.overflow = c.overflow;
   s.up = c.up;
+  s.pair_table = c.pair_mode;
+  s.pad = 0;
+  s.n_claims = c.n_miss;
+  s.n_claim_repeats = c.n_gdup;
+  s.n_scanned = c.n_scan;
+  s.n_scanned_sampled = c.n_scan_samp;
+  s.n_set_probes = c.n_probe;
   Ctl n = c;
   for (int i = 0; i < SRLA_MAX_ROWS; i++) {
     s.census[i] = c.census[i];
@@ -521,6 +578,9 @@ __device__ __forceinline__ void close_slice(const Geo& geo, Ctl* __restrict__ ct
   n.pair_mode = (measured ? worth : false) || ((T + 1) % 16 == 0) ? 1u : 0u;
   n.n_miss = 0;
   n.n_gdup = 0;
+  n.n_scan = 0;
+  n.n_scan_samp = 0;
+  n.n_probe = 0;
   *ctl = n;
   __threadfence();
 }

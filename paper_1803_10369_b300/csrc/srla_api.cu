@@ -19,17 +19,6 @@
 using namespace srla;
 using namespace srla::host;
 
-namespace {
-
-struct StateHeader {
-  uint32_t magic, version;
-  uint32_t u, v, g, gl, dr_bytes, z, k, theta;
-  uint64_t slice;
-  uint32_t n_carry, pad;
-};
-
-}  // namespace
-
 struct srla_s {
   srla_params p;
   Geo geo;
@@ -52,6 +41,8 @@ struct srla_s {
   uint64_t n_pkts_open;   // packets pushed into the open slice
   uint64_t staging_used;  // staging packets used in the open slice
   uint64_t launches;      // kernels launched so far
+  uint32_t scan_build;    // SRLA_SCAN_AUTO, SRLA_SCAN_PLAIN or SRLA_SCAN_READ_FIRST
+  uint64_t scans[2];      // scan launches of the plain build and of the read-first build
   int occ_scan[2];        // resident scan blocks per SM (unaligned, aligned batches)
   int occ_sweep;          // resident sweep blocks per SM
   int sort_grid;          // blocks of the cooperative sort
@@ -141,7 +132,9 @@ bool read_first_hint(const srla_t* h) {
 template <typename CellT>
 int launch_scan(srla_t* h, const uint32_t* pairs, uint64_t n) {
   const bool vec = (reinterpret_cast<uintptr_t>(pairs) & 15u) == 0;
-  const bool elide = !kIsBit<CellT> && !inline_mode(h) && read_first_hint(h);
+  const bool elide = !kIsBit<CellT> && !inline_mode(h) &&
+                     (h->scan_build == SRLA_SCAN_READ_FIRST || (h->scan_build == SRLA_SCAN_AUTO && read_first_hint(h)));
+  h->scans[elide ? 1 : 0]++;
   auto kern = inline_mode(h) ? (vec ? k_scan<CellT, true, true> : k_scan<CellT, false, true>)
               : elide        ? (vec ? k_scan<CellT, true, false, true> : k_scan<CellT, false, false, true>)
                              : (vec ? k_scan<CellT, true> : k_scan<CellT, false>);
@@ -595,8 +588,7 @@ int srla_sync(srla_t* h) {
 
 size_t srla_state_bytes(const srla_t* h) {
   if (!h) return 0;
-  const srla_params& p = h->p;
-  return sizeof(StateHeader) + (size_t)p.u * p.v * (p.g + p.gl) * 2 + (size_t)p.max_candidates * 4;
+  return state_bytes_of(&h->p, h->p.max_candidates);
 }
 
 }  // extern "C"
@@ -713,6 +705,21 @@ int srla_import_state(srla_t* h, const void* host_buf, size_t len) {
 
 uint64_t srla_kernel_launches(const srla_t* h) { return h ? h->launches : 0; }
 
+int srla_set_scan_build(srla_t* h, uint32_t build) {
+  if (!h || build > SRLA_SCAN_READ_FIRST) return SRLA_E_INVAL;
+  // the read-first build exists for 8- and 16-bit recorders under the order-free rule
+  if (build == SRLA_SCAN_READ_FIRST && (h->p.dr_bytes == 0 || inline_mode(h))) return SRLA_E_INVAL;
+  h->scan_build = build;
+  return SRLA_OK;
+}
+
+int srla_scan_builds(const srla_t* h, uint64_t* plain, uint64_t* read_first) {
+  if (!h) return SRLA_E_INVAL;
+  if (plain) *plain = h->scans[0];
+  if (read_first) *read_first = h->scans[1];
+  return SRLA_OK;
+}
+
 int srla_uses_graph(const srla_t* h) { return h && h->graph[0] && h->graph[1] ? 1 : 0; }
 
 void srla_destroy(srla_t* h) {
@@ -759,9 +766,9 @@ const char* srla_strerror(int code) {
 // ------------------------------------------------------ allocation-free batch report
 //
 // Some callers cannot allocate device memory at all: a capture thread with real-time
-// deadlines (cudaMalloc and cudaFree may synchronize the whole device), a plugin whose host
-// framework owns every device buffer and hands out only fixed input/output slots, or code
-// that runs while a stream is being captured.  For them, srla_batch_report_static runs the
+// deadlines (cudaMalloc and cudaFree may synchronize the whole device), or a plugin whose
+// host framework owns every device buffer and hands out only fixed input/output slots.  For
+// them, srla_batch_report_static runs the
 // scan and the slice end of a fresh estimator over one device batch with its workspace
 // carved out of a fixed scratch array compiled into this library, instead of a caller
 // workspace.  Every GPU that loads the library holds the array until the process exits.
@@ -886,19 +893,33 @@ template <typename CellT>
 static void launch_probe(uint32_t policy, int grid, cudaStream_t st, void* buf, uint64_t cells, uint64_t n,
                          uint64_t seed) {
   CellT* b = static_cast<CellT*>(buf);
-  if (policy == kProbeStore)
-    k_scatter_probe<CellT, kProbeStore><<<grid, 256, 0, st>>>(b, cells, n, seed);
-  else if (policy == kProbeAtomicMax)
-    k_scatter_probe<CellT, kProbeAtomicMax><<<grid, 256, 0, st>>>(b, cells, n, seed);
-  else
-    k_scatter_probe<CellT, kProbeReadFirst><<<grid, 256, 0, st>>>(b, cells, n, seed);
+  if constexpr (sizeof(CellT) == 8) {
+    if (policy == kProbeCas)
+      k_scatter_probe<CellT, kProbeCas><<<grid, 256, 0, st>>>(b, cells, n, seed);
+    else
+      k_scatter_probe<CellT, kProbeLoad><<<grid, 256, 0, st>>>(b, cells, n, seed);
+  } else {
+    if (policy == kProbeStore)
+      k_scatter_probe<CellT, kProbeStore><<<grid, 256, 0, st>>>(b, cells, n, seed);
+    else if (policy == kProbeAtomicMax)
+      k_scatter_probe<CellT, kProbeAtomicMax><<<grid, 256, 0, st>>>(b, cells, n, seed);
+    else if (policy == kProbeReadFirst)
+      k_scatter_probe<CellT, kProbeReadFirst><<<grid, 256, 0, st>>>(b, cells, n, seed);
+    else
+      k_scatter_probe<CellT, kProbeLoad><<<grid, 256, 0, st>>>(b, cells, n, seed);
+  }
 }
 
 extern "C" int srla_scatter_probe(void* dev_buf, size_t bytes, uint32_t cell_bytes, uint64_t n_stores, uint64_t seed,
                                   uint32_t policy, void* stream) {
-  if (!dev_buf || (cell_bytes != 1 && cell_bytes != 2 && cell_bytes != 4) || policy > kProbeReadFirst)
-    return SRLA_E_INVAL;
-  if (reinterpret_cast<uintptr_t>(dev_buf) & 3u) return SRLA_E_INVAL;  // word-aligned for the CAS loop
+  if (!dev_buf || policy > kProbeLoad) return SRLA_E_INVAL;
+  // 1-, 2- and 4-byte cells for stores, maxima and read-first writes; 8-byte slots for the
+  // compare-and-swap; any of them for loads
+  const bool cell_ok = policy == kProbeCas    ? cell_bytes == 8
+                       : policy == kProbeLoad ? (cell_bytes == 1 || cell_bytes == 2 || cell_bytes == 4 || cell_bytes == 8)
+                                              : (cell_bytes == 1 || cell_bytes == 2 || cell_bytes == 4);
+  if (!cell_ok) return SRLA_E_INVAL;
+  if (reinterpret_cast<uintptr_t>(dev_buf) & (cell_bytes == 8 ? 7u : 3u)) return SRLA_E_INVAL;  // word-aligned
   // the CAS loop of the atomic maximum reads and writes whole 32-bit words: only cells of
   // whole words of the buffer are used
   const uint64_t cells = (policy == kProbeAtomicMax ? bytes & ~(size_t)3 : bytes) / cell_bytes;
@@ -912,7 +933,9 @@ extern "C" int srla_scatter_probe(void* dev_buf, size_t bytes, uint32_t cell_byt
     launch_probe<uint8_t>(policy, grid, st, dev_buf, cells, n_stores, seed);
   else if (cell_bytes == 2)
     launch_probe<uint16_t>(policy, grid, st, dev_buf, cells, n_stores, seed);
-  else
+  else if (cell_bytes == 4)
     launch_probe<uint32_t>(policy, grid, st, dev_buf, cells, n_stores, seed);
+  else
+    launch_probe<unsigned long long>(policy, grid, st, dev_buf, cells, n_stores, seed);
   return cuda_err(cudaGetLastError());
 }

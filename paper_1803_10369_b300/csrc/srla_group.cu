@@ -38,8 +38,11 @@ uint64_t max_tasks_for(uint32_t max_links, uint64_t max_pkts) {
   return max_pkts / kMinTaskPkts + 8ull * max_links + 64;
 }
 
+// Recorders decoded per step of a state export (through the fixed part's export area).
+constexpr size_t kExportChunk = (size_t)1 << 21;
+
 struct Fixed {
-  size_t gctl, descs, tasks, filt_off, gstats[2], rep_off[2], grep[2], stage[2], total;
+  size_t gctl, descs, tasks, filt_off, gstats[2], rep_off[2], grep[2], stage[2], xstage, total;
   uint64_t max_tasks;
 };
 
@@ -62,6 +65,7 @@ Fixed fixed_layout(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_pkts
     F.grep[q] = take(sizeof(srla_entry) * (size_t)max_report);
     F.stage[q] = take(8 * (size_t)max_host_pkts);
   }
+  F.xstage = take(kExportChunk * sizeof(uint16_t));
   F.total = off;
   return F;
 }
@@ -718,10 +722,16 @@ int srla_group_autotune(srla_group_t* g, int reps, uint32_t* best_threads, uint3
       best = c;
     }
   }
-  // the slice end starts from empty pair tables and a zero task counter, as without tuning
-  for (const Slot& s : g->slots)
-    if (s.active && s.L.pairs)
+  // the slice end starts from empty pair tables, zero scan counters and a zero task counter,
+  // as without tuning
+  for (const Slot& s : g->slots) {
+    if (!s.active) continue;
+    if (s.L.pairs)
       r = r ? r : gerr(cudaMemsetAsync(g->ws + s.off + s.L.ptab[0], 0xFF, ((size_t)s.L.pmask + 1) * 8, g->st));
+    char* c = g->ws + s.off + s.L.ctl;
+    r = r ? r : gerr(cudaMemsetAsync(c + offsetof(Ctl, n_miss), 0, 2 * sizeof(unsigned), g->st));
+    r = r ? r : gerr(cudaMemsetAsync(c + offsetof(Ctl, n_scan), 0, 3 * sizeof(unsigned long long), g->st));
+  }
   r = r ? r : gerr(cudaMemsetAsync(&g->gctl()->next_task, 0, sizeof(unsigned), g->st));
   g->scan_threads = threads[best / 3];
   g->task_pkts = tasks[best % 3];
@@ -735,6 +745,62 @@ int srla_group_autotune(srla_group_t* g, int reps, uint32_t* best_threads, uint3
   if (best_threads) *best_threads = (uint32_t)g->scan_threads;
   if (best_task_pkts) *best_task_pkts = g->task_pkts;
   return r;
+}
+
+size_t srla_group_state_bytes(const srla_group_t* g, uint32_t link) {
+  if (!g || link >= g->max_links || !g->slots[link].active) return 0;
+  return state_bytes_of(&g->slots[link].p, g->slots[link].p.max_candidates);
+}
+
+int srla_group_export_state(srla_group_t* g, uint32_t link, void* host_buf, size_t cap) {
+  if (!g || !host_buf || link >= g->max_links || !g->slots[link].active) return SRLA_E_INVAL;
+  if (!g->segments.empty()) return SRLA_E_ORDER;  // only at a slice boundary
+  const Slot& s = g->slots[link];
+  const srla_params& p = s.p;
+  char* base = g->ws + s.off;
+  G_TRY(cudaStreamSynchronize(g->st));
+  Ctl c;
+  G_TRY(cudaMemcpy(&c, base + s.L.ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+  const uint32_t nc = std::min<uint32_t>(c.cat_count[c.T & 1], p.max_candidates);
+  const size_t nre = (size_t)p.u * p.v * p.g, nle = (size_t)p.u * p.v * p.gl;
+  if (cap < state_bytes_of(&p, nc)) return SRLA_E_NOMEM;
+  StateHeader hd{kStateMagic, kStateVersion, p.u, p.v, p.g, p.gl, p.dr_bytes, p.z, p.k, p.theta, c.T, nc, 0};
+  char* b = static_cast<char*>(host_buf);
+  std::memcpy(b, &hd, sizeof(hd));
+  uint16_t* dst = reinterpret_cast<uint16_t*>(b + sizeof(hd));
+  uint16_t* stage = reinterpret_cast<uint16_t*>(g->ws + g->F.xstage);
+  const uint32_t P = (1u << p.z) - 1u;
+  const Ctl* dctl = reinterpret_cast<const Ctl*>(base + s.L.ctl);
+  // SRE then SLE, decoded to the paper's distances one chunk (a multiple of 32 recorders) at a time
+  const size_t arr_off[2] = {s.L.re, s.L.le}, arr_n[2] = {nre, nle};
+  for (int a = 0; a < 2; a++) {
+    for (size_t x = 0; x < arr_n[a]; x += kExportChunk) {
+      const size_t m = std::min(kExportChunk, arr_n[a] - x);
+      const int grid = (int)std::min<size_t>((m + 255) / 256, (size_t)g->sms * 8);
+      g->launches++;
+      auto run = [&](auto cell) {
+        using CellT = decltype(cell);
+        k_decode<CellT><<<grid, 256, 0, g->st>>>(cells_from(reinterpret_cast<CellT*>(base + arr_off[a]), x), stage,
+                                                  m, dctl, P);
+      };
+      if (p.dr_bytes == 1)
+        run(uint8_t{});
+      else if (p.dr_bytes == 2)
+        run(uint16_t{});
+      else
+        run(Bit{});
+      G_TRY(cudaGetLastError());
+      G_TRY(cudaMemcpyAsync(dst + x, stage, m * 2, cudaMemcpyDeviceToHost, g->st));
+      G_TRY(cudaStreamSynchronize(g->st));
+    }
+    dst += arr_n[a];
+  }
+  uint32_t* carry = reinterpret_cast<uint32_t*>(dst);
+  if (nc) {
+    G_TRY(cudaMemcpy(carry, base + s.L.clist[c.T & 1], (size_t)nc * 4, cudaMemcpyDeviceToHost));
+    std::sort(carry, carry + nc);
+  }
+  return SRLA_OK;
 }
 
 int srla_group_sync(srla_group_t* g) {

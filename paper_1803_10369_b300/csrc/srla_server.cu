@@ -260,6 +260,28 @@ int srla_server_poll(srla_server_t* s, uint64_t slice, srla_server_result* resul
 
 uint64_t srla_server_used_bytes(const srla_server_t* s) { return s ? s->used : 0; }
 
+// The state of an admitted link between ticks (driver thread): the group link's export.
+static int server_link(srla_server_t* s, uint64_t key, uint32_t* link) {
+  std::lock_guard<std::mutex> lock(s->mu);
+  const auto it = s->link_of.find(key);
+  if (it == s->link_of.end()) return SRLA_E_ORDER;
+  *link = it->second;
+  return SRLA_OK;
+}
+
+size_t srla_server_state_bytes(srla_server_t* s, uint64_t key) {
+  uint32_t link = 0;
+  if (!s || server_link(s, key, &link) != SRLA_OK) return 0;
+  return srla_group_state_bytes(s->g, link);
+}
+
+int srla_server_export_state(srla_server_t* s, uint64_t key, void* host_buf, size_t cap) {
+  if (!s || !host_buf) return SRLA_E_INVAL;
+  uint32_t link = 0;
+  const int r = server_link(s, key, &link);
+  return r != SRLA_OK ? r : srla_group_export_state(s->g, link, host_buf, cap);
+}
+
 void srla_server_destroy(srla_server_t* s) {
   if (!s) return;
   srla_group_destroy(s->g);

@@ -19,6 +19,7 @@ N_HASH = MAX_ROWS + 3
 OK, E_INVAL, E_NOMEM, E_CAPACITY, E_CUDA, E_ORDER, E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 SUPER, SATURATED, CARRIED, NEW = 1, 2, 4, 8
 MODE_ORDER_FREE, MODE_INLINE = 0, 1
+SCAN_AUTO, SCAN_PLAIN, SCAN_READ_FIRST = 0, 1, 2
 
 
 class srla_params(ctypes.Structure):
@@ -42,6 +43,10 @@ class srla_slice_stats(ctypes.Structure):
         ("n_sampled", ctypes.c_uint32), ("n_new", ctypes.c_uint32), ("n_candidates", ctypes.c_uint32),
         ("n_carry_out", ctypes.c_uint32), ("w_star", ctypes.c_uint32), ("overflow", ctypes.c_uint32),
         ("up", ctypes.c_double), ("census", ctypes.c_uint64 * MAX_ROWS),
+        ("pair_table", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+        ("n_claims", ctypes.c_uint64), ("n_claim_repeats", ctypes.c_uint64),
+        ("n_scanned", ctypes.c_uint64), ("n_scanned_sampled", ctypes.c_uint64),
+        ("n_set_probes", ctypes.c_uint64),
     ]
 
 
@@ -66,6 +71,8 @@ SIGNATURES = {
     "srla_export_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "srla_import_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "srla_kernel_launches": (ctypes.c_uint64, [_P]),
+    "srla_set_scan_build": (ctypes.c_int, [_P, ctypes.c_uint32]),
+    "srla_scan_builds": (ctypes.c_int, [_P, _P, _P]),
     "srla_uses_graph": (ctypes.c_int, [_P]),
     "srla_destroy": (None, [_P]),
     "srla_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -84,6 +91,8 @@ SIGNATURES = {
     "srla_group_report_all": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_size_t, _P, _P, _P]),
     "srla_group_report": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, ctypes.c_size_t, _P, _P]),
     "srla_group_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "srla_group_state_bytes": (ctypes.c_size_t, [_P, ctypes.c_uint32]),
+    "srla_group_export_state": (ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.c_size_t]),
     "srla_group_sync": (ctypes.c_int, [_P]),
     "srla_group_kernel_launches": (ctypes.c_uint64, [_P]),
     "srla_group_destroy": (None, [_P]),
@@ -97,6 +106,8 @@ SIGNATURES = {
     "srla_server_tick": (ctypes.c_int, [_P, _P, _P, _P]),
     "srla_server_poll": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_size_t, _P, _P, ctypes.c_size_t, _P]),
     "srla_server_used_bytes": (ctypes.c_uint64, [_P]),
+    "srla_server_state_bytes": (ctypes.c_size_t, [_P, ctypes.c_uint64]),
+    "srla_server_export_state": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_size_t]),
     "srla_server_destroy": (None, [_P]),
 }
 
@@ -161,12 +172,13 @@ def wait_selftest(blocks=2, absent=1, spin_limit=10000, device="cuda") -> int:
                                     blocks, absent, spin_limit)
 
 
-PROBE_STORE, PROBE_ATOMIC_MAX, PROBE_READ_FIRST = 0, 1, 2
+PROBE_STORE, PROBE_ATOMIC_MAX, PROBE_READ_FIRST, PROBE_CAS, PROBE_LOAD = 0, 1, 2, 3, 4
 
 
 def scatter_probe(buf, cell_bytes: int, n_stores: int, seed: int = 1, stream=None, policy: int = PROBE_STORE):
     """Enqueue the store roofline probe (srla_scatter_probe) on `stream` over the torch buffer
-    `buf`; `policy` is PROBE_STORE, PROBE_ATOMIC_MAX or PROBE_READ_FIRST."""
+    `buf`; `policy` is PROBE_STORE, PROBE_ATOMIC_MAX, PROBE_READ_FIRST, PROBE_CAS (8-byte
+    cells) or PROBE_LOAD."""
     import torch
 
     st = stream if stream is not None else torch.cuda.current_stream(buf.device)
@@ -281,6 +293,16 @@ class Link:
     def kernel_launches(self) -> int:
         return self.L.srla_kernel_launches(self._h)
 
+    def set_scan_build(self, build: int):
+        """SCAN_AUTO, SCAN_PLAIN or SCAN_READ_FIRST (srla_set_scan_build)."""
+        _ck(self.L.srla_set_scan_build(self._h, build), "srla_set_scan_build")
+
+    def scan_builds(self):
+        """Scan launches so far of the plain build and of the read-first build."""
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        _ck(self.L.srla_scan_builds(self._h, ctypes.byref(a), ctypes.byref(b)), "srla_scan_builds")
+        return a.value, b.value
+
     def uses_graph(self) -> bool:
         return bool(self.L.srla_uses_graph(self._h))
 
@@ -300,17 +322,7 @@ class Link:
 
     def state_arrays(self):
         """Exported state as (re[u, v, g], le[u, v, gl], slice, carried hosts), distances uint16."""
-        b = self.export_state()
-        p = self.params
-        hdr = np.frombuffer(b[:56], dtype=np.uint32)
-        slice_ = int(np.frombuffer(b[40:48], dtype=np.uint64)[0])
-        n_carry = int(hdr[12])
-        nre, nle = p.u * p.v * p.g, p.u * p.v * p.gl
-        d = np.frombuffer(b[56:56 + 2 * (nre + nle)], dtype=np.uint16)
-        re = d[:nre].reshape(p.u, p.v, p.g).copy()
-        le = d[nre:].reshape(p.u, p.v, p.gl).copy()
-        carry = np.frombuffer(b[56 + 2 * (nre + nle):56 + 2 * (nre + nle) + 4 * n_carry], dtype=np.uint32).copy()
-        return re, le, slice_, carry
+        return state_arrays_of(self.params, self.export_state())
 
     def close(self):
         if getattr(self, "_h", None):
@@ -322,6 +334,20 @@ class Link:
             self.close()
         except Exception:
             pass
+
+
+def state_arrays_of(p: srla_params, b: bytes):
+    """Split an exported state (srla_export_state format) into (re[u, v, g], le[u, v, gl],
+    open slice, carried hosts); distances are uint16."""
+    hdr = np.frombuffer(b[:56], dtype=np.uint32)
+    slice_ = int(np.frombuffer(b[40:48], dtype=np.uint64)[0])
+    n_carry = int(hdr[12])
+    nre, nle = p.u * p.v * p.g, p.u * p.v * p.gl
+    d = np.frombuffer(b[56:56 + 2 * (nre + nle)], dtype=np.uint16)
+    re = d[:nre].reshape(p.u, p.v, p.g).copy()
+    le = d[nre:].reshape(p.u, p.v, p.gl).copy()
+    carry = np.frombuffer(b[56 + 2 * (nre + nle):56 + 2 * (nre + nle) + 4 * n_carry], dtype=np.uint32).copy()
+    return re, le, slice_, carry
 
 
 def _stats_dict(st, u):
@@ -437,6 +463,15 @@ class Group:
         t, k = ctypes.c_uint32(), ctypes.c_uint32()
         _ck(self.L.srla_group_autotune(self._h, reps, ctypes.byref(t), ctypes.byref(k)), "srla_group_autotune")
         return t.value, k.value
+
+    def state_arrays(self, link: int):
+        """One link's exported state (srla_group_export_state), as Link.state_arrays."""
+        n = self.L.srla_group_state_bytes(self._h, link)
+        if n == 0:
+            raise SRLAError(E_INVAL, "srla_group_state_bytes")
+        buf = ctypes.create_string_buffer(n)
+        _ck(self.L.srla_group_export_state(self._h, link, buf, n), "srla_group_export_state")
+        return state_arrays_of(self.params[link], buf.raw)
 
     def sync(self):
         _ck(self.L.srla_group_sync(self._h), "srla_group_sync")
@@ -556,6 +591,15 @@ class Server:
 
     def used_bytes(self) -> int:
         return self.L.srla_server_used_bytes(self._h)
+
+    def state_arrays(self, key: int):
+        """An admitted link's exported state (srla_server_export_state), as Link.state_arrays."""
+        n = self.L.srla_server_state_bytes(self._h, key)
+        if n == 0:
+            raise SRLAError(E_ORDER, "srla_server_state_bytes")
+        buf = ctypes.create_string_buffer(n)
+        _ck(self.L.srla_server_export_state(self._h, key, buf, n), "srla_server_export_state")
+        return state_arrays_of(self.params[key], buf.raw)
 
     def destroy(self):
         if getattr(self, "_h", None):

@@ -34,8 +34,10 @@ def compare_reports(ro: dict, rg: dict, where: str = ""):
     assert st["n_carry_out"] == ro["n_carry"], f"{where}: carried count differs"
 
 
-def compare_state(o: "oracle.Oracle", link: "srla.Link", where: str = ""):
-    re_g, le_g, T_g, carry_g = link.state_arrays()
+def compare_state(o: "oracle.Oracle", link, where: str = ""):
+    """Exported recorder distances, open slice and carried list against the oracle's.  `link`
+    is a srla.Link, or the (re, le, slice, carry) tuple of a group or served link's export."""
+    re_g, le_g, T_g, carry_g = link if isinstance(link, tuple) else link.state_arrays()
     re_o, le_o = o.state()
     assert T_g == o.slice, f"{where}: open slice differs"
     assert np.array_equal(re_g, re_o), f"{where}: SRE recorders differ ({(re_g != re_o).sum()} cells)"
@@ -48,3 +50,13 @@ def make_pair(w, device="cuda", **over):
     o = oracle.Oracle.for_workload(w, ha, hb)
     link = srla.Link(srla.params_for(w, ha, hb, **over), device=device)
     return o, link
+
+
+def oracle_for(params, start_slice=None) -> "oracle.Oracle":
+    """An oracle with the geometry, window, threshold and hash coefficients of libsrla
+    parameters (one-bit recorders are z = 1 distances, as everywhere)."""
+    u = params.u
+    ha = np.array([params.hash_a[r] for r in range(u + 3)], dtype=np.uint64)
+    hb = np.array([params.hash_b[r] for r in range(u + 3)], dtype=np.uint64)
+    return oracle.Oracle(u, params.v, params.g, params.gl, params.z, params.k, params.theta, ha, hb,
+                         params.start_slice if start_slice is None else start_slice)

@@ -1,12 +1,26 @@
-"""Groups of links: every link's report in the group equals the report of the same link run
-alone (a single-link handle fed the same packets), slice by slice, while links of different
-geometry, recorder width and window share one graph launch per slice, and while links attach
-and detach between slices.  The single-link path is itself checked against the oracle."""
+"""Groups of links against the CPU oracle.
+
+Each link of a group is its own estimator array (one per edge router, Section 3.1), so each
+link's result is defined by the method alone: Algorithm 2 over that link's packets, the slice
+end of Section 4.2 and Algorithm 3.  Every test runs one oracle beside every group link, with
+the link's parameters, start slice and packets, and compares every report (bit-exact
+integers, estimates within 1e-5 relative) and the exported recorder state with it.  A second
+check compares each group link with the same link run alone through srla_create.
+
+Covered: links of different geometry, recorder width (one-bit, 8-bit, 16-bit), z and window
+in one graph launch per slice, host and device pushes, links that skip slices, an autotune
+in the middle of a run, attach and detach between slices with slot and arena reuse, and the
+64-link batched geometry (mixed 8/16-bit recorders, windows 16..300, SLE 2^16..2^22 cells per
+row) with its packet rates scaled down so that the oracle keeps up.
+"""
+import dataclasses
+import math
+
 import numpy as np
 import pytest
-import torch
 
 import synth
+from gpu_helpers import compare_reports, compare_state, oracle_for
 from paper_1803_10369_b300 import srla
 
 pytestmark = pytest.mark.gpu
@@ -28,11 +42,13 @@ def _links():
                       pkts_per_slice=50_000), {"pair_slots_log2": -1}),
         (TINY.replace(z=1, k=1, seed=24, pkts_per_slice=40_000), {}),
         (TINY.replace(dr_bytes=0, z=1, k=1, g=8, gl=256, seed=25, pkts_per_slice=40_000), {}),
+        (TINY.replace(z=3, k=6, seed=26, start_slice=5, pkts_per_slice=20_000), {}),
         (many, {}),
     ]
 
 
 def _same(got, want, where):
+    """Group link against the same link alone (CUDA against CUDA, a second check)."""
     assert got["aip"].tolist() == want["aip"].tolist(), where
     for key in ("w", "flags", "est"):
         assert np.array_equal(got[key], want[key]), (where, key)
@@ -47,18 +63,19 @@ def _params(w, **over):
     return srla.params_for(w, ha, hb, **over)
 
 
-def _group(n_links=8, arena=1 << 30):
-    return srla.Group(max_links=n_links, max_pkts=4 << 20, arena_bytes=arena, max_host_pkts=1 << 20,
-                      max_report=1 << 18)
+def _group(n_links=8, arena=1 << 30, max_pkts=4 << 20, max_report=1 << 18):
+    return srla.Group(max_links=n_links, max_pkts=max_pkts, arena_bytes=arena, max_host_pkts=1 << 20,
+                      max_report=max_report)
 
 
-def test_group_equals_links_alone(cuda_device):
+def test_group_links_match_oracle(cuda_device):
     links = _links()
     g = _group()
-    solo, ids = [], []
+    ids, orc, solo = [], [], []
     for w, over in links:
         p = _params(w, **over)
         ids.append(g.attach(p))
+        orc.append(oracle_for(p))
         solo.append(srla.Link(p, device=cuda_device))
     rng = np.random.default_rng(3)
     for s in range(6):
@@ -66,6 +83,7 @@ def test_group_equals_links_alone(cuda_device):
             if (s + i) % 5 == 4:
                 continue  # this link gets no packets in this slice
             pk = synth.generate_slice(w.traffic, s)
+            orc[i].push(synth.pairs_to_numpy(pk))
             if rng.random() < 0.5:
                 g.push(ids[i], pk.to(cuda_device))
             else:
@@ -75,24 +93,26 @@ def test_group_equals_links_alone(cuda_device):
             threads, task = g.autotune(reps=1)
             assert threads in (128, 256, 512) and task in (1 << 14, 1 << 16, 1 << 18)
         gs = g.end_slice()
-        want = [solo[i].report(solo[i].end_slice()) for i in range(len(links))]
         allr = g.report_all(gs)
         for i in range(len(links)):
-            _same(allr[ids[i]], want[i], f"slice {s} link {i} (report_all)")
-            _same(g.report(ids[i], gs), want[i], f"slice {s} link {i} (report)")
-    assert max(r["stats"]["n_candidates"] for r in want) > 3 * 4096  # the cooperative sort ran
+            ro = orc[i].end_slice()
+            compare_reports(ro, allr[ids[i]], f"slice {s} link {i} (report_all)")
+            compare_reports(ro, g.report(ids[i], gs), f"slice {s} link {i} (report)")
+            _same(allr[ids[i]], solo[i].report(solo[i].end_slice()), f"slice {s} link {i} (alone)")
+            compare_state(orc[i], g.state_arrays(ids[i]), f"slice {s} link {i}")
+    assert max(int(o_n) for o_n in (allr[l]["stats"]["n_candidates"] for l in ids)) > 3 * 4096  # multi-tile sort
     g.close()
 
 
 def test_links_attach_and_detach_between_slices(cuda_device):
     links = _links()[:4]
     g = _group(n_links=3, arena=256 << 20)
-    live = {}  # group link -> (workload index, solo link)
+    live = {}  # group link -> (workload index, oracle)
 
     def attach(i, start):
         w, over = links[i]
         p = _params(w.replace(start_slice=start), **over)
-        live[g.attach(p)] = (i, srla.Link(p, device=cuda_device))
+        live[g.attach(p)] = (i, oracle_for(p))
 
     attach(0, 0)
     attach(1, 100)
@@ -105,14 +125,54 @@ def test_links_attach_and_detach_between_slices(cuda_device):
             del live[gone]
         if s == 6:
             attach(3, 40)  # reuses the detached link's slot and arena space
-        for link, (i, solo) in live.items():
-            pk = synth.generate_slice(links[i][0].traffic, s).to(cuda_device)
-            g.push(link, pk)
-            solo.push(pk)
+        for link, (i, o) in live.items():
+            pk = synth.generate_slice(links[i][0].traffic, s)
+            g.push(link, pk.to(cuda_device))
+            o.push(synth.pairs_to_numpy(pk))
         gs = g.end_slice()
         allr = g.report_all(gs)
-        for link, (i, solo) in live.items():
-            _same(allr[link], solo.report(solo.end_slice()), f"slice {s} workload {i}")
+        for link, (i, o) in live.items():
+            compare_reports(o.end_slice(), allr[link], f"slice {s} workload {i}")
+            compare_state(o, g.state_arrays(link), f"slice {s} workload {i}")
+    g.close()
+
+
+def _scaled_batched_links(n_links, scale):
+    """The batched workload's links (synth.batched_links) with packet rates and planted hosts
+    divided by `scale`: same geometry, recorder widths and windows."""
+    out = []
+    for w, plog in synth.batched_links(n_links):
+        t = w.traffic
+        t = dataclasses.replace(t, pkts_per_slice=max(2048, t.pkts_per_slice // scale),
+                                n_planted=max(1, t.n_planted // 8), planted_card=(1 << 8, 1 << 12))
+        out.append((dataclasses.replace(w, traffic=t), plog))
+    return out
+
+
+def test_batched_geometry_64_links_match_oracle(cuda_device):
+    """64 links of the batched workload's geometry in one group, 20 slices (past the shortest
+    windows), every report against its oracle, every link's state at the end."""
+    links = _scaled_batched_links(64, 32)
+    params = [srla.params_for(w, *synth.hash_coefficients(w.hash_seed, w.u + 3), pair_slots_log2=plog)
+              for w, plog in links]
+    assert {p.dr_bytes for p in params} == {1, 2} and min(p.k for p in params) <= 20
+    arena = sum(srla.Group.link_bytes(p) for p in params) + (64 << 20)
+    total = sum(w.pkts_per_slice for w, _ in links)
+    g = srla.Group(max_links=64, max_pkts=4 * total + (1 << 20), arena_bytes=arena, max_report=1 << 20,
+                   device=cuda_device)
+    ids = [g.attach(p) for p in params]
+    orc = [oracle_for(p) for p in params]
+    n_slices = 20
+    for s in range(n_slices):
+        for i, (w, _) in enumerate(links):
+            pk = synth.generate_slice(w.traffic, s)
+            orc[i].push(synth.pairs_to_numpy(pk))
+            g.push(ids[i], pk.to(cuda_device))
+        allr = g.report_all(g.end_slice())
+        for i in range(len(links)):
+            compare_reports(orc[i].end_slice(), allr[ids[i]], f"slice {s} link {i} ({links[i][0].name})")
+    for i in range(len(links)):
+        compare_state(orc[i], g.state_arrays(ids[i]), f"end link {i}")
     g.close()
 
 
@@ -127,6 +187,9 @@ def test_group_rules(cuda_device):
     with pytest.raises(srla.SRLAError) as e:  # packets already pushed in the open slice
         g.attach(_params(w.replace(v=64)))
     assert e.value.code == srla.E_ORDER
+    with pytest.raises(srla.SRLAError) as e:  # state export only at a slice boundary
+        g.state_arrays(a)
+    assert e.value.code == srla.E_ORDER
     s0 = g.end_slice()
     g.end_slice()
     g.end_slice()
@@ -139,13 +202,15 @@ def test_group_rules(cuda_device):
         g.attach(small)
     assert e.value.code == srla.E_CAPACITY
     g.detach(b)
+    with pytest.raises(srla.SRLAError):  # a free slot has no state
+        g.state_arrays(b)
     g.close()
 
 
 def test_failed_attach_leaves_the_group_working(cuda_device):
     """The second link's recorders fit the arena but the rebuilt sweep list of both links does
     not (512 spare bytes: room for one tiny link's list, not two): the attach fails with
-    E_NOMEM, is rolled back, and the first link keeps matching the same link run alone."""
+    E_NOMEM, is rolled back, and the first link keeps matching the oracle."""
     small = _params(TINY, pair_slots_log2=10)
     lb = srla.Group.link_bytes(small)
     g = _group(n_links=2, arena=2 * lb + 512)
@@ -153,10 +218,11 @@ def test_failed_attach_leaves_the_group_working(cuda_device):
     with pytest.raises(srla.SRLAError) as e:
         g.attach(_params(TINY.replace(seed=31), pair_slots_log2=10))
     assert e.value.code == srla.E_NOMEM
-    solo = srla.Link(small, device=cuda_device)
+    o = oracle_for(small)
     for s in range(4):
-        pk = synth.generate_slice(TINY.traffic, s).to(cuda_device)
-        g.push(a, pk)
-        solo.push(pk)
-        _same(g.report(a, g.end_slice()), solo.report(solo.end_slice()), f"slice {s}")
+        pk = synth.generate_slice(TINY.traffic, s)
+        g.push(a, pk.to(cuda_device))
+        o.push(synth.pairs_to_numpy(pk))
+        compare_reports(o.end_slice(), g.report(a, g.end_slice()), f"slice {s}")
+    compare_state(o, g.state_arrays(a), "end")
     g.close()

@@ -20,7 +20,9 @@ TINY = synth.workload("tiny")
 # The tiny trace's destinations are uniform over 2^20, so almost no pair repeats: after the
 # first slice the pair table is switched off, and with 8/16-bit recorders the scan runs its
 # read-first build (the one that skips recorders already holding the slice's stamp).  These
-# variants therefore check both scan builds against the oracle.
+# variants therefore check both scan builds against the oracle; the test asserts from the
+# library's per-build launch counts that both ran (flow bursts repeat pairs, so their table
+# stays on and only the plain build runs).
 
 VARIANTS = {
     "tiny": TINY,
@@ -60,8 +62,57 @@ def test_parity_tiny_variants(name, cuda_device):
         rg = link.report(sid)
         compare_reports(ro, rg, f"{name} slice {s}")
         compare_state(o, link, f"{name} slice {s}")
+    plain, read_first = link.scan_builds()
+    assert plain >= 1
+    if w.dr_bytes and name != "flow-bursts-mean8":
+        assert read_first >= w.n_slices // 2, (plain, read_first)
     link.close()
     o.close()
+
+
+# Variants where a wrong skip of the read-first build would show: stamps that wrap (z = 3),
+# k = P (the saturating stamps are cleared after the close), 16-bit stamps with k = P, the
+# paper's g = 8, and pairs that repeat within the slice (pool destinations).
+FORCED = {
+    "tiny": TINY,
+    "z3-k5-stamp-wrap": TINY.replace(z=3, k=5),
+    "z4-k15-k-equals-P": TINY.replace(z=4, k=15),
+    "2byte-z12-k-equals-P": TINY.replace(dr_bytes=2, z=12, k=4095),
+    "paper-g8": TINY.replace(g=8, gl=256, dr_bytes=2, z=16, k=6),
+    "pool-repeats": TINY.replace(dst_model="pool", pool_max=8, z=4, k=6),
+}
+
+
+@pytest.mark.parametrize("build", [srla.SCAN_PLAIN, srla.SCAN_READ_FIRST])
+@pytest.mark.parametrize("name", list(FORCED))
+def test_each_scan_build_alone_matches_oracle(name, build, cuda_device):
+    """Every scan of the run forced to one build: recorders, candidates and estimates still
+    equal the oracle's, and the launch counts show that only that build ran."""
+    w = FORCED[name]
+    o, link = make_pair(w)
+    link.set_scan_build(build)
+    trace = synth.generate_trace(w.traffic, w.n_slices)
+    for s in range(w.n_slices):
+        o.push(synth.pairs_to_numpy(trace[s]))
+        link.push(trace[s].to(cuda_device))
+        compare_reports(o.end_slice(), link.report(link.end_slice()), f"{name} build {build} slice {s}")
+        compare_state(o, link, f"{name} build {build} slice {s}")
+    plain, read_first = link.scan_builds()
+    assert (plain, read_first) == ((w.n_slices, 0) if build == srla.SCAN_PLAIN else (0, w.n_slices))
+    link.close()
+    o.close()
+
+
+def test_scan_build_rules(cuda_device):
+    _, bits = make_pair(TINY.replace(dr_bytes=0, z=1, k=1))
+    with pytest.raises(srla.SRLAError) as e:  # one-bit recorders have no read-first build
+        bits.set_scan_build(srla.SCAN_READ_FIRST)
+    assert e.value.code == srla.E_INVAL
+    with pytest.raises(srla.SRLAError) as e:
+        bits.set_scan_build(3)
+    assert e.value.code == srla.E_INVAL
+    bits.set_scan_build(srla.SCAN_PLAIN)
+    bits.close()
 
 
 def test_ragged_pushes_unaligned_host_and_empty_slices(cuda_device):

@@ -1,8 +1,8 @@
 """The allocation-free entry point (srla_batch_report_static) against the workspace path.
 
-Callers that cannot allocate device memory (real-time capture threads, plugins that only
-get fixed buffers from their host framework, code inside a stream capture) use one fixed
-scratch array compiled into the library.  Its report for a device batch must equal what a
+Callers that cannot allocate device memory (real-time capture threads, for which cudaMalloc
+and cudaFree may stall the whole device, and plugins that only get fixed buffers from their
+host framework) use one fixed scratch array compiled into the library.  Its report for a device batch must equal what a
 freshly created estimator reports after pushing that batch and closing its first slice.
 Two calls in a row check that the shared scratch is cleared between calls.  This file sorts
 last so that a failure here does not hide the rest of the suite.

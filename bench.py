@@ -64,6 +64,34 @@ def max_over_ranks(x: float, world: int, device=None) -> float:
     return float(t.item())
 
 
+def sum_over_ranks(x: float, world: int, device=None) -> float:
+    """Sum of a per-rank figure over all ranks."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def rank_traffic(w, rank: int):
+    """Each rank monitors its own link (replicas): rank r > 0 draws its trace with seed
+    seed + 1000 r."""
+    import dataclasses
+
+    return w.traffic if rank == 0 else dataclasses.replace(w.traffic, seed=w.traffic.seed + 1000 * rank)
+
+
+def job_throughput(pkts: float, elapsed_ms: float, world: int, device=None):
+    """Whole-job Mpkts/s: the packets every rank scanned over the slowest rank's time; also
+    returns that time (ms)."""
+    t = max_over_ranks(elapsed_ms, world, device)
+    total = sum_over_ranks(pkts, world, device)
+    return total / (t * 1e-3) / 1e6, t
+
+
 def _algorithmic_bytes_per_pkt(w, tau):
     """Bytes the scan must move per packet: the 8-byte pair, u SLE recorders, u SRE recorders
     for the 2^-tau sampled share, and a 4-byte sampled-host record for that share (a one-bit
@@ -259,8 +287,7 @@ def bench_srla(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     w = synth.workload(args.workload)
-    # each rank monitors its own link: a different trace seed per rank
-    spec = w.traffic if rank == 0 else w.replace(seed=w.traffic.seed + 1000 * rank).traffic
+    spec = rank_traffic(w, rank)
     ha, hb = synth.hash_coefficients(w.hash_seed, w.u + 3)
     mode = srla.MODE_INLINE if args.mode == "inline" else srla.MODE_ORDER_FREE
     params = srla.params_for(w, ha, hb, staging_pkts=w.pkts_per_slice, mode=mode)
@@ -311,10 +338,8 @@ def bench_srla(args):
     launches = link.kernel_launches() - launches0
     builds = [b - a for a, b in zip(builds0, link.scan_builds())]
     barrier()
-    elapsed_ms = max_over_ranks(ev[0].elapsed_time(ev[1]), world, dev)
+    value, elapsed_ms = job_throughput(pkts, ev[0].elapsed_time(ev[1]), world, dev)
     scan_ms = [a.elapsed_time(b) for a, b in scan_ev]
-    total_pkts = pkts * world
-    value = total_pkts / (elapsed_ms * 1e-3) / 1e6
 
     # ---- latency: slice end -> report, with the slice's scan already complete
     lat, lat_gpu = [], []
@@ -351,8 +376,7 @@ def bench_srla(args):
     r = link.report(pending)
     d2h.append(64 + 16 * len(r["aip"]))
     torch.cuda.synchronize(dev)
-    e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
-    e2e = total_pkts / e2e_s / 1e6
+    e2e, _ = job_throughput(pkts, (time.perf_counter() - t0) * 1e3, world, dev)
 
     peak, peak_kind = _peaks()
     bpp = _algorithmic_bytes_per_pkt(w, tau)
@@ -509,10 +533,12 @@ def _l2_roofline(w, params, stats, builds, scan_ms, store_roof, dev, stream):
             "rates_per_s": {k: round(v, 0) for k, v in rates.items()},
             "time_at_rates_us": {k: round(v * 1e6, 2) for k, v in t.items()},
             "achieved_us": round(scan_ms * 1e3, 2), "bound_us": round(t_sum * 1e6, 2),
-            "frac": round(t_sum / (scan_ms * 1e-3), 4), "scan_build": "read-first" if read_first else "plain",
+            "frac": round(t_sum / (scan_ms * 1e-3), 4),
+            "scan_builds": {"plain": builds[0], "read_first": builds[1], "heavy": builds[2]},
             "pair_table_slices": int(sum(int(st["pair_table"]) for st in stats)), "slices": n,
             "note": "frac = time the scan's L2 operations take at rates measured alone on the same footprints "
-                    "/ measured scan time"}
+                    "/ measured scan time" + ("; the heavy build skips repeated stores of heavy hosts, so "
+                                              "recorder_stores is an upper bound" if builds[2] else "")}
 
 
 def _pctl(xs, q):
@@ -763,20 +789,26 @@ def measure_served(K, W, prefill, dev, n_ident=256, conc=96, life=600.0):
     del srv
 
     # ---- the plain per-link loop on the same schedule
-    links = {}
+    links, retiring = {}, []
 
     def loop_tick(t):
         gone, new, _ = events[t]
-        for k in gone:
-            links.pop(k).close()
+        # a departed link is closed once its last report (of the previous tick) was fetched
+        retiring.extend(links.pop(k) for k in gone)
         for k in new:
             links[k] = srla.Link(params[k], device=dev, stream=stream)
         ends = []
         for k, L in links.items():
             for x in plan[t].get(k, []):
                 L.push(x)
-            ends.append((k, L.end_slice()))
-        return lambda: [links[k].report(sid) for k, sid in ends]
+            ends.append((L, L.end_slice()))
+
+        def fetch():
+            for L, sid in ends:
+                L.report(sid)
+            while retiring:
+                retiring.pop().close()
+        return fetch
 
     with torch.cuda.stream(stream):
         for k in events[0][2]:

@@ -122,7 +122,9 @@ typedef struct srla_slice_stats {
    * timing (which of the repeats of a pair are skipped), the results above do not.         */
   uint32_t pair_table;       /* 1: the scans consulted the per-slice table of scanned pairs
                                 (when the link has one); 0: it was switched off this slice */
-  uint32_t pad;
+  uint32_t heavy_hosts;      /* 1: the previous slice close saw heavy hosts, which selects the
+                                heavy scan build for this slice (groups; single links take it
+                                from the newest reported slice, see srla_set_scan_build) */
   uint64_t n_claims;         /* pairs that missed their block's table of recent pairs and
                                 claimed a slot of the pair table (one compare-and-swap each) */
   uint64_t n_claim_repeats;  /* of which the pair table had seen already (not scanned again) */
@@ -130,6 +132,8 @@ typedef struct srla_slice_stats {
   uint64_t n_scanned_sampled; /* of which sampled: their u SRE recorders set as well */
   uint64_t n_set_probes;     /* insertions tried into the slice's set of sampled hosts (one
                                 per distinct host of a warp's sampled pairs) */
+  uint64_t n_heavy_events;   /* of which hosts with two or more sampled pairs in one warp's
+                                batch of 32 scanned pairs */
 } srla_slice_stats;
 
 typedef struct srla_s srla_t;
@@ -201,21 +205,27 @@ int srla_import_state(srla_t *h, const void *host_buf, size_t len);
 uint64_t srla_kernel_launches(const srla_t *h);
 
 /*
- * The scan (Algorithm 2) has two builds that leave the same recorders: the plain build stores
- * every recorder of a scanned pair; the read-first build (8- and 16-bit recorders, order-free
- * rule) reads the recorders first and skips those already holding the open slice's stamp,
- * which pays when most pairs are new.  SRLA_SCAN_AUTO (the default) picks the read-first build
- * while the newest slice whose report reached the host ran with its pair table switched off;
- * the other two force one build (a tuning and testing aid).  srla_set_scan_build returns
- * SRLA_E_INVAL for an unknown value, or for SRLA_SCAN_READ_FIRST on one-bit recorders or in
- * the inline mode.  srla_scan_builds counts the scan launches of each build since
- * srla_create (either pointer may be NULL).
+ * The scan (Algorithm 2) has three builds that leave the same recorders: the plain build
+ * stores every recorder of a scanned pair; the read-first build (8- and 16-bit recorders,
+ * order-free rule) reads the recorders first and skips those already holding the open
+ * slice's stamp, which pays when most pairs are new; the heavy build (the same recorders,
+ * and u*g' <= 4096, u*g <= 2048) is the plain build in which every block keeps a bitmap of
+ * the recorders it has stamped for one heavy host (a host filling at least 4 of a warp's 32
+ * scanned pairs) and stores each of them once, which pays when one host talks to very many
+ * destinations.  SRLA_SCAN_AUTO (the default) takes the newest slice whose report reached
+ * the host: the read-first build if its pair table was switched off, else the heavy build if
+ * its close saw heavy hosts (slice statistics heavy_hosts / n_heavy_events), else the plain
+ * build.  The other values force one build (a tuning and testing aid).  srla_set_scan_build
+ * returns SRLA_E_INVAL for an unknown value or a build the link cannot run.
+ * srla_scan_builds counts the scan launches of each build since srla_create (any pointer
+ * may be NULL).
  */
 #define SRLA_SCAN_AUTO 0u
 #define SRLA_SCAN_PLAIN 1u
 #define SRLA_SCAN_READ_FIRST 2u
+#define SRLA_SCAN_HEAVY 3u
 int srla_set_scan_build(srla_t *h, uint32_t build);
-int srla_scan_builds(const srla_t *h, uint64_t *plain, uint64_t *read_first);
+int srla_scan_builds(const srla_t *h, uint64_t *plain, uint64_t *read_first, uint64_t *heavy);
 
 /* 1 if srla_end_slice replays a CUDA graph captured at srla_create (one per slice parity),
  * 0 if it launches its kernels one by one (capture was not possible on this device). */
@@ -346,11 +356,31 @@ int srla_group_report_all(srla_group_t *g, uint64_t group_slice, srla_entry *out
 int srla_group_report(srla_group_t *g, uint32_t link, uint64_t group_slice, srla_entry *out,
                       size_t cap, size_t *n_out, srla_slice_stats *stats);
 
+/* Aggregation policy of a link's scan (the pair table of scanned pairs and the scan build):
+ *   SRLA_SCAN_POLICY_ADAPTIVE     pair table switched per slice by the previous slice close
+ *                                 (off while fewer than a quarter of its claims find repeats),
+ *                                 plain build;
+ *   SRLA_SCAN_POLICY_ADAPTIVE_RF  the same table rule, and the read-first build (8/16-bit
+ *                                 recorders) in the slices where the table is off (default);
+ *   SRLA_SCAN_POLICY_OFF          no pair table, plain build;
+ *   SRLA_SCAN_POLICY_OFF_RF       no pair table, read-first build (8/16-bit recorders).
+ * All four leave the same recorders; they differ in speed only.  srla_group_set_scan_policy
+ * takes effect from the next scan; INVAL for a free slot or an unknown policy.            */
+#define SRLA_SCAN_POLICY_ADAPTIVE 0u
+#define SRLA_SCAN_POLICY_ADAPTIVE_RF 1u
+#define SRLA_SCAN_POLICY_OFF 2u
+#define SRLA_SCAN_POLICY_OFF_RF 3u
+int srla_group_set_scan_policy(srla_group_t *g, uint32_t link, uint32_t policy);
+int srla_group_scan_policy(const srla_group_t *g, uint32_t link, uint32_t *policy);
+
 /* Scan autotuner: with the open slice's packets pushed, time the group scan with block sizes
- * 128/256/512 and tasks of 2^14/2^16/2^18 packets (reps runs each, on empty pair tables),
- * keep the fastest (median) for all later slices, and leave the slice's results unchanged
- * (the trial scans repeat the slice's own idempotent recorder stores).  Errors: ORDER when
- * nothing was pushed, CUDA.                                                              */
+ * 128/256/512 and tasks of 2^14/2^16/2^18 packets (reps runs each, on empty pair tables) and
+ * keep the fastest (median); then, per link class (links with fewer than 2^18 packets in the
+ * open slice, and links with more), time the four aggregation policies above for that class's
+ * links and keep the fastest.  The choices hold for all later slices (srla_group_scan_policy
+ * reads a link's); the slice's results are unchanged (the trial scans repeat the slice's own
+ * idempotent recorder stores and set insertions).  Errors: ORDER when nothing was pushed,
+ * CUDA.                                                                                  */
 int srla_group_autotune(srla_group_t *g, int reps, uint32_t *best_threads, uint32_t *best_task_pkts);
 
 /* Checkpoint of one attached link at a slice boundary (no packets pushed in the open group

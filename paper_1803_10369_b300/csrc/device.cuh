@@ -55,17 +55,19 @@ struct Ctl {
   unsigned int pair_mode;         // 1: the scan consults the per-slice pair table
   unsigned int n_miss;            // block-table misses of the open slice that claimed a pair-table slot
   unsigned int n_gdup;            // of which the per-slice pair table found already scanned
-  unsigned int pad2;
+  unsigned int heavy_mode;        // 1: the scan blocks track one heavy host each (HeavyTrack)
   double up;                      // UP of Eq. 8 for the open slice (set at its end)
   unsigned long long n_scan;      // pairs of the open slice scanned (their SLE recorders set)
   unsigned long long n_scan_samp; // of which sampled (their SRE recorders set too)
   unsigned long long n_probe;     // sampled-host set insertions tried (one probe load each)
+  unsigned long long n_heavy;     // heavy events (two or more sampled lanes of one host in a drain)
   unsigned long long census[SRLA_MAX_ROWS];
 };
 
-// Per-thread scan counters, added to the control block once per block.
+// Scan counters of a thread (miss, gdup, probe, heavy) or of its warp (scan, samp: the same
+// value in every lane), added to the control block once per block.
 struct ScanCount {
-  uint32_t miss, gdup, scan, samp, probe;
+  uint32_t miss, gdup, scan, samp, probe, heavy;
 };
 
 // ---------------------------------------------------------------------------- hashing

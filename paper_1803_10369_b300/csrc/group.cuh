@@ -17,7 +17,7 @@ struct LinkDesc {
   uint32_t cell_bytes;  // 1 or 2; 0: one-bit recorders
   uint32_t k_is_P;
   uint32_t umask, umax, cmask, cmax, ntiles, pmask;
-  uint32_t pad;
+  uint32_t scan_policy;  // SRLA_SCAN_POLICY_*: pair table and scan build of this link
   Ctl* ctl;
   void* re;
   void* le;
@@ -87,15 +87,28 @@ __device__ __forceinline__ void with_cells(uint32_t cell_bytes, F&& f) {
 
 // ------------------------------------------------------------------------ scan
 
-template <typename CellT, bool kVec>
+// The link's aggregation policy for this slice: whether the scan consults the per-slice pair
+// table (the adaptive policies follow the pair_mode the previous slice close chose), and
+// whether it runs the read-first build (8/16-bit recorders only).
+__device__ __forceinline__ bool policy_table(const LinkDesc& D, const Ctl* ctl) {
+  const bool adaptive = D.scan_policy == SRLA_SCAN_POLICY_ADAPTIVE || D.scan_policy == SRLA_SCAN_POLICY_ADAPTIVE_RF;
+  return D.ptab && adaptive && ctl->pair_mode;
+}
+
+__device__ __forceinline__ bool policy_read_first(const LinkDesc& D, bool table) {
+  if (D.cell_bytes == 0) return false;
+  return D.scan_policy == SRLA_SCAN_POLICY_OFF_RF || (D.scan_policy == SRLA_SCAN_POLICY_ADAPTIVE_RF && !table);
+}
+
+template <typename CellT, bool kVec, bool kElide, bool kHeavy>
 __device__ __forceinline__ void group_scan_task(const ScanTask& t, const LinkDesc& D, Ctl* ctl,
                                                 volatile unsigned long long* seen, ScanQueues& Q, int lane, int warp,
-                                                int nwarps, ScanCount& sc) {
+                                                int nwarps, ScanCount& sc, bool table, HeavyTrack* hv) {
   const uint32_t* pairs = reinterpret_cast<const uint32_t*>(t.ptr);
   const uint64_t n = t.n;
   CellT* re = static_cast<CellT*>(D.re);
   CellT* le = static_cast<CellT*>(D.le);
-  unsigned long long* ptab = (D.ptab && ctl->pair_mode) ? D.ptab : nullptr;
+  unsigned long long* ptab = table ? D.ptab : nullptr;
   const CellT code = stamp_code<CellT>(ctl->tm);
   const uint32_t tag = slice_tag(ctl->T);
   const Geo& geo = D.geo;
@@ -119,27 +132,31 @@ __device__ __forceinline__ void group_scan_task(const ScanTask& t, const LinkDes
         queue_push(Q.q1, Q.n1, miss && key != kNoPair, key, lane);
         queue_push(Q.q2, Q.n2, miss && key == kNoPair, key, lane);
         if (Q.n2 >= 32)
-          drain_scan<CellT>(Q, sc, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag, lane);
+          drain_scan<CellT, false, kElide, kHeavy>(Q, sc, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag,
+                                           lane, hv);
         if (Q.n1 >= 32)
-          drain_claim<CellT>(Q, sc, ptab, D.pmask, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag,
-                             lane);
+          drain_claim<CellT, kElide, kHeavy>(Q, sc, ptab, D.pmask, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist,
+                                     D.umax, tag, lane, hv);
       } else {
         queue_push(Q.q2, Q.n2, miss, key, lane);
         if (Q.n2 >= 32)
-          drain_scan<CellT>(Q, sc, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag, lane);
+          drain_scan<CellT, false, kElide, kHeavy>(Q, sc, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag,
+                                           lane, hv);
       }
     }
   }
   if (ptab && Q.n1)
-    drain_claim<CellT>(Q, sc, ptab, D.pmask, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag,
-                       lane);
-  while (Q.n2) drain_scan<CellT>(Q, sc, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag, lane);
+    drain_claim<CellT, kElide, kHeavy>(Q, sc, ptab, D.pmask, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax,
+                               tag, lane, hv);
+  while (Q.n2)
+    drain_scan<CellT, false, kElide, kHeavy>(Q, sc, geo, coef, code, re, le, ctl, D.utab, D.umask, D.ulist, D.umax, tag, lane,
+                                     hv);
 }
 
 // Persistent blocks take scan tasks one at a time; a task is one link's batch, so the block's
 // pair table and the link's parameters (in shared memory) serve the whole task.
 template <int kThreads>
-__global__ void __launch_bounds__(kThreads) kg_scan(const LinkDesc* __restrict__ descs,
+__global__ void __launch_bounds__(kThreads, kThreads >= 512 ? 1 : 768 / kThreads) kg_scan(const LinkDesc* __restrict__ descs,
                                                     const TaskHeader* __restrict__ thdr, GroupCtl* __restrict__ gctl) {
   const ScanTask* tasks = reinterpret_cast<const ScanTask*>(thdr + 1);
   __shared__ unsigned long long seen_mem[1 << kGroupSeenLog2];
@@ -147,6 +164,7 @@ __global__ void __launch_bounds__(kThreads) kg_scan(const LinkDesc* __restrict__
   __shared__ LinkDesc sdesc;
   __shared__ ScanTask stask;
   __shared__ unsigned s_task;
+  __shared__ HeavyTrack s_heavy;
   volatile unsigned long long* seen = seen_mem;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned n_tasks = thdr->n_tasks;
@@ -163,17 +181,41 @@ __global__ void __launch_bounds__(kThreads) kg_scan(const LinkDesc* __restrict__
       for (int x = threadIdx.x; x < (int)(sizeof(LinkDesc) / 4); x += kThreads) dst[x] = src[x];
     }
     for (int x = threadIdx.x; x < (1 << kGroupSeenLog2); x += kThreads) seen[x] = kNoPair;
+    heavy_reset(&s_heavy);
     __syncthreads();
     ScanQueues Q{queue_mem[warp][0], queue_mem[warp][1], 0u, 0u};
-    ScanCount sc{0u, 0u, 0u, 0u, 0u};
+    ScanCount sc{0u, 0u, 0u, 0u, 0u, 0u};
     const bool vec = (stask.ptr & 15ull) == 0;
     Ctl* ctl = sdesc.ctl;
+    const bool table = policy_table(sdesc, ctl);
+    const bool elide = policy_read_first(sdesc, table);
+    // the heavy build when the link's previous slice showed heavy hosts (see HeavyTrack)
+    const bool heavy = sdesc.cell_bytes && !elide && ctl->heavy_mode && heavy_fits(sdesc.geo);
+    HeavyTrack* hv = heavy ? &s_heavy : nullptr;
+    const int nw = kThreads / 32;
     with_cells(sdesc.cell_bytes, [&](auto cell) {
       using CellT = decltype(cell);
-      if (vec)
-        group_scan_task<CellT, true>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, sc);
-      else
-        group_scan_task<CellT, false>(stask, sdesc, ctl, seen, Q, lane, warp, kThreads / 32, sc);
+      if constexpr (kIsBit<CellT>) {
+        if (vec)
+          group_scan_task<CellT, true, false, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
+        else
+          group_scan_task<CellT, false, false, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
+      } else if (elide) {
+        if (vec)
+          group_scan_task<CellT, true, true, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
+        else
+          group_scan_task<CellT, false, true, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
+      } else if (heavy) {
+        if (vec)
+          group_scan_task<CellT, true, false, true>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
+        else
+          group_scan_task<CellT, false, false, true>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
+      } else {
+        if (vec)
+          group_scan_task<CellT, true, false, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
+        else
+          group_scan_task<CellT, false, false, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
+      }
     });
     scan_count_flush(sc, ctl, lane);
     __syncthreads();

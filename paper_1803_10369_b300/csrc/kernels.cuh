@@ -18,7 +18,7 @@ constexpr size_t scan_smem_bytes() {
   return (kInline ? 0 : (size_t)kSeen * 8) + (size_t)((kInline ? kScanThreadsInline : kScanThreads) / 32) * 2 * kQueue * 8;
 }
 
-template <typename CellT, bool kVec, bool kInline = false, bool kElide = false>
+template <typename CellT, bool kVec, bool kInline = false, bool kElide = false, bool kHeavy = false>
 __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, kInline ? 2 : 1) k_scan(const uint32_t* __restrict__ pairs, uint64_t n, Geo geo,
                                                           const __grid_constant__ Coef coef, CellT* __restrict__ re,
                                                           CellT* __restrict__ le, Ctl* __restrict__ ctl,
@@ -27,12 +27,15 @@ __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, k
                                                           unsigned long long* __restrict__ ptab, uint32_t pmask,
                                                           const __grid_constant__ InlineArgs ia) {
   extern __shared__ unsigned long long scan_smem[];
+  __shared__ HeavyTrack s_heavy;
   volatile unsigned long long* seen = scan_smem;
   auto queue_mem = reinterpret_cast<unsigned long long(*)[2][kQueue]>(scan_smem + (kInline ? 0 : kSeen));
   if (!kInline)
     for (int x = threadIdx.x; x < kSeen; x += blockDim.x) seen[x] = kNoPair;
+  if constexpr (kHeavy) heavy_reset(&s_heavy);
   __syncthreads();
   if (kInline || (ptab && ctl->pair_mode == 0)) ptab = nullptr;
+  HeavyTrack* hv = (kHeavy && heavy_fits(geo)) ? &s_heavy : nullptr;
   const uint32_t tm = ctl->tm;
   const CellT code = stamp_code<CellT>(tm);
   const uint32_t tag = slice_tag(ctl->T);
@@ -45,7 +48,7 @@ __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, k
   uint64_t base = gw * 128;
   uint32_t a[4], b[4];
   bool ok[4];
-  ScanCount sc{0u, 0u, 0u, 0u, 0u};
+  ScanCount sc{0u, 0u, 0u, 0u, 0u, 0u};
   load_pairs<kVec>(pairs, n, base, lane, a, b, ok);
   while (base < n) {
     const uint64_t next = base + nw * 128;
@@ -70,15 +73,16 @@ __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, k
         queue_push(Q.q1, Q.n1, miss && key != kNoPair, key, lane);
         queue_push(Q.q2, Q.n2, miss && key == kNoPair, key, lane);
         if (Q.n2 >= 32)
-          drain_scan<CellT, false, kElide>(Q, sc, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+          drain_scan<CellT, false, kElide, kHeavy>(Q, sc, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag,
+                                                   lane, hv);
         if (Q.n1 >= 32)
-          drain_claim<CellT, kElide>(Q, sc, ptab, pmask, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag,
-                                     lane);
+          drain_claim<CellT, kElide, kHeavy>(Q, sc, ptab, pmask, geo, coef, code, re, le, ctl, utab, umask, ulist, umax,
+                                             tag, lane, hv);
       } else {
         queue_push(Q.q2, Q.n2, miss, key, lane);
         if (Q.n2 >= 32)
-          drain_scan<CellT, kInline, kElide>(Q, sc, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane,
-                                             &ia, &win);
+          drain_scan<CellT, kInline, kElide, kHeavy>(Q, sc, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag,
+                                                     lane, hv, &ia, &win);
       }
     }
 #pragma unroll
@@ -89,10 +93,11 @@ __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, k
   }
   // what is left in the queues
   if (ptab && Q.n1)
-    drain_claim<CellT, kElide>(Q, sc, ptab, pmask, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+    drain_claim<CellT, kElide, kHeavy>(Q, sc, ptab, pmask, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag,
+                                       lane, hv);
   while (Q.n2)
-    drain_scan<CellT, kInline, kElide>(Q, sc, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane, &ia,
-                                       &win);
+    drain_scan<CellT, kInline, kElide, kHeavy>(Q, sc, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane,
+                                               hv, &ia, &win);
   scan_count_flush(sc, ctl, lane);
 }
 

@@ -54,6 +54,40 @@ __device__ __forceinline__ bool pair_claim_from(unsigned long long* __restrict__
   return true;
 }
 
+// Heavy sources.  One host that talks to very many destinations in a slice (a scanner, a
+// flood victim, a super point far above the threshold) sends all of its recorder stores to
+// the same u runs of g' SLE and g SRE recorders, whose few L2 lines then take them one after
+// another.  When the previous slice close saw such a host (heavy_mode), the scan runs its
+// heavy build (a separate instantiation, so the plain build carries none of this), in which
+// every scan block tracks one heavy host: the first host found filling at least kHeavyLanes of a warp's 32
+// scanned pairs.  For that host the block keeps a bitmap of the recorders it has stamped in
+// this launch (u*g' + u*g bits in shared memory) and stores each recorder once; a stamped
+// recorder keeps the slice's stamp until the slice ends (no other writer changes it), so the
+// skipped stores are exact.  The heavy_mode hint comes from the sampled-host insertion,
+// which already groups a warp's sampled lanes by host: a group of two or more sampled lanes
+// of one host is a heavy event; heavy_mode is set for the next slice when heavy events occur
+// in at least 1/16 of the 32-pair scan drains.
+constexpr int kHeavyLanes = 4;
+constexpr uint32_t kHeavyLeBits = 4096;  // u * g' recorders a block can track
+constexpr uint32_t kHeavyReBits = 2048;  // u * g recorders a block can track
+
+struct HeavyTrack {
+  unsigned long long host;  // 0: none yet; else (1 << 32) | aip
+  uint32_t le[kHeavyLeBits / 32];
+  uint32_t re[kHeavyReBits / 32];
+};
+
+// True if the geometry's runs fit the block's bitmaps.
+__device__ __forceinline__ bool heavy_fits(const Geo& geo) {
+  return geo.u * geo.gl <= kHeavyLeBits && geo.u * geo.g <= kHeavyReBits;
+}
+
+// Clear the tracking state (all threads of the block; the caller synchronises after).
+__device__ __forceinline__ void heavy_reset(HeavyTrack* hv) {
+  uint32_t* w = reinterpret_cast<uint32_t*>(hv);
+  for (uint32_t x = threadIdx.x; x < sizeof(HeavyTrack) / 4; x += blockDim.x) w[x] = 0u;
+}
+
 template <int kLog2 = kSeenLog2>
 __device__ __forceinline__ uint32_t seen_slot(unsigned long long key) {
   return (uint32_t)((key * 0x9E3779B97F4A7C15ull) >> (64 - kLog2));
@@ -62,14 +96,31 @@ __device__ __forceinline__ uint32_t seen_slot(unsigned long long key) {
 // Full scan of one pair per lane (a dense batch): Algorithm 2's DRsets, and the sampled host
 // into the slice's set (one probe per distinct host of the warp, one append counter update
 // per warp).  All 32 lanes call it; `ok` marks the lanes that hold a pair.
-template <typename CellT, bool kInline = false, bool kElide = false>
+template <typename CellT, bool kInline = false, bool kElide = false, bool kHeavy = false>
 __device__ __forceinline__ unsigned scan_dense(uint32_t aip, uint32_t bip, bool ok, const Geo& geo, const Coef& coef,
                                            CellT code, CellT* __restrict__ re, CellT* __restrict__ le,
                                            Ctl* __restrict__ ctl, unsigned long long* __restrict__ utab,
                                            uint32_t umask, uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag,
-                                           int lane, uint32_t& n_probe) {
+                                           int lane, ScanCount& sc, HeavyTrack* hv) {
   const uint32_t u = geo.u;
   bool samp = false;
+  // Heavy-host tracking (the heavy build only: 8/16-bit recorders; hv is non-null when the
+  // geometry fits the bitmaps, the same for the whole warp).  Every lane takes part in the
+  // ballot and the match (full mask), including the lanes without a pair; only then is the
+  // result combined with `ok`.  In the other builds `track` is the constant false.
+  bool track = false;
+  if constexpr (kHeavy && !kIsBit<CellT> && !kElide && !kInline) {
+    if (hv) {
+      const unsigned okm = __ballot_sync(kFull, ok);
+      const unsigned peers = __match_any_sync(kFull, aip) & okm;
+      const bool lead = ok && (peers & ((1u << lane) - 1u)) == 0 && __popc(peers) >= kHeavyLanes;
+      if (lead && *reinterpret_cast<volatile unsigned long long*>(&hv->host) == 0ull)
+        atomicCAS(&hv->host, 0ull, (1ull << 32) | aip);  // the block's first heavy host wins
+      __syncwarp();
+      const unsigned long long hh = *reinterpret_cast<volatile unsigned long long*>(&hv->host);
+      track = ok && (hh >> 32) != 0ull && (uint32_t)hh == aip;
+    }
+  }
   if (ok) {
     const uint32_t jl = hash61(coef.a[u], coef.b[u], bip) & geo.glmask;
     const uint32_t jr = hash61(coef.a[u + 1], coef.b[u + 1], bip) & geo.gmask;
@@ -133,6 +184,21 @@ __device__ __forceinline__ unsigned scan_dense(uint32_t aip, uint32_t bip, bool 
           if (hr[r] != code) dr_set<CellT>(re, xr[r], code);
         }
       }
+    } else if (track) {
+      // the block's heavy host: each of its recorders is stored once per launch (bit i*g'+j
+      // of the SLE bitmap, i*g+j of the SRE bitmap, set by a shared-memory atomic OR)
+      for (uint32_t i = 0; i < u; i++) {
+        const uint32_t c = hash61(coef.a[i], coef.b[i], aip) & geo.vmask;
+        const size_t se = (size_t)i * geo.v + c;
+        const uint32_t bl = i * geo.gl + jl;
+        if (!((atomicOr(&hv->le[bl >> 5], 1u << (bl & 31u)) >> (bl & 31u)) & 1u))
+          dr_set<CellT>(le, se * geo.gl + jl, code);
+        if (samp) {
+          const uint32_t br = i * geo.g + jr;
+          if (!((atomicOr(&hv->re[br >> 5], 1u << (br & 31u)) >> (br & 31u)) & 1u))
+            dr_set<CellT>(re, se * geo.g + jr, code);
+        }
+      }
     } else {
 #pragma unroll 4
       for (uint32_t i = 0; i < u; i++) {
@@ -150,7 +216,8 @@ __device__ __forceinline__ unsigned scan_dense(uint32_t aip, uint32_t bip, bool 
     const unsigned peers = __match_any_sync(sm, aip);
     if ((peers & ((1u << lane) - 1u)) == 0) {
       uint32_t slot;
-      n_probe++;
+      sc.probe++;
+      sc.heavy += __popc(peers) >= 2 ? 1u : 0u;  // a heavy event (see HeavyTrack)
       r = set_insert(utab, umask, tag, aip, &slot);
       if (r < 0) atomicOr(&ctl->overflow, 1u);
     }
@@ -275,28 +342,31 @@ __device__ __forceinline__ bool queue_take(volatile unsigned long long* q, uint3
   return ok;
 }
 
-template <typename CellT, bool kInline = false, bool kElide = false>
+template <typename CellT, bool kInline = false, bool kElide = false, bool kHeavy = false>
 __device__ __forceinline__ void drain_scan(ScanQueues& Q, ScanCount& sc, const Geo& geo, const Coef& coef,
                                            CellT code, CellT* __restrict__ re, CellT* __restrict__ le,
                                            Ctl* __restrict__ ctl, unsigned long long* __restrict__ utab,
                                            uint32_t umask, uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag,
-                                           int lane, const InlineArgs* ia = nullptr, const Win* win = nullptr) {
+                                           int lane, HeavyTrack* hv, const InlineArgs* ia = nullptr,
+                                           const Win* win = nullptr) {
   unsigned long long key;
+  const uint32_t took = min(Q.n2, 32u);  // pairs of this drain (the same in every lane)
   const bool ok = queue_take(Q.q2, Q.n2, lane, key);
   const uint32_t aip = (uint32_t)(key >> 32);
-  const unsigned sm = scan_dense<CellT, kInline, kElide>(aip, (uint32_t)key, ok, geo, coef, code, re, le, ctl, utab,
-                                                         umask, ulist, umax, tag, lane, sc.probe);
-  sc.scan += ok ? 1u : 0u;
-  sc.samp += (sm >> lane) & 1u;
+  const unsigned sm = scan_dense<CellT, kInline, kElide, kHeavy>(aip, (uint32_t)key, ok, geo, coef, code, re, le, ctl,
+                                                                 utab, umask, ulist, umax, tag, lane, sc, hv);
+  sc.scan += took;            // warp-uniform counts: every lane holds the warp's total
+  sc.samp += (uint32_t)__popc(sm);
   if constexpr (kInline) inline_test<CellT>(sm, aip, geo, coef, re, *win, ctl, *ia, lane);
 }
 
-template <typename CellT, bool kElide = false>
+template <typename CellT, bool kElide = false, bool kHeavy = false>
 __device__ __forceinline__ void drain_claim(ScanQueues& Q, ScanCount& sc, unsigned long long* __restrict__ ptab,
                                             uint32_t pmask, const Geo& geo, const Coef& coef, CellT code,
                                             CellT* __restrict__ re, CellT* __restrict__ le, Ctl* __restrict__ ctl,
                                             unsigned long long* __restrict__ utab, uint32_t umask,
-                                            uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag, int lane) {
+                                            uint32_t* __restrict__ ulist, uint32_t umax, uint32_t tag, int lane,
+                                            HeavyTrack* hv) {
   unsigned long long key;
   const bool ok = queue_take(Q.q1, Q.n1, lane, key);
   bool scan = false;
@@ -311,21 +381,23 @@ __device__ __forceinline__ void drain_claim(ScanQueues& Q, ScanCount& sc, unsign
   }
   queue_push(Q.q2, Q.n2, scan, key, lane);
   if (Q.n2 >= 32)
-    drain_scan<CellT, false, kElide>(Q, sc, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane);
+    drain_scan<CellT, false, kElide, kHeavy>(Q, sc, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane,
+                                             hv);
 }
 
 // The block's scan counters into the control block: one reduction per block (all threads
 // of the block call it), one atomic per counter.
 __device__ __forceinline__ void scan_count_flush(ScanCount sc, Ctl* __restrict__ ctl, int lane) {
-  __shared__ unsigned s_cnt[5];
+  __shared__ unsigned s_cnt[6];
   __syncthreads();
-  if (threadIdx.x < 5) s_cnt[threadIdx.x] = 0;
+  if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0;
   __syncthreads();
-  const uint32_t v[5] = {warp_sum(sc.miss), warp_sum(sc.gdup), warp_sum(sc.scan), warp_sum(sc.samp),
-                         warp_sum(sc.probe)};
+  // miss, gdup, probe and heavy are per lane; scan and samp are the warp's totals in every lane
+  const uint32_t v[6] = {warp_sum(sc.miss), warp_sum(sc.gdup), sc.scan, sc.samp, warp_sum(sc.probe),
+                         warp_sum(sc.heavy)};
   if (lane == 0) {
 #pragma unroll
-    for (int i = 0; i < 5; i++)
+    for (int i = 0; i < 6; i++)
       if (v[i]) atomicAdd(&s_cnt[i], v[i]);
   }
   __syncthreads();
@@ -335,6 +407,7 @@ __device__ __forceinline__ void scan_count_flush(ScanCount sc, Ctl* __restrict__
     if (s_cnt[2]) atomicAdd(&ctl->n_scan, (unsigned long long)s_cnt[2]);
     if (s_cnt[3]) atomicAdd(&ctl->n_scan_samp, (unsigned long long)s_cnt[3]);
     if (s_cnt[4]) atomicAdd(&ctl->n_probe, (unsigned long long)s_cnt[4]);
+    if (s_cnt[5]) atomicAdd(&ctl->n_heavy, (unsigned long long)s_cnt[5]);
   }
 }
 
@@ -551,12 +624,13 @@ __device__ __forceinline__ void close_slice(const Geo& geo, Ctl* __restrict__ ct
   s.overflow = c.overflow;
   s.up = c.up;
   s.pair_table = c.pair_mode;
-  s.pad = 0;
   s.n_claims = c.n_miss;
   s.n_claim_repeats = c.n_gdup;
   s.n_scanned = c.n_scan;
   s.n_scanned_sampled = c.n_scan_samp;
   s.n_set_probes = c.n_probe;
+  s.heavy_hosts = c.heavy_mode;
+  s.n_heavy_events = c.n_heavy;
   Ctl n = c;
   for (int i = 0; i < SRLA_MAX_ROWS; i++) {
     s.census[i] = c.census[i];
@@ -581,6 +655,10 @@ __device__ __forceinline__ void close_slice(const Geo& geo, Ctl* __restrict__ ct
   n.n_scan = 0;
   n.n_scan_samp = 0;
   n.n_probe = 0;
+  // heavy-host tracking for the next slice: heavy events in at least 1/16 of the slice's
+  // 32-pair scan drains (n_scan / 32 of them)
+  n.heavy_mode = (c.n_scan > 0 && 512ull * c.n_heavy >= c.n_scan) ? 1u : 0u;
+  n.n_heavy = 0;
   *ctl = n;
   __threadfence();
 }

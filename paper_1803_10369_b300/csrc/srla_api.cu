@@ -41,8 +41,8 @@ struct srla_s {
   uint64_t n_pkts_open;   // packets pushed into the open slice
   uint64_t staging_used;  // staging packets used in the open slice
   uint64_t launches;      // kernels launched so far
-  uint32_t scan_build;    // SRLA_SCAN_AUTO, SRLA_SCAN_PLAIN or SRLA_SCAN_READ_FIRST
-  uint64_t scans[2];      // scan launches of the plain build and of the read-first build
+  uint32_t scan_build;    // SRLA_SCAN_AUTO, _PLAIN, _READ_FIRST or _HEAVY
+  uint64_t scans[3];      // scan launches of the plain, read-first and heavy builds
   int occ_scan[2];        // resident scan blocks per SM (unaligned, aligned batches)
   int occ_sweep;          // resident sweep blocks per SM
   int sort_grid;          // blocks of the cooperative sort
@@ -55,6 +55,7 @@ struct srla_s {
     srla_slice_stats* h_stats;
     srla_entry* h_entries;
     uint32_t* h_pair_mode;  // pair-table state of the slice after this one (read-first scan hint)
+    uint32_t* h_heavy_mode;  // heavy-host state of the slice after this one (heavy scan hint)
   } slot[2];
   void* h_pinned;
 
@@ -119,14 +120,32 @@ InlineArgs inline_args(const srla_t* h) {
 // has reached the host ran with the pair table off: most pairs are then new, and a good share
 // of their stores would repeat a stamp already in place.  The hint is one or two slices old
 // and never waits; either scan gives the same recorders.
-bool read_first_hint(const srla_t* h) {
+// The newest slice whose report copy has reached the host (one or two slices old; never
+// waits), or null.
+const srla_s::Slot* newest_reported(const srla_t* h) {
   for (uint64_t back = 1; back <= 2 && back <= h->T; back++) {
     const srla_s::Slot& s = h->slot[(h->T - back) & 1];
     if (!s.valid || s.slice != h->T - back) continue;
     if (cudaEventQuery(s.ev) != cudaSuccess) continue;
-    return *s.h_pair_mode == 0;
+    return &s;
   }
-  return false;
+  return nullptr;
+}
+
+bool read_first_hint(const srla_t* h) {
+  const srla_s::Slot* s = newest_reported(h);
+  return s && *s->h_pair_mode == 0;
+}
+
+// Heavy build (8/16-bit recorders, order-free rule, runs that fit the block's bitmaps) when
+// the newest reported slice close switched heavy-host tracking on.
+bool heavy_possible(const srla_t* h) {
+  return h->p.dr_bytes != 0 && !inline_mode(h) && h->p.u * h->p.gl <= kHeavyLeBits && h->p.u * h->p.g <= kHeavyReBits;
+}
+
+bool heavy_hint(const srla_t* h) {
+  const srla_s::Slot* s = newest_reported(h);
+  return s && *s->h_heavy_mode != 0;
 }
 
 template <typename CellT>
@@ -134,9 +153,12 @@ int launch_scan(srla_t* h, const uint32_t* pairs, uint64_t n) {
   const bool vec = (reinterpret_cast<uintptr_t>(pairs) & 15u) == 0;
   const bool elide = !kIsBit<CellT> && !inline_mode(h) &&
                      (h->scan_build == SRLA_SCAN_READ_FIRST || (h->scan_build == SRLA_SCAN_AUTO && read_first_hint(h)));
-  h->scans[elide ? 1 : 0]++;
+  const bool heavy = !kIsBit<CellT> && !elide && heavy_possible(h) &&
+                     (h->scan_build == SRLA_SCAN_HEAVY || (h->scan_build == SRLA_SCAN_AUTO && heavy_hint(h)));
+  h->scans[elide ? 1 : heavy ? 2 : 0]++;
   auto kern = inline_mode(h) ? (vec ? k_scan<CellT, true, true> : k_scan<CellT, false, true>)
               : elide        ? (vec ? k_scan<CellT, true, false, true> : k_scan<CellT, false, false, true>)
+              : heavy        ? (vec ? k_scan<CellT, true, false, false, true> : k_scan<CellT, false, false, false, true>)
                              : (vec ? k_scan<CellT, true> : k_scan<CellT, false>);
   const int threads = inline_mode(h) ? kScanThreadsInline : kScanThreads;
   const size_t smem = inline_mode(h) ? scan_smem_bytes<true>() : scan_smem_bytes<false>();
@@ -289,6 +311,8 @@ int enqueue_report_copy(srla_t* h, int q) {
                            cudaMemcpyDeviceToHost, h->st_d2h));
   SRLA_TRY(cudaMemcpyAsync(s.h_pair_mode, &h->ctl()->pair_mode, sizeof(uint32_t), cudaMemcpyDeviceToHost,
                            h->st_d2h));
+  SRLA_TRY(cudaMemcpyAsync(s.h_heavy_mode, &h->ctl()->heavy_mode, sizeof(uint32_t), cudaMemcpyDeviceToHost,
+                           h->st_d2h));
   SRLA_TRY(cudaEventRecord(s.ev, h->st_d2h));
   return SRLA_OK;
 }
@@ -344,6 +368,10 @@ int occupancy(srla_t* h) {
         cudaFuncSetAttribute(k_scan<CellT, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)scan_smem_bytes<false>()) != cudaSuccess ||
         cudaFuncSetAttribute(k_scan<CellT, true, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scan_smem_bytes<false>()) != cudaSuccess ||
+        cudaFuncSetAttribute(k_scan<CellT, false, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)scan_smem_bytes<false>()) != cudaSuccess ||
+        cudaFuncSetAttribute(k_scan<CellT, true, false, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)scan_smem_bytes<false>()) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, k0, threads, smem) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k1, threads, smem) != cudaSuccess ||
@@ -449,7 +477,9 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
     h->slot[q].h_entries = reinterpret_cast<srla_entry*>(reinterpret_cast<char*>(h->slot[q].h_stats) +
                                                          sizeof(srla_slice_stats));
     h->slot[q].h_pair_mode = reinterpret_cast<uint32_t*>(h->slot[q].h_entries + kPrefetch);
+    h->slot[q].h_heavy_mode = h->slot[q].h_pair_mode + 1;
     *h->slot[q].h_pair_mode = 1u;
+    *h->slot[q].h_heavy_mode = 0u;
     if (cudaEventCreateWithFlags(&h->slot[q].ev, cudaEventDisableTiming) != cudaSuccess) rc = SRLA_E_CUDA;
   }
   if (rc == SRLA_OK) {
@@ -706,17 +736,20 @@ int srla_import_state(srla_t* h, const void* host_buf, size_t len) {
 uint64_t srla_kernel_launches(const srla_t* h) { return h ? h->launches : 0; }
 
 int srla_set_scan_build(srla_t* h, uint32_t build) {
-  if (!h || build > SRLA_SCAN_READ_FIRST) return SRLA_E_INVAL;
-  // the read-first build exists for 8- and 16-bit recorders under the order-free rule
+  if (!h || build > SRLA_SCAN_HEAVY) return SRLA_E_INVAL;
+  // the read-first build exists for 8- and 16-bit recorders under the order-free rule; the
+  // heavy build, in addition, for runs that fit its bitmaps
   if (build == SRLA_SCAN_READ_FIRST && (h->p.dr_bytes == 0 || inline_mode(h))) return SRLA_E_INVAL;
+  if (build == SRLA_SCAN_HEAVY && !heavy_possible(h)) return SRLA_E_INVAL;
   h->scan_build = build;
   return SRLA_OK;
 }
 
-int srla_scan_builds(const srla_t* h, uint64_t* plain, uint64_t* read_first) {
+int srla_scan_builds(const srla_t* h, uint64_t* plain, uint64_t* read_first, uint64_t* heavy) {
   if (!h) return SRLA_E_INVAL;
   if (plain) *plain = h->scans[0];
   if (read_first) *read_first = h->scans[1];
+  if (heavy) *heavy = h->scans[2];
   return SRLA_OK;
 }
 

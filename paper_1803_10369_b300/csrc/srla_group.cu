@@ -85,6 +85,7 @@ struct Slot {
   uint64_t pkts_open = 0;
   uint64_t attached_at = 0;   // first group slice of the link
   uint64_t pkts_slice[2] = {0, 0};
+  uint32_t policy = SRLA_SCAN_POLICY_ADAPTIVE_RF;  // aggregation policy of its scan
 };
 
 struct Region {
@@ -201,6 +202,7 @@ LinkDesc make_desc(srla_group_t* g, const Slot& s) {
     D.coef.b[r] = p.hash_b[r];
   }
   D.active = 1;
+  D.scan_policy = s.policy;
   D.cell_bytes = p.dr_bytes;
   D.k_is_P = p.k == D.geo.P;
   D.umask = L.umask;
@@ -668,6 +670,21 @@ int srla_group_report(srla_group_t* g, uint32_t link, uint64_t gs, srla_entry* o
   return SRLA_OK;
 }
 
+int srla_group_set_scan_policy(srla_group_t* g, uint32_t link, uint32_t policy) {
+  if (!g || link >= g->max_links || !g->slots[link].active || policy > SRLA_SCAN_POLICY_OFF_RF) return SRLA_E_INVAL;
+  g->slots[link].policy = policy;
+  // stream-ordered after every slice end already enqueued, before the next one
+  G_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(g->descs() + link) + offsetof(LinkDesc, scan_policy),
+                        &g->slots[link].policy, sizeof(uint32_t), cudaMemcpyHostToDevice, g->st));
+  return gerr(cudaStreamSynchronize(g->st));
+}
+
+int srla_group_scan_policy(const srla_group_t* g, uint32_t link, uint32_t* policy) {
+  if (!g || !policy || link >= g->max_links || !g->slots[link].active) return SRLA_E_INVAL;
+  *policy = g->slots[link].policy;
+  return SRLA_OK;
+}
+
 int srla_group_autotune(srla_group_t* g, int reps, uint32_t* best_threads, uint32_t* best_task_pkts) {
   if (!g || reps < 1) return SRLA_E_INVAL;
   if (g->segments.empty()) return SRLA_E_ORDER;
@@ -683,45 +700,90 @@ int srla_group_autotune(srla_group_t* g, int reps, uint32_t* best_threads, uint3
     cudaEventDestroy(e0);
     return SRLA_E_CUDA;
   }
+  // Each trial starts from empty pair tables and a zero task counter; the recorder stores and
+  // sampled-host inserts repeat the slice's own, so the state after tuning is unchanged.
+  auto trial = [&](int nthreads, float* ms) -> int {
+    int rr = split_tasks(g);
+    if (rr != SRLA_OK) return rr;
+    g->h_tasks[q]->n_tasks = (unsigned)g->pending.size();
+    std::memcpy(reinterpret_cast<ScanTask*>(g->h_tasks[q] + 1), g->pending.data(), g->pending.size() * sizeof(ScanTask));
+    for (const Slot& s : g->slots)
+      if (s.active && s.L.pairs)
+        rr = rr ? rr : gerr(cudaMemsetAsync(g->ws + s.off + s.L.ptab[0], 0xFF, ((size_t)s.L.pmask + 1) * 8, g->st));
+    rr = rr ? rr : gerr(cudaMemsetAsync(&g->gctl()->next_task, 0, sizeof(unsigned), g->st));
+    rr = rr ? rr : gerr(cudaMemcpyAsync(g->ws + g->F.tasks, g->h_tasks[q], sizeof(TaskHeader) + sizeof(ScanTask) * g->pending.size(),
+                                        cudaMemcpyHostToDevice, g->st));
+    rr = rr ? rr : gerr(cudaEventRecord(e0, g->st));
+    if (rr == SRLA_OK) {
+      g->launches++;
+      launch_group_scan(g, nthreads, reinterpret_cast<const TaskHeader*>(g->ws + g->F.tasks));
+    }
+    rr = rr ? rr : gerr(cudaEventRecord(e1, g->st));
+    rr = rr ? rr : gerr(cudaEventSynchronize(e1));
+    if (rr == SRLA_OK && cudaEventElapsedTime(ms, e0, e1) != cudaSuccess) rr = SRLA_E_CUDA;
+    return rr;
+  };
+  auto median = [](std::vector<float>& v) {
+    std::sort(v.begin(), v.end());
+    return v.empty() ? 1e30f : v[v.size() / 2];
+  };
+  // 1. launch shape: block size x packets per task
   std::vector<std::vector<float>> ms(9);
   for (int rep = 0; rep < reps && r == SRLA_OK; rep++) {
     for (int c = 0; c < 9 && r == SRLA_OK; c++) {
       g->task_pkts = tasks[c % 3];
-      if ((r = split_tasks(g)) != SRLA_OK) break;
-      g->h_tasks[q]->n_tasks = (unsigned)g->pending.size();
-      std::memcpy(reinterpret_cast<ScanTask*>(g->h_tasks[q] + 1), g->pending.data(), g->pending.size() * sizeof(ScanTask));
-      // each trial starts from empty pair tables and a zero task counter; the recorder stores and
-      // sampled-host inserts repeat the slice's own, so the state after tuning is unchanged
-      for (const Slot& s : g->slots)
-        if (s.active && s.L.pairs)
-          r = r ? r : gerr(cudaMemsetAsync(g->ws + s.off + s.L.ptab[0], 0xFF, ((size_t)s.L.pmask + 1) * 8, g->st));
-      r = r ? r : gerr(cudaMemsetAsync(&g->gctl()->next_task, 0, sizeof(unsigned), g->st));
-      r = r ? r : gerr(cudaMemcpyAsync(g->ws + g->F.tasks, g->h_tasks[q], sizeof(TaskHeader) + sizeof(ScanTask) * g->pending.size(),
-                                       cudaMemcpyHostToDevice, g->st));
-      r = r ? r : gerr(cudaEventRecord(e0, g->st));
-      if (r == SRLA_OK) {
-        g->launches++;
-        launch_group_scan(g, threads[c / 3], reinterpret_cast<const TaskHeader*>(g->ws + g->F.tasks));
-      }
-      r = r ? r : gerr(cudaEventRecord(e1, g->st));
-      r = r ? r : gerr(cudaEventSynchronize(e1));
       float t = 0;
-      if (r == SRLA_OK && cudaEventElapsedTime(&t, e0, e1) == cudaSuccess) ms[c].push_back(t);
+      if ((r = trial(threads[c / 3], &t)) == SRLA_OK) ms[c].push_back(t);
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   int best = 4;  // 256 threads, 64K packets
   float best_ms = 1e30f;
   for (int c = 0; c < 9; c++) {
-    if (ms[c].empty()) continue;
-    std::sort(ms[c].begin(), ms[c].end());
-    const float med = ms[c][ms[c].size() / 2];
+    const float med = median(ms[c]);
     if (med < best_ms) {
       best_ms = med;
       best = c;
     }
   }
+  g->scan_threads = threads[best / 3];
+  g->task_pkts = tasks[best % 3];
+  // 2. aggregation policy per link class (by packets in the open slice), one class at a time
+  constexpr uint64_t kHeavyPkts = 1ull << 18;
+  auto set_class = [&](int cls, uint32_t pol) -> int {
+    for (uint32_t l = 0; l < g->max_links; l++) {
+      Slot& s = g->slots[l];
+      if (!s.active || (int)(s.pkts_open >= kHeavyPkts) != cls) continue;
+      s.policy = pol;
+      G_TRY(cudaMemcpyAsync(reinterpret_cast<char*>(g->descs() + l) + offsetof(LinkDesc, scan_policy), &s.policy,
+                            sizeof(uint32_t), cudaMemcpyHostToDevice, g->st));
+      G_TRY(cudaStreamSynchronize(g->st));  // the host value is reused before the copy would run
+    }
+    return SRLA_OK;
+  };
+  for (int cls = 0; cls < 2 && r == SRLA_OK; cls++) {
+    bool any = false;
+    for (const Slot& s : g->slots) any |= s.active && s.pkts_open && (int)(s.pkts_open >= kHeavyPkts) == cls;
+    if (!any) continue;
+    std::vector<float> pm[4];
+    for (int rep = 0; rep < reps && r == SRLA_OK; rep++) {
+      for (uint32_t pol = 0; pol < 4 && r == SRLA_OK; pol++) {
+        float t = 0;
+        if ((r = set_class(cls, pol)) == SRLA_OK && (r = trial(g->scan_threads, &t)) == SRLA_OK) pm[pol].push_back(t);
+      }
+    }
+    uint32_t best_pol = SRLA_SCAN_POLICY_ADAPTIVE_RF;
+    float best_pol_ms = median(pm[best_pol]);
+    for (uint32_t pol = 0; pol < 4; pol++) {
+      const float med = median(pm[pol]);
+      if (med < best_pol_ms) {
+        best_pol_ms = med;
+        best_pol = pol;
+      }
+    }
+    r = r ? r : set_class(cls, best_pol);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
   // the slice end starts from empty pair tables, zero scan counters and a zero task counter,
   // as without tuning
   for (const Slot& s : g->slots) {
@@ -730,11 +792,9 @@ int srla_group_autotune(srla_group_t* g, int reps, uint32_t* best_threads, uint3
       r = r ? r : gerr(cudaMemsetAsync(g->ws + s.off + s.L.ptab[0], 0xFF, ((size_t)s.L.pmask + 1) * 8, g->st));
     char* c = g->ws + s.off + s.L.ctl;
     r = r ? r : gerr(cudaMemsetAsync(c + offsetof(Ctl, n_miss), 0, 2 * sizeof(unsigned), g->st));
-    r = r ? r : gerr(cudaMemsetAsync(c + offsetof(Ctl, n_scan), 0, 3 * sizeof(unsigned long long), g->st));
+    r = r ? r : gerr(cudaMemsetAsync(c + offsetof(Ctl, n_scan), 0, 4 * sizeof(unsigned long long), g->st));
   }
   r = r ? r : gerr(cudaMemsetAsync(&g->gctl()->next_task, 0, sizeof(unsigned), g->st));
-  g->scan_threads = threads[best / 3];
-  g->task_pkts = tasks[best % 3];
   g->pending.clear();
   // the captured slice ends must launch the chosen scan
   for (int x = 0; x < 2; x++) {

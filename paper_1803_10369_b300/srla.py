@@ -19,7 +19,10 @@ N_HASH = MAX_ROWS + 3
 OK, E_INVAL, E_NOMEM, E_CAPACITY, E_CUDA, E_ORDER, E_TIMEOUT = 0, -1, -2, -3, -4, -5, -6
 SUPER, SATURATED, CARRIED, NEW = 1, 2, 4, 8
 MODE_ORDER_FREE, MODE_INLINE = 0, 1
-SCAN_AUTO, SCAN_PLAIN, SCAN_READ_FIRST = 0, 1, 2
+SCAN_AUTO, SCAN_PLAIN, SCAN_READ_FIRST, SCAN_HEAVY = 0, 1, 2, 3
+SCAN_POLICY_ADAPTIVE, SCAN_POLICY_ADAPTIVE_RF, SCAN_POLICY_OFF, SCAN_POLICY_OFF_RF = 0, 1, 2, 3
+SCAN_POLICY_NAMES = {0: "adaptive-table/plain", 1: "adaptive-table/read-first-when-off", 2: "table-off/plain",
+                     3: "table-off/read-first"}
 
 
 class srla_params(ctypes.Structure):
@@ -43,10 +46,10 @@ class srla_slice_stats(ctypes.Structure):
         ("n_sampled", ctypes.c_uint32), ("n_new", ctypes.c_uint32), ("n_candidates", ctypes.c_uint32),
         ("n_carry_out", ctypes.c_uint32), ("w_star", ctypes.c_uint32), ("overflow", ctypes.c_uint32),
         ("up", ctypes.c_double), ("census", ctypes.c_uint64 * MAX_ROWS),
-        ("pair_table", ctypes.c_uint32), ("pad", ctypes.c_uint32),
+        ("pair_table", ctypes.c_uint32), ("heavy_hosts", ctypes.c_uint32),
         ("n_claims", ctypes.c_uint64), ("n_claim_repeats", ctypes.c_uint64),
         ("n_scanned", ctypes.c_uint64), ("n_scanned_sampled", ctypes.c_uint64),
-        ("n_set_probes", ctypes.c_uint64),
+        ("n_set_probes", ctypes.c_uint64), ("n_heavy_events", ctypes.c_uint64),
     ]
 
 
@@ -72,7 +75,7 @@ SIGNATURES = {
     "srla_import_state": (ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     "srla_kernel_launches": (ctypes.c_uint64, [_P]),
     "srla_set_scan_build": (ctypes.c_int, [_P, ctypes.c_uint32]),
-    "srla_scan_builds": (ctypes.c_int, [_P, _P, _P]),
+    "srla_scan_builds": (ctypes.c_int, [_P, _P, _P, _P]),
     "srla_uses_graph": (ctypes.c_int, [_P]),
     "srla_destroy": (None, [_P]),
     "srla_strerror": (ctypes.c_char_p, [ctypes.c_int]),
@@ -91,6 +94,8 @@ SIGNATURES = {
     "srla_group_report_all": (ctypes.c_int, [_P, ctypes.c_uint64, _P, ctypes.c_size_t, _P, _P, _P]),
     "srla_group_report": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint64, _P, ctypes.c_size_t, _P, _P]),
     "srla_group_autotune": (ctypes.c_int, [_P, ctypes.c_int, _P, _P]),
+    "srla_group_set_scan_policy": (ctypes.c_int, [_P, ctypes.c_uint32, ctypes.c_uint32]),
+    "srla_group_scan_policy": (ctypes.c_int, [_P, ctypes.c_uint32, _P]),
     "srla_group_state_bytes": (ctypes.c_size_t, [_P, ctypes.c_uint32]),
     "srla_group_export_state": (ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.c_size_t]),
     "srla_group_sync": (ctypes.c_int, [_P]),
@@ -294,14 +299,14 @@ class Link:
         return self.L.srla_kernel_launches(self._h)
 
     def set_scan_build(self, build: int):
-        """SCAN_AUTO, SCAN_PLAIN or SCAN_READ_FIRST (srla_set_scan_build)."""
+        """SCAN_AUTO, SCAN_PLAIN, SCAN_READ_FIRST or SCAN_HEAVY (srla_set_scan_build)."""
         _ck(self.L.srla_set_scan_build(self._h, build), "srla_set_scan_build")
 
     def scan_builds(self):
-        """Scan launches so far of the plain build and of the read-first build."""
-        a, b = ctypes.c_uint64(), ctypes.c_uint64()
-        _ck(self.L.srla_scan_builds(self._h, ctypes.byref(a), ctypes.byref(b)), "srla_scan_builds")
-        return a.value, b.value
+        """Scan launches so far of the plain, read-first and heavy builds."""
+        a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _ck(self.L.srla_scan_builds(self._h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "srla_scan_builds")
+        return a.value, b.value, c.value
 
     def uses_graph(self) -> bool:
         return bool(self.L.srla_uses_graph(self._h))
@@ -459,10 +464,19 @@ class Group:
                 "stats": _stats_dict(st, p.u), "rc": rc}
 
     def autotune(self, reps=3):
-        """Pick the scan block size and task size on the open slice's packets; returns both."""
+        """Pick the scan block size, task size and per-class aggregation policies on the open
+        slice's packets; returns (block size, packets per task)."""
         t, k = ctypes.c_uint32(), ctypes.c_uint32()
         _ck(self.L.srla_group_autotune(self._h, reps, ctypes.byref(t), ctypes.byref(k)), "srla_group_autotune")
         return t.value, k.value
+
+    def set_scan_policy(self, link: int, policy: int):
+        _ck(self.L.srla_group_set_scan_policy(self._h, link, policy), "srla_group_set_scan_policy")
+
+    def scan_policy(self, link: int) -> int:
+        p = ctypes.c_uint32()
+        _ck(self.L.srla_group_scan_policy(self._h, link, ctypes.byref(p)), "srla_group_scan_policy")
+        return p.value
 
     def state_arrays(self, link: int):
         """One link's exported state (srla_group_export_state), as Link.state_arrays."""

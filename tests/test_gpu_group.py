@@ -43,6 +43,7 @@ def _links():
         (TINY.replace(z=1, k=1, seed=24, pkts_per_slice=40_000), {}),
         (TINY.replace(dr_bytes=0, z=1, k=1, g=8, gl=256, seed=25, pkts_per_slice=40_000), {}),
         (TINY.replace(z=3, k=6, seed=26, start_slice=5, pkts_per_slice=20_000), {}),
+        (TINY.replace(heavy_frac=0.3, dst_model="pool", pool_max=16, seed=28), {}),  # heavy-host tracking
         (many, {}),
     ]
 
@@ -63,7 +64,7 @@ def _params(w, **over):
     return srla.params_for(w, ha, hb, **over)
 
 
-def _group(n_links=8, arena=1 << 30, max_pkts=4 << 20, max_report=1 << 18):
+def _group(n_links=12, arena=1 << 30, max_pkts=4 << 20, max_report=1 << 18):
     return srla.Group(max_links=n_links, max_pkts=max_pkts, arena_bytes=arena, max_host_pkts=1 << 20,
                       max_report=max_report)
 
@@ -92,6 +93,7 @@ def test_group_links_match_oracle(cuda_device):
         if s == 2:  # tuning repeats the slice's own scan with other launch shapes: no effect on results
             threads, task = g.autotune(reps=1)
             assert threads in (128, 256, 512) and task in (1 << 14, 1 << 16, 1 << 18)
+            assert all(g.scan_policy(l) in range(4) for l in ids)
         gs = g.end_slice()
         allr = g.report_all(gs)
         for i in range(len(links)):
@@ -134,6 +136,33 @@ def test_links_attach_and_detach_between_slices(cuda_device):
         for link, (i, o) in live.items():
             compare_reports(o.end_slice(), allr[link], f"slice {s} workload {i}")
             compare_state(o, g.state_arrays(link), f"slice {s} workload {i}")
+    g.close()
+
+
+def test_group_scan_policies_match_oracle(cuda_device):
+    """The four aggregation policies (pair table adaptive or off, plain or read-first build)
+    rotate over the links slice by slice; every report and state still equals the oracle's."""
+    links = _links()[:8] + [(TINY.replace(seed=27, dst_model="pool", pool_max=4, dr_bytes=2, z=16, k=5), {})]
+    g = _group()
+    ids, orc = [], []
+    for w, over in links:
+        p = _params(w, **over)
+        ids.append(g.attach(p))
+        orc.append(oracle_for(p))
+    for s in range(8):
+        for i, (w, _) in enumerate(links):
+            g.set_scan_policy(ids[i], (s + i) % 4)
+            pk = synth.generate_slice(w.traffic, s)
+            orc[i].push(synth.pairs_to_numpy(pk))
+            g.push(ids[i], pk.to(cuda_device))
+        allr = g.report_all(g.end_slice())
+        for i in range(len(links)):
+            assert g.scan_policy(ids[i]) == (s + i) % 4
+            compare_reports(orc[i].end_slice(), allr[ids[i]], f"slice {s} link {i} policy {(s + i) % 4}")
+            compare_state(orc[i], g.state_arrays(ids[i]), f"slice {s} link {i}")
+    with pytest.raises(srla.SRLAError) as e:
+        g.set_scan_policy(ids[0], 4)
+    assert e.value.code == srla.E_INVAL
     g.close()
 
 

@@ -39,6 +39,9 @@ VARIANTS = {
     "tag-wrap-2^31": TINY.replace(start_slice=(1 << 31) - 5),
     "slice-wrap-2^64": TINY.replace(start_slice=(1 << 64) - 6),
     "flow-bursts-mean8": TINY.replace(burst_mean=8.0),
+    # one source sends 30 % of the packets to random destinations: the scan blocks track it
+    # (heavy-host bitmaps) from the second slice on; pool destinations keep the pair table on
+    "heavy-source": TINY.replace(heavy_frac=0.3, dst_model="pool", pool_max=16),
     # one-bit recorders packed 32 to a word (z = 1, k = 1); runs of 8 and of 4/16 recorders
     # share words, runs of 64 and 1024 span whole words
     "bits-discrete": TINY.replace(dr_bytes=0, z=1, k=1),
@@ -53,6 +56,7 @@ def test_parity_tiny_variants(name, cuda_device):
     o, link = make_pair(w)
     assert link.uses_graph()  # the slice end replays the captured graphs
     trace = synth.generate_trace(w.traffic, w.n_slices)
+    heavy = set()
     for s in range(w.n_slices):
         pk = trace[s]
         o.push(synth.pairs_to_numpy(pk))
@@ -62,10 +66,14 @@ def test_parity_tiny_variants(name, cuda_device):
         rg = link.report(sid)
         compare_reports(ro, rg, f"{name} slice {s}")
         compare_state(o, link, f"{name} slice {s}")
-    plain, read_first = link.scan_builds()
+        heavy.add(int(rg["stats"]["heavy_hosts"]))
+    plain, read_first, heavy_builds = link.scan_builds()
     assert plain >= 1
-    if w.dr_bytes and name != "flow-bursts-mean8":
+    if w.dr_bytes and name not in ("flow-bursts-mean8", "heavy-source"):
         assert read_first >= w.n_slices // 2, (plain, read_first)
+    if name == "heavy-source":  # off in the first slice, on once heavy events were seen
+        assert heavy == {0, 1}, heavy
+        assert heavy_builds >= w.n_slices // 2, (plain, read_first, heavy_builds)
     link.close()
     o.close()
 
@@ -80,10 +88,12 @@ FORCED = {
     "2byte-z12-k-equals-P": TINY.replace(dr_bytes=2, z=12, k=4095),
     "paper-g8": TINY.replace(g=8, gl=256, dr_bytes=2, z=16, k=6),
     "pool-repeats": TINY.replace(dst_model="pool", pool_max=8, z=4, k=6),
+    "heavy-source-uniform": TINY.replace(heavy_frac=0.3, z=5, k=9),
+    "heavy-source-2byte": TINY.replace(heavy_frac=0.3, dr_bytes=2, z=16, k=6, gl=256, theta=256),
 }
 
 
-@pytest.mark.parametrize("build", [srla.SCAN_PLAIN, srla.SCAN_READ_FIRST])
+@pytest.mark.parametrize("build", [srla.SCAN_PLAIN, srla.SCAN_READ_FIRST, srla.SCAN_HEAVY])
 @pytest.mark.parametrize("name", list(FORCED))
 def test_each_scan_build_alone_matches_oracle(name, build, cuda_device):
     """Every scan of the run forced to one build: recorders, candidates and estimates still
@@ -97,8 +107,10 @@ def test_each_scan_build_alone_matches_oracle(name, build, cuda_device):
         link.push(trace[s].to(cuda_device))
         compare_reports(o.end_slice(), link.report(link.end_slice()), f"{name} build {build} slice {s}")
         compare_state(o, link, f"{name} build {build} slice {s}")
-    plain, read_first = link.scan_builds()
-    assert (plain, read_first) == ((w.n_slices, 0) if build == srla.SCAN_PLAIN else (0, w.n_slices))
+    counts = link.scan_builds()
+    want = [0, 0, 0]
+    want[{srla.SCAN_PLAIN: 0, srla.SCAN_READ_FIRST: 1, srla.SCAN_HEAVY: 2}[build]] = w.n_slices
+    assert counts == tuple(want), counts
     link.close()
     o.close()
 
@@ -108,11 +120,20 @@ def test_scan_build_rules(cuda_device):
     with pytest.raises(srla.SRLAError) as e:  # one-bit recorders have no read-first build
         bits.set_scan_build(srla.SCAN_READ_FIRST)
     assert e.value.code == srla.E_INVAL
+    with pytest.raises(srla.SRLAError) as e:  # nor a heavy build
+        bits.set_scan_build(srla.SCAN_HEAVY)
+    assert e.value.code == srla.E_INVAL
     with pytest.raises(srla.SRLAError) as e:
-        bits.set_scan_build(3)
+        bits.set_scan_build(4)
     assert e.value.code == srla.E_INVAL
     bits.set_scan_build(srla.SCAN_PLAIN)
     bits.close()
+    _, wide = make_pair(TINY.replace(gl=2048))  # u*g' = 8192 recorders: beyond the heavy bitmaps
+    with pytest.raises(srla.SRLAError) as e:
+        wide.set_scan_build(srla.SCAN_HEAVY)
+    assert e.value.code == srla.E_INVAL
+    wide.set_scan_build(srla.SCAN_READ_FIRST)
+    wide.close()
 
 
 def test_ragged_pushes_unaligned_host_and_empty_slices(cuda_device):

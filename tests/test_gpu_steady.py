@@ -56,7 +56,7 @@ def test_paper_geometry_full_window(cuda_device):
         n_cand = max(n_cand, ro["n_candidates"])
         if (s + 1) % 50 == 0 or s == n - 1:
             compare_state(o, link, f"slice {s}")
-    plain, read_first = link.scan_builds()
+    plain, read_first, _ = link.scan_builds()
     assert table == {0, 1}, table            # the pair table was switched off and on again
     assert plain > 0 and read_first > 0, (plain, read_first)
     assert n_cand >= 100

@@ -45,6 +45,41 @@ def test_max_over_ranks_gloo():
     assert got == {0: 15.0, 1: 15.0}
 
 
+def _job_worker(rank, world, port, q):
+    import torch.distributed as dist
+
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank, world_size=world)
+    w = synth.workload("paper")
+    spec = bench.rank_traffic(w, rank)
+    # rank r scanned 1e6 (r + 1) packets in 10 (r + 1) ms
+    value, t = bench.job_throughput(1e6 * (rank + 1), 10.0 * (rank + 1), world)
+    q.put((rank, spec.seed, value, t))
+    dist.destroy_process_group()
+
+
+def test_srla_arm_job_throughput_gloo():
+    """The srla arm's rank logic: every rank its own trace seed (independent links), the job's
+    value = all ranks' packets over the slowest rank's time, the same on every rank."""
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_job_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = {r: (seed, v, t) for r, seed, v, t in (q.get(timeout=120) for _ in procs)}
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert got[0][0] != got[1][0]
+    for r in (0, 1):
+        seed, value, t = got[r]
+        assert t == 20.0 and abs(value - 3e6 / 20e-3 / 1e6) < 1e-9
+
+
 def test_reference_arm_under_torchrun_prints_once():
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",

@@ -105,8 +105,8 @@ def _algorithmic_bytes_per_pkt(w, tau):
 # capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel sources it was taken on.
 SCAN_TRAFFIC = {
-    "sources": "c0b046b4b67206a2",
-    "paper-1link-u8-v16384-g128-gl256-z16-k300-5Mpps": {"bytes_per_launch": 103.776768e6 + 55.736576e6,
+    "sources": "ccc22d14685f6528",
+    "paper-1link-u8-v16384-g128-gl256-z16-k300-5Mpps": {"bytes_per_launch": 103.811584e6 + 56.599808e6,
                                                          "pkts": 5_000_000},
 }
 

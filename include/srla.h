@@ -132,8 +132,10 @@ typedef struct srla_slice_stats {
   uint64_t n_scanned_sampled; /* of which sampled: their u SRE recorders set as well */
   uint64_t n_set_probes;     /* insertions tried into the slice's set of sampled hosts (one
                                 per distinct host of a warp's sampled pairs) */
-  uint64_t n_heavy_events;   /* of which hosts with two or more sampled pairs in one warp's
-                                batch of 32 scanned pairs */
+  uint64_t n_heavy_events;   /* of which hosts with three or more sampled pairs in one
+                                warp's batch of 32 scanned pairs (heavy hosts: the next slice
+                                takes the heavy build when they occur in at least 1/8 of the
+                                batches) */
 } srla_slice_stats;
 
 typedef struct srla_s srla_t;

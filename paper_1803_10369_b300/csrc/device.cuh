@@ -56,11 +56,14 @@ struct Ctl {
   unsigned int n_miss;            // block-table misses of the open slice that claimed a pair-table slot
   unsigned int n_gdup;            // of which the per-slice pair table found already scanned
   unsigned int heavy_mode;        // 1: the scan blocks track one heavy host each (HeavyTrack)
+  unsigned int sat_hint;          // bit 0 / 1: this slice's census sweep records saturated SLE /
+                                  // SRE estimators (the previous slice was nearly saturated)
   double up;                      // UP of Eq. 8 for the open slice (set at its end)
   unsigned long long n_scan;      // pairs of the open slice scanned (their SLE recorders set)
   unsigned long long n_scan_samp; // of which sampled (their SRE recorders set too)
   unsigned long long n_probe;     // sampled-host set insertions tried (one probe load each)
-  unsigned long long n_heavy;     // heavy events (two or more sampled lanes of one host in a drain)
+  unsigned long long n_heavy;     // heavy events (three or more sampled lanes of one host in a drain)
+  unsigned long long sre_post;    // SRE recorders inside the post-slide window (age + 1 < k), all rows
   unsigned long long census[SRLA_MAX_ROWS];
 };
 

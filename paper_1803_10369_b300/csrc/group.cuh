@@ -32,6 +32,9 @@ struct LinkDesc {
   uint32_t* lut_flags;
   srla_slice_stats* st[2];
   unsigned long long* ptab;  // per-slice pair table, or null
+  uint8_t* le_sat;           // saturated-estimator bytes of the SLE / SRE (see sat_mark), or null
+  uint8_t* re_sat;
+  uint32_t le_spv, re_spv;   // vectors per run when those bytes are recorded, else 0
 };
 
 constexpr int kGroupSeenLog2 = 12;  // pairs remembered per group scan block (several per SM)
@@ -165,11 +168,13 @@ __global__ void __launch_bounds__(kThreads, kThreads >= 512 ? 1 : 768 / kThreads
   __shared__ ScanTask stask;
   __shared__ unsigned s_task;
   __shared__ HeavyTrack s_heavy;
+  __shared__ unsigned s_cnt[6];
   volatile unsigned long long* seen = seen_mem;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const unsigned n_tasks = thdr->n_tasks;
   for (;;) {
     if (threadIdx.x == 0) s_task = atomicAdd(&gctl->next_task, 1u);
+    if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0u;
     __syncthreads();
     const unsigned ti = s_task;
     if (ti >= n_tasks) break;
@@ -217,7 +222,7 @@ __global__ void __launch_bounds__(kThreads, kThreads >= 512 ? 1 : 768 / kThreads
           group_scan_task<CellT, false, false, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
       }
     });
-    scan_count_flush(sc, ctl, lane);
+    scan_count_flush(sc, ctl, s_cnt, lane);
     __syncthreads();
   }
 }
@@ -234,12 +239,16 @@ __device__ __forceinline__ void group_sweep_chunk(const SweepChunk& c, const Lin
   const uint32_t tm = ctl->tm, P = D.geo.P;
   const uint32_t alias = 1u + (after_close ? tm : ((tm + 1u == P) ? 0u : tm + 1u));
   const uint32_t asplat = splat<CellT>(alias);
-  const bool count = is_le && !after_close;
+  // SLE rows: the census; SRE rows: the recorders inside the post-slide window (see k_sweep)
+  const bool count = !after_close && (is_le || !kIsBit<CellT>);
   const bool reset = after_close ? true : !D.k_is_P;
-  const SweepWin sw = make_sweep_win<CellT>(tm, P, D.geo.k);
+  const SweepWin sw = make_sweep_win<CellT>(tm, P, is_le ? D.geo.k : D.geo.k - 1u);
   const size_t nvec = c.count;
-  uint32_t cnt = sw.wrap ? sweep_part<CellT, true>(base, nvec, threadIdx.x, blockDim.x, count, reset, sw, alias, asplat)
-                         : sweep_part<CellT, false>(base, nvec, threadIdx.x, blockDim.x, count, reset, sw, alias, asplat);
+  const uint32_t hint = ctl->sat_hint;
+  const uint32_t spv = !count ? 0u : is_le ? ((hint & 1u) ? D.le_spv : 0u) : ((hint & 2u) ? D.re_spv : 0u);
+  uint8_t* sat_row = spv ? (is_le ? D.le_sat : D.re_sat) + (size_t)c.row * D.geo.v : nullptr;
+  uint32_t cnt = sweep_any<CellT>(base, nvec, threadIdx.x, blockDim.x, count, reset, sw, alias, asplat, sat_row, spv,
+                                  c.begin);
   if (count) {
     __shared__ uint32_t part[32];
     cnt = warp_sum(cnt);
@@ -248,7 +257,7 @@ __device__ __forceinline__ void group_sweep_chunk(const SweepChunk& c, const Lin
     if (threadIdx.x == 0) {
       unsigned long long s = 0;
       for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += part[w];
-      atomicAdd(&ctl->census[c.row], s);
+      atomicAdd(is_le ? &ctl->census[c.row] : &ctl->sre_post, s);
     }
     __syncthreads();
   }
@@ -266,7 +275,7 @@ __device__ __forceinline__ unsigned link_of(const uint32_t* off, unsigned nl, ui
   return lo;
 }
 
-__global__ void __launch_bounds__(256) kg_sweep(const LinkDesc* __restrict__ descs, const GroupCtl* __restrict__ gctl,
+__global__ void __launch_bounds__(256, 4) kg_sweep(const LinkDesc* __restrict__ descs, const GroupCtl* __restrict__ gctl,
                                                 int post) {
   const unsigned n = post ? gctl->n_post : gctl->n_chunks;
   const SweepChunk* __restrict__ chunks = post ? gctl->post : gctl->chunks;
@@ -468,6 +477,18 @@ __device__ __forceinline__ void group_estimate_one(const LinkDesc& D, uint32_t i
   const int par = (int)(T & 1);
   const uint32_t aip = D.clist[par][idx];
   const uint32_t mycol = (uint32_t)lane < D.geo.u ? hash61(D.coef.a[lane], D.coef.b[lane], aip) & D.geo.vmask : 0u;
+  // saturated sketches skip the gathers exactly (see k_estimate)
+  bool le_full = true;
+  unsigned long long min_census = ~0ull;
+  for (uint32_t i = 0; i < D.geo.u; i++) {
+    le_full &= ctl->census[i] == (unsigned long long)D.geo.v * D.geo.gl;
+    min_census = min(min_census, ctl->census[i]);
+  }
+  const bool re_full = ctl->sre_post == (unsigned long long)D.geo.u * D.geo.v * D.geo.g;
+  const uint32_t hint = ctl->sat_hint;
+  const bool le_map = !le_full && D.le_spv && (hint & 1u) && 16ull * min_census >= 15ull * D.geo.v * D.geo.gl;
+  const bool re_map = !re_full && D.re_spv && (hint & 2u) && !D.k_is_P &&
+                      16ull * ctl->sre_post >= 15ull * D.geo.u * D.geo.v * D.geo.g;
   if (est) {
     uint32_t origin = 0;
     if (lane == 0) {  // issued before the gather, used after it
@@ -475,7 +496,10 @@ __device__ __forceinline__ void group_estimate_one(const LinkDesc& D, uint32_t i
       origin = (s != 0xFFFFFFFFu) ? D.cflags[par][s] : 0u;
     }
     const Win win = make_win<CellT>(ctl->tm, D.geo.P, D.geo.k);
-    const uint32_t w = union_count<CellT>(static_cast<const CellT*>(D.le), D.geo.v, D.geo.gl, D.geo.u, mycol, win, lane);
+    const bool sat = le_full || (le_map && host_saturated(D.le_sat, D.geo.v, D.geo.u, mycol, lane));
+    const uint32_t w =
+        sat ? D.geo.gl
+            : union_count<CellT>(static_cast<const CellT*>(D.le), D.geo.v, D.geo.gl, D.geo.u, mycol, win, lane);
     if (lane == 0) {
       srla_entry e;
       e.aip = aip;
@@ -487,8 +511,10 @@ __device__ __forceinline__ void group_estimate_one(const LinkDesc& D, uint32_t i
     return;
   }
   const Win win_post = make_win<CellT>(ctl->tm, D.geo.P, D.geo.k - 1u);
+  const bool sat = re_full || (re_map && host_saturated(D.re_sat, D.geo.v, D.geo.u, mycol, lane));
   const uint32_t cw =
-      union_count<CellT>(static_cast<const CellT*>(D.re), D.geo.v, D.geo.g, D.geo.u, mycol, win_post, lane);
+      sat ? D.geo.g
+          : union_count<CellT>(static_cast<const CellT*>(D.re), D.geo.v, D.geo.g, D.geo.u, mycol, win_post, lane);
   if (lane == 0 && cw >= D.geo.rho_g) {
     uint32_t slot;
     const int r = set_insert(D.ctab[par ^ 1], D.cmask, slice_tag(T + 1), aip, &slot);

@@ -42,7 +42,9 @@ inline uint64_t next_pow2(uint64_t x) {
 
 struct Layout {
   size_t ctl, re, le, staging, utab, ulist, ctab[2], cflags[2], clist[2], sort_tmp, sort_hist, lut_est,
-      lut_flags, rep_stats[2], rep_entries[2], ptab[2], si[2], total;
+      lut_flags, rep_stats[2], rep_entries[2], ptab[2], si[2], le_sat, re_sat, total;
+  uint32_t le_spv, re_spv;  // 16-byte vectors per SLE / SRE run when the sweep records
+                            // saturated estimators (one byte each, u*v per array); 0: not recorded
   uint64_t staging_pkts;
   uint32_t umask, cmask, ntiles, pmask;
   bool pairs;   // per-slice pair table present
@@ -92,6 +94,17 @@ inline int check(const srla_params* p) {
   return SRLA_OK;
 }
 
+// Vectors of 16 bytes per run of `cells` 8/16-bit recorders when the sweep can record the
+// saturated estimators of an array (the run is a power of two of at most 32 vectors and a row
+// is a whole number of 32-vector warp steps), else 0.
+inline uint32_t sat_spv(const srla_params* p, uint32_t cells) {
+  if (!p->dr_bytes) return 0;
+  const uint64_t bytes = (uint64_t)cells * p->dr_bytes;
+  if (bytes % 16 || bytes / 16 == 0 || bytes / 16 > 32) return 0;
+  const uint32_t spv = (uint32_t)(bytes / 16);
+  return ((uint64_t)p->v * spv) % 32 == 0 ? spv : 0;
+}
+
 // n_pair_tables: 2 for a single link (the next slice's table is cleared while one slice is
 // closed), 1 for a group link (the group sweep clears it).
 inline Layout layout_of(const srla_params* p, int n_pair_tables = 2) {
@@ -135,6 +148,10 @@ inline Layout layout_of(const srla_params* p, int n_pair_tables = 2) {
   for (int q = 0; q < 2; q++) L.ptab[q] = take(q < L.n_ptab ? ((size_t)1 << plog) * 8 : 0);
   // inline mode: one 32-bit word of super point indicator bits per estimator, by parity
   for (int q = 0; q < 2; q++) L.si[q] = take(p->mode == SRLA_MODE_INLINE ? (size_t)p->u * p->v * 4 : 0);
+  L.le_spv = sat_spv(p, p->gl);
+  L.re_spv = sat_spv(p, p->g);
+  L.le_sat = take(L.le_spv ? (size_t)p->u * p->v : 0);
+  L.re_sat = take(L.re_spv ? (size_t)p->u * p->v : 0);
   L.total = off;
   return L;
 }

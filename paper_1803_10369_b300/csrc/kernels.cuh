@@ -28,6 +28,8 @@ __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, k
                                                           const __grid_constant__ InlineArgs ia) {
   extern __shared__ unsigned long long scan_smem[];
   __shared__ HeavyTrack s_heavy;
+  __shared__ unsigned s_cnt[6];
+  if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0u;
   volatile unsigned long long* seen = scan_smem;
   auto queue_mem = reinterpret_cast<unsigned long long(*)[2][kQueue]>(scan_smem + (kInline ? 0 : kSeen));
   if (!kInline)
@@ -98,7 +100,7 @@ __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, k
   while (Q.n2)
     drain_scan<CellT, kInline, kElide, kHeavy>(Q, sc, geo, coef, code, re, le, ctl, utab, umask, ulist, umax, tag, lane,
                                                hv, &ia, &win);
-  scan_count_flush(sc, ctl, lane);
+  scan_count_flush(sc, ctl, s_cnt, lane);
 }
 
 // One streaming pass over the recorders: census and stamp ageing.  Each block sweeps one
@@ -109,7 +111,9 @@ __global__ void __launch_bounds__(kInline ? kScanThreadsInline : kScanThreads, k
 template <typename CellT>
 __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, CellT* __restrict__ le,
                                                Ctl* __restrict__ ctl, int do_census, int do_reset,
-                                               int after_close, uint32_t gx_le, uint32_t gx_re) {
+                                               int after_close, uint32_t gx_le, uint32_t gx_re,
+                                               uint8_t* __restrict__ le_sat, uint8_t* __restrict__ re_sat,
+                                               uint32_t le_spv, uint32_t re_spv) {
   const bool census = do_census != 0;
   const bool reset = do_reset != 0;
   const uint32_t n_le_blocks = (census || reset) ? geo.u * gx_le : 0u;
@@ -118,7 +122,10 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
   const uint32_t gx = is_le ? gx_le : gx_re;
   const uint32_t row = b / gx, part = b % gx;
   if (row >= geo.u) return;
-  const bool count = is_le && census;
+  // SLE rows: the census (in-window recorders at the open slice); SRE rows (present when the
+  // sweep ages them): the recorders inside the window after the slide (age + 1 < k), which
+  // lets the estimate skip the carry gathers when every SRE recorder passes
+  const bool count = census && (is_le || !kIsBit<CellT>);
   const size_t cells = (size_t)geo.v * (is_le ? geo.gl : geo.g);
   uint4* base = reinterpret_cast<uint4*>(words_at<CellT>(is_le ? le : re, (size_t)row * cells));
   const size_t nvec = cell_array_bytes<CellT>(cells) / 16;
@@ -126,11 +133,14 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
   // stamp of the slice that opens next: after the slice was closed, that is the open slice
   const uint32_t alias = 1u + (after_close ? tm : ((tm + 1u == P) ? 0u : tm + 1u));
   const uint32_t asplat = splat<CellT>(alias);
-  const SweepWin sw = make_sweep_win<CellT>(tm, P, geo.k);
+  const SweepWin sw = make_sweep_win<CellT>(tm, P, is_le ? geo.k : geo.k - 1u);
   const size_t stride = (size_t)gx * blockDim.x;
   const size_t x = (size_t)part * blockDim.x + threadIdx.x;
-  uint32_t cnt = sw.wrap ? sweep_part<CellT, true>(base, nvec, x, stride, count, reset, sw, alias, asplat)
-                         : sweep_part<CellT, false>(base, nvec, x, stride, count, reset, sw, alias, asplat);
+  // saturated-estimator bytes only when the previous slice was nearly saturated (sat_hint)
+  const uint32_t hint = ctl->sat_hint;
+  const uint32_t spv = !count ? 0u : is_le ? ((hint & 1u) ? le_spv : 0u) : ((hint & 2u) ? re_spv : 0u);
+  uint8_t* sat_row = spv ? (is_le ? le_sat : re_sat) + (size_t)row * geo.v : nullptr;
+  uint32_t cnt = sweep_any<CellT>(base, nvec, x, stride, count, reset, sw, alias, asplat, sat_row, spv, 0);
   if (count) {
     __shared__ uint32_t part_sum[8];
     cnt = warp_sum(cnt);
@@ -139,7 +149,7 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
     if (threadIdx.x == 0) {
       unsigned long long s = 0;
       for (int w = 0; w < (int)(blockDim.x >> 5); w++) s += part_sum[w];
-      atomicAdd(&ctl->census[row], s);
+      atomicAdd(is_le ? &ctl->census[row] : &ctl->sre_post, s);
     }
   }
 }
@@ -220,7 +230,8 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
                                                   srla_slice_stats* st1, uint32_t umax,
                                                   const float* __restrict__ lut_est,
                                                   const uint32_t* __restrict__ lut_flags, uint32_t* si0,
-                                                  uint32_t* si1) {
+                                                  uint32_t* si1, const uint8_t* __restrict__ le_sat,
+                                                  const uint8_t* __restrict__ re_sat, uint32_t sat_maps) {
   __shared__ int s_last;
   const unsigned long long T = ctl->T;
   const int par = (int)(T & 1);
@@ -235,6 +246,25 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
   const uint32_t n = min(ctl->cat_count[par], cmax);
   const Win win = make_win<CellT>(ctl->tm, geo.P, geo.k);
   const Win win_post = make_win<CellT>(ctl->tm, geo.P, geo.k - 1u);  // age + 1 < k after the slide
+  // Saturated sketches: when every SLE recorder of every row is inside the window (the
+  // census is v*g' in each row, so UP = 1), every host's union SLE weight is g'; when every
+  // SRE recorder is inside the post-slide window (counted by the sweep), every carry test
+  // passes.  Both are exact, and spare the gathers.
+  bool le_full = true;
+  unsigned long long min_census = ~0ull;
+  for (uint32_t i = 0; i < geo.u; i++) {
+    le_full &= ctl->census[i] == (unsigned long long)geo.v * geo.gl;
+    min_census = min(min_census, ctl->census[i]);
+  }
+  const bool re_full = ctl->sre_post == (unsigned long long)geo.u * geo.v * geo.g;
+  // Nearly saturated sketches (at least 15/16 of the recorders inside the window): the
+  // per-estimator bytes of the sweep (sat_mark) spare the gathers of hosts whose u estimators
+  // are all saturated.  The SRE bytes exist when the census sweep aged the SRE (k < 2^z - 1).
+  // (only in slices whose census sweep recorded them: sat_hint, set by the previous close)
+  const uint32_t hint = ctl->sat_hint;
+  const bool le_map = !le_full && (sat_maps & hint & 1u) && 16ull * min_census >= 15ull * geo.v * geo.gl;
+  const bool re_map = !re_full && (sat_maps & hint & 2u) && geo.k != geo.P &&
+                      16ull * ctl->sre_post >= 15ull * geo.u * geo.v * geo.g;
   const int lane = threadIdx.x & 31;
   const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
@@ -252,7 +282,8 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
         const uint32_t s = set_find(ctab, cmask, tag, aip);
         origin = (s != 0xFFFFFFFFu) ? cflags[s] : 0u;
       }
-      const uint32_t w = union_count<CellT>(le, geo.v, geo.gl, geo.u, mycol, win, lane);
+      const bool sat = le_full || (le_map && host_saturated(le_sat, geo.v, geo.u, mycol, lane));
+      const uint32_t w = sat ? geo.gl : union_count<CellT>(le, geo.v, geo.gl, geo.u, mycol, win, lane);
       if (lane == 0) {
         srla_entry e;
         e.aip = aip;
@@ -263,7 +294,8 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
       }
       continue;
     }
-    const uint32_t cw = union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, win_post, lane);
+    const bool sat = re_full || (re_map && host_saturated(re_sat, geo.v, geo.u, mycol, lane));
+    const uint32_t cw = sat ? geo.g : union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, win_post, lane);
     if (cw < geo.rho_g) continue;
     // inline mode: a carried host gets its SI bits in the next slice's indicators (Algorithm 3)
     uint32_t* si_next = par ? si0 : si1;
@@ -303,11 +335,12 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
         const uint32_t s = set_find(ctab, cmask, tag, my_aip);
         origin = (s != 0xFFFFFFFFu) ? cflags[s] : 0u;
       }
-      uint32_t my_w = 0;
-      for (uint32_t j = 0; j < m; j++) {
+      uint32_t my_w = geo.gl;
+      for (uint32_t j = 0; j < m && !le_full; j++) {
         const uint32_t aip = __shfl_sync(kFull, my_aip, (int)j);
         const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
-        const uint32_t w = union_count<CellT>(le, geo.v, geo.gl, geo.u, mycol, win, lane);
+        const bool sat = le_map && host_saturated(le_sat, geo.v, geo.u, mycol, lane);
+        const uint32_t w = sat ? geo.gl : union_count<CellT>(le, geo.v, geo.gl, geo.u, mycol, win, lane);
         if ((uint32_t)lane == j) my_w = w;
       }
       if (mine) {
@@ -326,7 +359,8 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
     for (uint32_t j = 0; j < m; j++) {
       const uint32_t aip = __shfl_sync(kFull, my_aip, (int)j);
       const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
-      const uint32_t cw = union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, win_post, lane);
+      const bool sat = re_full || (re_map && host_saturated(re_sat, geo.v, geo.u, mycol, lane));
+      const uint32_t cw = sat ? geo.g : union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, win_post, lane);
       if ((uint32_t)lane == j) pass = cw >= geo.rho_g;
       if (cw >= geo.rho_g && si_next && (uint32_t)lane < geo.u)
         atomicOr(si_next + (size_t)lane * geo.v + mycol, 1u << si_bit(coef, geo.u, aip));

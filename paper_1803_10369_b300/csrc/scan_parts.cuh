@@ -64,9 +64,12 @@ __device__ __forceinline__ bool pair_claim_from(unsigned long long* __restrict__
 // this launch (u*g' + u*g bits in shared memory) and stores each recorder once; a stamped
 // recorder keeps the slice's stamp until the slice ends (no other writer changes it), so the
 // skipped stores are exact.  The heavy_mode hint comes from the sampled-host insertion,
-// which already groups a warp's sampled lanes by host: a group of two or more sampled lanes
-// of one host is a heavy event; heavy_mode is set for the next slice when heavy events occur
-// in at least 1/16 of the 32-pair scan drains.
+// which already groups a warp's sampled lanes by host: a group of three or more sampled
+// lanes of one host (about 4 of a drain's 32 pairs are sampled at the paper's rate, so such a
+// host holds a large share of the slice's scanned pairs) is a heavy event; heavy_mode is set
+// for the next slice when heavy events occur in at least 1/8 of the 32-pair scan drains.
+// Weaker signals switched the heavy build on for small links whose busiest host has only a
+// few hundred pairs, where the tracking costs more than it saves.
 constexpr int kHeavyLanes = 4;
 constexpr uint32_t kHeavyLeBits = 4096;  // u * g' recorders a block can track
 constexpr uint32_t kHeavyReBits = 2048;  // u * g recorders a block can track
@@ -217,7 +220,7 @@ __device__ __forceinline__ unsigned scan_dense(uint32_t aip, uint32_t bip, bool 
     if ((peers & ((1u << lane) - 1u)) == 0) {
       uint32_t slot;
       sc.probe++;
-      sc.heavy += __popc(peers) >= 2 ? 1u : 0u;  // a heavy event (see HeavyTrack)
+      sc.heavy += __popc(peers) >= 3 ? 1u : 0u;  // a heavy event (see HeavyTrack)
       r = set_insert(utab, umask, tag, aip, &slot);
       if (r < 0) atomicOr(&ctl->overflow, 1u);
     }
@@ -385,29 +388,27 @@ __device__ __forceinline__ void drain_claim(ScanQueues& Q, ScanCount& sc, unsign
                                              hv);
 }
 
-// The block's scan counters into the control block: one reduction per block (all threads
-// of the block call it), one atomic per counter.
-__device__ __forceinline__ void scan_count_flush(ScanCount sc, Ctl* __restrict__ ctl, int lane) {
-  __shared__ unsigned s_cnt[6];
-  __syncthreads();
-  if (threadIdx.x < 6) s_cnt[threadIdx.x] = 0;
-  __syncthreads();
+// The block's scan counters into the control block: one shared-memory sum per block, one
+// global atomic per nonzero counter.  `acc` (6 words) is zeroed by the caller before a
+// barrier that precedes the scan; all threads of the block call this; the caller
+// synchronises again before it reuses `acc`.
+__device__ __forceinline__ void scan_count_flush(ScanCount sc, Ctl* __restrict__ ctl, unsigned* acc, int lane) {
   // miss, gdup, probe and heavy are per lane; scan and samp are the warp's totals in every lane
   const uint32_t v[6] = {warp_sum(sc.miss), warp_sum(sc.gdup), sc.scan, sc.samp, warp_sum(sc.probe),
                          warp_sum(sc.heavy)};
   if (lane == 0) {
 #pragma unroll
     for (int i = 0; i < 6; i++)
-      if (v[i]) atomicAdd(&s_cnt[i], v[i]);
+      if (v[i]) atomicAdd(&acc[i], v[i]);
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    if (s_cnt[0]) atomicAdd(&ctl->n_miss, s_cnt[0]);
-    if (s_cnt[1]) atomicAdd(&ctl->n_gdup, s_cnt[1]);
-    if (s_cnt[2]) atomicAdd(&ctl->n_scan, (unsigned long long)s_cnt[2]);
-    if (s_cnt[3]) atomicAdd(&ctl->n_scan_samp, (unsigned long long)s_cnt[3]);
-    if (s_cnt[4]) atomicAdd(&ctl->n_probe, (unsigned long long)s_cnt[4]);
-    if (s_cnt[5]) atomicAdd(&ctl->n_heavy, (unsigned long long)s_cnt[5]);
+    if (acc[0]) atomicAdd(&ctl->n_miss, acc[0]);
+    if (acc[1]) atomicAdd(&ctl->n_gdup, acc[1]);
+    if (acc[2]) atomicAdd(&ctl->n_scan, (unsigned long long)acc[2]);
+    if (acc[3]) atomicAdd(&ctl->n_scan_samp, (unsigned long long)acc[3]);
+    if (acc[4]) atomicAdd(&ctl->n_probe, (unsigned long long)acc[4]);
+    if (acc[5]) atomicAdd(&ctl->n_heavy, (unsigned long long)acc[5]);
   }
 }
 
@@ -498,12 +499,13 @@ __device__ __forceinline__ uint32_t clear_stamp(uint32_t word, uint32_t alias) {
   return word;
 }
 
+// Returns the number of cells of the vector inside the window (0 when not counting).
 template <typename CellT, bool kWrap>
-__device__ __forceinline__ void sweep_vec(uint4* base, size_t x, uint4 q, bool count, bool reset, const SweepWin& sw,
-                                          uint32_t alias, uint32_t asplat, uint32_t& cnt) {
-  if (count)
-    cnt += count_in_window<CellT, kWrap>(q.x, sw) + count_in_window<CellT, kWrap>(q.y, sw) +
-           count_in_window<CellT, kWrap>(q.z, sw) + count_in_window<CellT, kWrap>(q.w, sw);
+__device__ __forceinline__ uint32_t sweep_vec(uint4* base, size_t x, uint4 q, bool count, bool reset,
+                                              const SweepWin& sw, uint32_t alias, uint32_t asplat) {
+  const uint32_t n4 = count ? count_in_window<CellT, kWrap>(q.x, sw) + count_in_window<CellT, kWrap>(q.y, sw) +
+                                  count_in_window<CellT, kWrap>(q.z, sw) + count_in_window<CellT, kWrap>(q.w, sw)
+                            : 0u;
   if (reset && (has_stamp<CellT>(q.x, asplat) | has_stamp<CellT>(q.y, asplat) | has_stamp<CellT>(q.z, asplat) |
                 has_stamp<CellT>(q.w, asplat))) {
     uint4 r;
@@ -513,23 +515,90 @@ __device__ __forceinline__ void sweep_vec(uint4* base, size_t x, uint4 q, bool c
     r.w = clear_stamp<CellT>(q.w, alias);
     base[x] = r;
   }
+  return n4;
+}
+
+// Saturated estimators.  While it counts, the sweep also records, one byte per estimator
+// (row i, column c) of the array, whether all of its recorders are inside the counted
+// window (SLE: the census window; SRE: the post-slide window of the carry test).  A host
+// whose u estimators are all saturated has a union count equal to the run length, so the
+// estimate and the carry test need not gather its recorders.  Recorded when a run is a
+// power-of-two number spv <= 32 of 16-byte vectors and the row is a whole number of warps'
+// vectors: then each warp step of the sweep covers 32/spv whole runs, and the first lane of
+// each run writes its byte (every byte is rewritten at every sweep, so no clearing).  `vx` is
+// this lane's vector index within the row; all 32 lanes of the warp call it together.
+template <typename CellT>
+__device__ __forceinline__ void sat_mark(uint8_t* __restrict__ sat_row, uint32_t spv, size_t vx, uint32_t n4) {
+  constexpr uint32_t kCellsPerVec = 16u / (uint32_t)sizeof(CellT);
+  const unsigned full = __ballot_sync(kFull, n4 == kCellsPerVec);
+  const uint32_t lane = threadIdx.x & 31u;
+  if ((lane & (spv - 1u)) == 0u) {
+    const uint32_t m = spv == 32u ? kFull : ((1u << spv) - 1u);
+    sat_row[vx / spv] = ((full >> lane) & m) == m ? 1u : 0u;
+  }
 }
 
 // One block's part of one row: grid-stride over the row's vectors from `x`, four loads in
-// flight per thread.
-template <typename CellT, bool kWrap>
+// flight per thread.  kSat: also record the row's saturated-estimator bytes in sat_row (see
+// sat_mark; a separate instantiation, so the plain sweep carries none of it); vbase is the
+// row index of base[0], in vectors.
+template <typename CellT, bool kWrap, bool kSat>
 __device__ __forceinline__ uint32_t sweep_part(uint4* base, size_t nvec, size_t x, size_t stride, bool count,
-                                               bool reset, const SweepWin& sw, uint32_t alias, uint32_t asplat) {
+                                               bool reset, const SweepWin& sw, uint32_t alias, uint32_t asplat,
+                                               uint8_t* sat_row, uint32_t spv, size_t vbase) {
   uint32_t cnt = 0;
   for (; x + 3 * stride < nvec; x += 4 * stride) {
     uint4 q[4];
 #pragma unroll
     for (int j = 0; j < 4; j++) q[j] = base[x + j * stride];
 #pragma unroll
-    for (int j = 0; j < 4; j++) sweep_vec<CellT, kWrap>(base, x + j * stride, q[j], count, reset, sw, alias, asplat, cnt);
+    for (int j = 0; j < 4; j++) {
+      const uint32_t n4 = sweep_vec<CellT, kWrap>(base, x + j * stride, q[j], count, reset, sw, alias, asplat);
+      cnt += n4;
+      if constexpr (kSat && !kIsBit<CellT>) sat_mark<CellT>(sat_row, spv, vbase + x + j * stride, n4);
+    }
   }
-  for (; x < nvec; x += stride) sweep_vec<CellT, kWrap>(base, x, base[x], count, reset, sw, alias, asplat, cnt);
+  for (; x < nvec; x += stride) {
+    const uint32_t n4 = sweep_vec<CellT, kWrap>(base, x, base[x], count, reset, sw, alias, asplat);
+    cnt += n4;
+    if constexpr (kSat && !kIsBit<CellT>) sat_mark<CellT>(sat_row, spv, vbase + x, n4);
+  }
   return cnt;
+}
+
+// The four forms of sweep_part (window wrapped or not, saturated-estimator bytes or not).
+template <typename CellT>
+__device__ __forceinline__ uint32_t sweep_any(uint4* base, size_t nvec, size_t x, size_t stride, bool count,
+                                              bool reset, const SweepWin& sw, uint32_t alias, uint32_t asplat,
+                                              uint8_t* sat_row, uint32_t spv, size_t vbase) {
+  if (sat_row)
+    return sw.wrap ? sweep_part<CellT, true, true>(base, nvec, x, stride, count, reset, sw, alias, asplat, sat_row, spv,
+                                                   vbase)
+                   : sweep_part<CellT, false, true>(base, nvec, x, stride, count, reset, sw, alias, asplat, sat_row,
+                                                    spv, vbase);
+  return sw.wrap ? sweep_part<CellT, true, false>(base, nvec, x, stride, count, reset, sw, alias, asplat, nullptr, 0, 0)
+                 : sweep_part<CellT, false, false>(base, nvec, x, stride, count, reset, sw, alias, asplat, nullptr, 0,
+                                                   0);
+}
+
+// Hint for the next slice's sweep: record saturated estimators when at least 15/16 of the
+// SLE recorders of every row (bit 0), or of all SRE recorders in the post-slide window with
+// k < 2^z - 1 (bit 1), were inside the window in this slice.
+__device__ __forceinline__ uint32_t sat_hint_of(const Geo& geo, const Ctl& c) {
+  unsigned long long min_census = ~0ull;
+  for (uint32_t i = 0; i < geo.u; i++) min_census = min(min_census, c.census[i]);
+  const bool le = 16ull * min_census >= 15ull * geo.v * geo.gl;
+  const bool re = geo.k != geo.P && 16ull * c.sre_post >= 15ull * geo.u * geo.v * geo.g;
+  return (le ? 1u : 0u) | (re ? 2u : 0u);
+}
+
+// True if every estimator of the host (lane i < u holds its column of row i) is marked
+// saturated in the byte map `sat` (u rows of v bytes).  All lanes call it.
+__device__ __forceinline__ bool host_saturated(const uint8_t* __restrict__ sat, uint32_t v, uint32_t u,
+                                               uint32_t mycol, int lane) {
+  const bool mine = (uint32_t)lane < u;
+  const bool s = !mine || __ldcg(sat + (size_t)lane * v + mycol) != 0;
+  return __all_sync(kFull, s);
 }
 
 // ---------------------------------------------------------------- state export
@@ -655,10 +724,12 @@ __device__ __forceinline__ void close_slice(const Geo& geo, Ctl* __restrict__ ct
   n.n_scan = 0;
   n.n_scan_samp = 0;
   n.n_probe = 0;
-  // heavy-host tracking for the next slice: heavy events in at least 1/16 of the slice's
+  // heavy-host tracking for the next slice: heavy events in at least 1/8 of the slice's
   // 32-pair scan drains (n_scan / 32 of them)
-  n.heavy_mode = (c.n_scan > 0 && 512ull * c.n_heavy >= c.n_scan) ? 1u : 0u;
+  n.heavy_mode = (c.n_scan > 0 && 256ull * c.n_heavy >= c.n_scan) ? 1u : 0u;
   n.n_heavy = 0;
+  n.sat_hint = sat_hint_of(geo, c);
+  n.sre_post = 0;
   *ctl = n;
   __threadfence();
 }

@@ -192,7 +192,8 @@ int launch_sweep(srla_t* h, int census, int reset, int after_close) {
   const uint32_t grid = p.u * (gx_le + gx_re);
   h->launches++;
   k_sweep<CellT><<<grid, 256, 0, h->st>>>(h->geo, h->at<CellT>(h->L.re), h->at<CellT>(h->L.le), h->ctl(), census,
-                                          reset, after_close, gx_le, gx_re);
+                                          reset, after_close, gx_le, gx_re, h->at<uint8_t>(h->L.le_sat),
+                                          h->at<uint8_t>(h->L.re_sat), h->L.le_spv, h->L.re_spv);
   return cuda_err(cudaGetLastError());
 }
 
@@ -290,7 +291,8 @@ int launch_end_slice(srla_t* h, int q) {
       h->at<srla_entry>(L.rep_entries[0]), h->at<srla_entry>(L.rep_entries[1]),
       h->at<srla_slice_stats>(L.rep_stats[0]), h->at<srla_slice_stats>(L.rep_stats[1]), h->p.max_sampled,
       h->at<float>(L.lut_est), h->at<uint32_t>(L.lut_flags), inl ? h->at<uint32_t>(L.si[0]) : nullptr,
-      inl ? h->at<uint32_t>(L.si[1]) : nullptr);
+      inl ? h->at<uint32_t>(L.si[1]) : nullptr, h->at<uint8_t>(L.le_sat), h->at<uint8_t>(L.re_sat),
+      (L.le_spv ? 1u : 0u) | (L.re_spv ? 2u : 0u));
   SRLA_TRY(cudaGetLastError());
   // with k = 2^z - 1 the recorders that saturate are still inside the window of the closed
   // slice, so they are cleared only after the slice was estimated and closed

@@ -227,6 +227,10 @@ LinkDesc make_desc(srla_group_t* g, const Slot& s) {
   D.lut_est = reinterpret_cast<float*>(base + L.lut_est);
   D.lut_flags = reinterpret_cast<uint32_t*>(base + L.lut_flags);
   D.ptab = L.pairs ? reinterpret_cast<unsigned long long*>(base + L.ptab[0]) : nullptr;
+  D.le_spv = L.le_spv;
+  D.re_spv = L.re_spv;
+  D.le_sat = L.le_spv ? reinterpret_cast<uint8_t*>(base + L.le_sat) : nullptr;
+  D.re_sat = L.re_spv ? reinterpret_cast<uint8_t*>(base + L.re_sat) : nullptr;
   return D;
 }
 

@@ -43,7 +43,7 @@ def _links():
         (TINY.replace(z=1, k=1, seed=24, pkts_per_slice=40_000), {}),
         (TINY.replace(dr_bytes=0, z=1, k=1, g=8, gl=256, seed=25, pkts_per_slice=40_000), {}),
         (TINY.replace(z=3, k=6, seed=26, start_slice=5, pkts_per_slice=20_000), {}),
-        (TINY.replace(heavy_frac=0.3, dst_model="pool", pool_max=16, seed=28), {}),  # heavy-host tracking
+        (TINY.replace(heavy_frac=0.3, dst_model="pool", pool_max=16, seed=28, theta=256), {}),  # heavy build
         (many, {}),
     ]
 

@@ -40,8 +40,9 @@ VARIANTS = {
     "slice-wrap-2^64": TINY.replace(start_slice=(1 << 64) - 6),
     "flow-bursts-mean8": TINY.replace(burst_mean=8.0),
     # one source sends 30 % of the packets to random destinations: the scan blocks track it
-    # (heavy-host bitmaps) from the second slice on; pool destinations keep the pair table on
-    "heavy-source": TINY.replace(heavy_frac=0.3, dst_model="pool", pool_max=16),
+    # (heavy-host bitmaps) from the second slice on; pool destinations keep the pair table on,
+    # theta = 256 samples a quarter of the pairs (tau = 2), enough for the heavy-host signal
+    "heavy-source": TINY.replace(heavy_frac=0.3, dst_model="pool", pool_max=16, theta=256),
     # one-bit recorders packed 32 to a word (z = 1, k = 1); runs of 8 and of 4/16 recorders
     # share words, runs of 64 and 1024 span whole words
     "bits-discrete": TINY.replace(dr_bytes=0, z=1, k=1),
@@ -88,7 +89,7 @@ FORCED = {
     "2byte-z12-k-equals-P": TINY.replace(dr_bytes=2, z=12, k=4095),
     "paper-g8": TINY.replace(g=8, gl=256, dr_bytes=2, z=16, k=6),
     "pool-repeats": TINY.replace(dst_model="pool", pool_max=8, z=4, k=6),
-    "heavy-source-uniform": TINY.replace(heavy_frac=0.3, z=5, k=9),
+    "heavy-source-uniform": TINY.replace(heavy_frac=0.3, z=5, k=9, theta=256),
     "heavy-source-2byte": TINY.replace(heavy_frac=0.3, dr_bytes=2, z=16, k=6, gl=256, theta=256),
 }
 
@@ -168,12 +169,16 @@ def test_ragged_pushes_unaligned_host_and_empty_slices(cuda_device):
         assert rg["stats"]["n_pkts"] == pk.shape[0]
 
 
-def test_multi_tile_candidate_sort(cuda_device):
+@pytest.mark.parametrize("g", [64, 1024])
+def test_multi_tile_candidate_sort(g, cuda_device):
     """Tens of thousands of candidates per slice: every sampled host passes a saturated SRE,
-    which drives the multi-tile radix sort and large carried lists."""
+    which drives the multi-tile radix sort and large carried lists.  Every SLE recorder is
+    inside the window (UP = 1), so the estimate takes every union weight as g' without
+    gathering; with g = 64 every SRE recorder is inside the post-slide window too (every carry
+    test passes without gathering), with g = 1024 a few are not (the carry tests gather)."""
     spec = synth.TrafficSpec(seed=11, pkts_per_slice=200_000, n_src=1 << 16, zipf_s=0.6,
                              dst_model="uniform", dst_space=1 << 24)
-    w = synth.Workload(name="many-candidates", u=2, v=64, g=64, gl=64, dr_bytes=1, z=4, k=3, theta=64,
+    w = synth.Workload(name="many-candidates", u=2, v=64, g=g, gl=64, dr_bytes=1, z=4, k=3, theta=64,
                        n_slices=5, traffic=spec, max_sampled=1 << 17, max_candidates=1 << 17)
     o, link = make_pair(w)
     for s in range(w.n_slices):
@@ -183,6 +188,7 @@ def test_multi_tile_candidate_sort(cuda_device):
         ro = o.end_slice()
         rg = link.report(link.end_slice())
         assert ro["n_candidates"] > 3 * 4096
+        assert rg["stats"]["up"] == 1.0  # saturated SLE: the estimate's fast path
         compare_reports(ro, rg, f"slice {s}")
     compare_state(o, link, "end")
 

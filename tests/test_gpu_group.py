@@ -34,6 +34,12 @@ def _links():
         traffic=synth.TrafficSpec(seed=11, pkts_per_slice=200_000, n_src=1 << 16, zipf_s=0.6,
                                   dst_model="uniform", dst_space=1 << 24),
         max_sampled=1 << 17, max_candidates=1 << 17)
+    # rows nearly saturated: the sweep's saturated-estimator bytes are used from slice 2 on
+    nearly = synth.Workload(
+        name="nearly-saturated", u=2, v=256, g=512, gl=256, dr_bytes=1, z=4, k=3, theta=64, n_slices=6,
+        traffic=synth.TrafficSpec(seed=12, pkts_per_slice=200_000, n_src=1 << 16, zipf_s=0.6,
+                                  dst_model="uniform", dst_space=1 << 24),
+        max_sampled=1 << 17, max_candidates=1 << 17)
     return [
         (TINY, {}),
         (TINY.replace(dr_bytes=2, z=16, k=9, theta=128, gl=256, seed=21, pkts_per_slice=30_000), {}),
@@ -45,6 +51,7 @@ def _links():
         (TINY.replace(z=3, k=6, seed=26, start_slice=5, pkts_per_slice=20_000), {}),
         (TINY.replace(heavy_frac=0.3, dst_model="pool", pool_max=16, seed=28, theta=256), {}),  # heavy build
         (many, {}),
+        (nearly, {}),
     ]
 
 
@@ -64,7 +71,7 @@ def _params(w, **over):
     return srla.params_for(w, ha, hb, **over)
 
 
-def _group(n_links=12, arena=1 << 30, max_pkts=4 << 20, max_report=1 << 18):
+def _group(n_links=12, arena=1 << 30, max_pkts=4 << 20, max_report=1 << 19):
     return srla.Group(max_links=n_links, max_pkts=max_pkts, arena_bytes=arena, max_host_pkts=1 << 20,
                       max_report=max_report)
 

@@ -63,7 +63,8 @@ struct Ctl {
   unsigned long long n_scan_samp; // of which sampled (their SRE recorders set too)
   unsigned long long n_probe;     // sampled-host set insertions tried (one probe load each)
   unsigned long long n_heavy;     // heavy events (three or more sampled lanes of one host in a drain)
-  unsigned long long sre_post;    // SRE recorders inside the post-slide window (age + 1 < k), all rows
+  unsigned long long sre_post;    // SRE recorders inside the post-slide window (age + 1 < k), all
+                                  // rows; counted only in slices with sat_hint bit 0
   unsigned long long census[SRLA_MAX_ROWS];
 };
 

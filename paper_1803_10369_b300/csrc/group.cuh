@@ -239,12 +239,13 @@ __device__ __forceinline__ void group_sweep_chunk(const SweepChunk& c, const Lin
   const uint32_t tm = ctl->tm, P = D.geo.P;
   const uint32_t alias = 1u + (after_close ? tm : ((tm + 1u == P) ? 0u : tm + 1u));
   const uint32_t asplat = splat<CellT>(alias);
-  // SLE rows: the census; SRE rows: the recorders inside the post-slide window (see k_sweep)
-  const bool count = !after_close && (is_le || !kIsBit<CellT>);
+  // SLE rows: the census; SRE rows: the recorders inside the post-slide window, when the
+  // previous slice's SLE was nearly saturated (see k_sweep)
+  const uint32_t hint = ctl->sat_hint;
+  const bool count = !after_close && (is_le || (!kIsBit<CellT> && (hint & 1u)));
   const bool reset = after_close ? true : !D.k_is_P;
   const SweepWin sw = make_sweep_win<CellT>(tm, P, is_le ? D.geo.k : D.geo.k - 1u);
   const size_t nvec = c.count;
-  const uint32_t hint = ctl->sat_hint;
   const uint32_t spv = !count ? 0u : is_le ? ((hint & 1u) ? D.le_spv : 0u) : ((hint & 2u) ? D.re_spv : 0u);
   uint8_t* sat_row = spv ? (is_le ? D.le_sat : D.re_sat) + (size_t)c.row * D.geo.v : nullptr;
   uint32_t cnt = sweep_any<CellT>(base, nvec, threadIdx.x, blockDim.x, count, reset, sw, alias, asplat, sat_row, spv,

@@ -123,9 +123,11 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
   const uint32_t row = b / gx, part = b % gx;
   if (row >= geo.u) return;
   // SLE rows: the census (in-window recorders at the open slice); SRE rows (present when the
-  // sweep ages them): the recorders inside the window after the slide (age + 1 < k), which
-  // lets the estimate skip the carry gathers when every SRE recorder passes
-  const bool count = census && (is_le || !kIsBit<CellT>);
+  // sweep ages them), only when the previous slice's SLE was nearly saturated (sat_hint bit
+  // 0): the recorders inside the window after the slide (age + 1 < k), which lets the
+  // estimate skip the carry gathers when every SRE recorder passes
+  const uint32_t hint = ctl->sat_hint;
+  const bool count = census && (is_le || (!kIsBit<CellT> && (hint & 1u)));
   const size_t cells = (size_t)geo.v * (is_le ? geo.gl : geo.g);
   uint4* base = reinterpret_cast<uint4*>(words_at<CellT>(is_le ? le : re, (size_t)row * cells));
   const size_t nvec = cell_array_bytes<CellT>(cells) / 16;
@@ -137,7 +139,6 @@ __global__ void __launch_bounds__(256) k_sweep(Geo geo, CellT* __restrict__ re, 
   const size_t stride = (size_t)gx * blockDim.x;
   const size_t x = (size_t)part * blockDim.x + threadIdx.x;
   // saturated-estimator bytes only when the previous slice was nearly saturated (sat_hint)
-  const uint32_t hint = ctl->sat_hint;
   const uint32_t spv = !count ? 0u : is_le ? ((hint & 1u) ? le_spv : 0u) : ((hint & 2u) ? re_spv : 0u);
   uint8_t* sat_row = spv ? (is_le ? le_sat : re_sat) + (size_t)row * geo.v : nullptr;
   uint32_t cnt = sweep_any<CellT>(base, nvec, x, stride, count, reset, sw, alias, asplat, sat_row, spv, 0);

@@ -632,6 +632,10 @@ def measure_batched(K, W, prefill, dev, n_links=64):
                 g.report_all(g.end_slice())
                 continue
             group_slice(s)()
+        policies = {}
+        for l in ids:  # the aggregation policy the autotuner chose for each link's class
+            name = srla.SCAN_POLICY_NAMES[g.scan_policy(l)]
+            policies[name] = policies.get(name, 0) + 1
         launches0 = g.kernel_launches()
         grp = timed(group_slice, group_latency, "group")
         grp["gpu_launches_per_slice"] = (g.kernel_launches() - launches0) / (K + n_lat)
@@ -661,7 +665,7 @@ def measure_batched(K, W, prefill, dev, n_links=64):
                    "pkts_per_slice": pkts_slice, "prefill_slices": prefill,
                    "dr_bytes": sorted({int(p.dr_bytes) for p in params})},
         "latency_span": LATENCY_SPAN,
-        "scan_autotune": {"block_threads": tuned[0], "packets_per_task": tuned[1]},
+        "scan_autotune": {"block_threads": tuned[0], "packets_per_task": tuned[1], "links_per_policy": policies},
         "per_link_loop": loop,
     })
     return grp

@@ -27,7 +27,8 @@ struct srla_s {
   char* ws;
   cudaStream_t st;
   cudaStream_t st_copy;  // internal stream for report remainders and checkpoints
-  cudaStream_t st_h2d;   // internal stream for host-to-device copies of host batches
+  cudaStream_t st_h2d;   // internal streams for host-to-device copies of host batches, one per
+  cudaStream_t st_h2d2;  // staging half, so that consecutive halves can use two copy engines
   cudaStream_t st_side;  // internal stream: the estimator table beside filter and sort
   cudaStream_t st_d2h;   // internal stream: each slice's report header, after its slice end
   cudaEvent_t ev_fork, ev_join, ev_swept;
@@ -459,7 +460,9 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
     delete h;
     return SRLA_E_CUDA;
   }
-  if (cudaStreamCreateWithFlags(&h->st_h2d, cudaStreamNonBlocking) != cudaSuccess) rc = SRLA_E_CUDA;
+  if (cudaStreamCreateWithFlags(&h->st_h2d, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&h->st_h2d2, cudaStreamNonBlocking) != cudaSuccess)
+    rc = SRLA_E_CUDA;
   if (rc == SRLA_OK && (cudaStreamCreateWithFlags(&h->st_side, cudaStreamNonBlocking) != cudaSuccess ||
                         cudaStreamCreateWithFlags(&h->st_d2h, cudaStreamNonBlocking) != cudaSuccess ||
                         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -516,8 +519,9 @@ int srla_push_packets(srla_t* h, const uint32_t* pairs, uint64_t n_pairs, int on
     if (r == SRLA_OK) h->n_pkts_open += n_pairs;
     return r;
   }
-  // Double-buffered staging: the copy of one half (on the internal copy stream) overlaps
-  // with the scan of the other half (on the caller's stream); events order the reuse.
+  // Double-buffered staging: the copy of one half (on that half's internal copy stream, so
+  // that the copies of consecutive halves may run on two copy engines at once) overlaps with
+  // the scan of the other half (on the caller's stream); events order the reuse.
   uint32_t* staging = h->at<uint32_t>(h->L.staging);
   const uint64_t half = std::max<uint64_t>(2, (h->L.staging_pkts / 2) & ~1ull);
   while (n_pairs) {
@@ -525,9 +529,10 @@ int srla_push_packets(srla_t* h, const uint32_t* pairs, uint64_t n_pairs, int on
     h->stage_cur ^= 1;
     const uint64_t m = std::min<uint64_t>(n_pairs, half);
     uint32_t* dst = staging + 2 * half * (uint64_t)x;
-    if (h->free_pending[x]) SRLA_TRY(cudaStreamWaitEvent(h->st_h2d, h->ev_free[x], 0));
-    SRLA_TRY(cudaMemcpyAsync(dst, pairs, m * 8, cudaMemcpyHostToDevice, h->st_h2d));
-    SRLA_TRY(cudaEventRecord(h->ev_ready[x], h->st_h2d));
+    cudaStream_t cs = x ? h->st_h2d2 : h->st_h2d;
+    if (h->free_pending[x]) SRLA_TRY(cudaStreamWaitEvent(cs, h->ev_free[x], 0));
+    SRLA_TRY(cudaMemcpyAsync(dst, pairs, m * 8, cudaMemcpyHostToDevice, cs));
+    SRLA_TRY(cudaEventRecord(h->ev_ready[x], cs));
     SRLA_TRY(cudaStreamWaitEvent(h->st, h->ev_ready[x], 0));
     const int r = scan(dst, m);
     if (r != SRLA_OK) return r;
@@ -764,6 +769,7 @@ void srla_destroy(srla_t* h) {
     cudaStreamDestroy(h->st_copy);
   }
   if (h->st_h2d) cudaStreamDestroy(h->st_h2d);
+  if (h->st_h2d2) cudaStreamDestroy(h->st_h2d2);
   if (h->st_d2h) {
     cudaStreamSynchronize(h->st_d2h);
     cudaStreamDestroy(h->st_d2h);

@@ -93,9 +93,9 @@ __device__ __forceinline__ void with_cells(uint32_t cell_bytes, F&& f) {
 // The link's aggregation policy for this slice: whether the scan consults the per-slice pair
 // table (the adaptive policies follow the pair_mode the previous slice close chose), and
 // whether it runs the read-first build (8/16-bit recorders only).
-__device__ __forceinline__ bool policy_table(const LinkDesc& D, const Ctl* ctl) {
+__device__ __forceinline__ bool policy_table(const LinkDesc& D, uint32_t pair_mode) {
   const bool adaptive = D.scan_policy == SRLA_SCAN_POLICY_ADAPTIVE || D.scan_policy == SRLA_SCAN_POLICY_ADAPTIVE_RF;
-  return D.ptab && adaptive && ctl->pair_mode;
+  return D.ptab && adaptive && pair_mode;
 }
 
 __device__ __forceinline__ bool policy_read_first(const LinkDesc& D, bool table) {
@@ -106,14 +106,15 @@ __device__ __forceinline__ bool policy_read_first(const LinkDesc& D, bool table)
 template <typename CellT, bool kVec, bool kElide, bool kHeavy>
 __device__ __forceinline__ void group_scan_task(const ScanTask& t, const LinkDesc& D, Ctl* ctl,
                                                 volatile unsigned long long* seen, ScanQueues& Q, int lane, int warp,
-                                                int nwarps, ScanCount& sc, bool table, HeavyTrack* hv) {
+                                                int nwarps, ScanCount& sc, bool table, HeavyTrack* hv, uint32_t tm,
+                                                unsigned long long T) {
   const uint32_t* pairs = reinterpret_cast<const uint32_t*>(t.ptr);
   const uint64_t n = t.n;
   CellT* re = static_cast<CellT*>(D.re);
   CellT* le = static_cast<CellT*>(D.le);
   unsigned long long* ptab = table ? D.ptab : nullptr;
-  const CellT code = stamp_code<CellT>(ctl->tm);
-  const uint32_t tag = slice_tag(ctl->T);
+  const CellT code = stamp_code<CellT>(tm);
+  const uint32_t tag = slice_tag(T);
   const Geo& geo = D.geo;
   const Coef& coef = D.coef;
   for (uint64_t base = (uint64_t)warp * 128; base < n; base += (uint64_t)nwarps * 128) {
@@ -157,9 +158,12 @@ __device__ __forceinline__ void group_scan_task(const ScanTask& t, const LinkDes
 }
 
 // Persistent blocks take scan tasks one at a time; a task is one link's batch, so the block's
-// pair table and the link's parameters (in shared memory) serve the whole task.
-template <int kThreads>
-__global__ void __launch_bounds__(kThreads, kThreads >= 512 ? 1 : 768 / kThreads) kg_scan(const LinkDesc* __restrict__ descs,
+// pair table and the link's parameters (in shared memory) serve the whole task.  kReadFirst
+// adds the read-first build: it needs more registers than the others, so it sits in its own
+// instantiation, and groups whose policies never choose it run the leaner kernel (two
+// 512-thread blocks per SM at 64 registers).
+template <int kThreads, bool kReadFirst>
+__global__ void __launch_bounds__(kThreads, kThreads >= 512 ? 2 : 768 / kThreads) kg_scan(const LinkDesc* __restrict__ descs,
                                                     const TaskHeader* __restrict__ thdr, GroupCtl* __restrict__ gctl) {
   const ScanTask* tasks = reinterpret_cast<const ScanTask*>(thdr + 1);
   __shared__ unsigned long long seen_mem[1 << kGroupSeenLog2];
@@ -192,34 +196,43 @@ __global__ void __launch_bounds__(kThreads, kThreads >= 512 ? 1 : 768 / kThreads
     ScanCount sc{0u, 0u, 0u, 0u, 0u, 0u};
     const bool vec = (stask.ptr & 15ull) == 0;
     Ctl* ctl = sdesc.ctl;
-    const bool table = policy_table(sdesc, ctl);
-    const bool elide = policy_read_first(sdesc, table);
+    // the control block fields of the task, loaded together (one round trip per task)
+    const uint32_t pair_mode = ctl->pair_mode, heavy_mode = ctl->heavy_mode, tm = ctl->tm;
+    const unsigned long long T = ctl->T;
+    const bool table = policy_table(sdesc, pair_mode);
+    const bool elide = kReadFirst && policy_read_first(sdesc, table);
     // the heavy build when the link's previous slice showed heavy hosts (see HeavyTrack)
-    const bool heavy = sdesc.cell_bytes && !elide && ctl->heavy_mode && heavy_fits(sdesc.geo);
+    const bool heavy = sdesc.cell_bytes && !elide && heavy_mode && heavy_fits(sdesc.geo);
     HeavyTrack* hv = heavy ? &s_heavy : nullptr;
     const int nw = kThreads / 32;
     with_cells(sdesc.cell_bytes, [&](auto cell) {
       using CellT = decltype(cell);
       if constexpr (kIsBit<CellT>) {
         if (vec)
-          group_scan_task<CellT, true, false, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
+          group_scan_task<CellT, true, false, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv, tm, T);
         else
-          group_scan_task<CellT, false, false, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
-      } else if (elide) {
-        if (vec)
-          group_scan_task<CellT, true, true, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
-        else
-          group_scan_task<CellT, false, true, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
-      } else if (heavy) {
-        if (vec)
-          group_scan_task<CellT, true, false, true>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
-        else
-          group_scan_task<CellT, false, false, true>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
+          group_scan_task<CellT, false, false, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv, tm, T);
       } else {
-        if (vec)
-          group_scan_task<CellT, true, false, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
-        else
-          group_scan_task<CellT, false, false, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv);
+        if constexpr (kReadFirst) {
+          if (elide) {
+            if (vec)
+              group_scan_task<CellT, true, true, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv, tm, T);
+            else
+              group_scan_task<CellT, false, true, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv, tm, T);
+            return;
+          }
+        }
+        if (heavy) {
+          if (vec)
+            group_scan_task<CellT, true, false, true>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv, tm, T);
+          else
+            group_scan_task<CellT, false, false, true>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv, tm, T);
+        } else {
+          if (vec)
+            group_scan_task<CellT, true, false, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv, tm, T);
+          else
+            group_scan_task<CellT, false, false, false>(stask, sdesc, ctl, seen, Q, lane, warp, nw, sc, table, hv, tm, T);
+        }
       }
     });
     scan_count_flush(sc, ctl, s_cnt, lane);

@@ -103,7 +103,7 @@ struct srla_group_s {
   size_t ws_bytes = 0;
   cudaStream_t st = nullptr, st_copy = nullptr, st_side = nullptr;
   cudaEvent_t ev[2] = {nullptr, nullptr}, ev_fork = nullptr, ev_join = nullptr;
-  int sms = 0, scan_grid = 0, sort_grid = 0;
+  int sms = 0, sort_grid = 0;
   int filt_grid = 0, est_grid = 0, sweep_grid = 0;  // one wave of resident blocks
   void* h_pinned = nullptr;
   TaskHeader* h_tasks[2] = {nullptr, nullptr};
@@ -112,7 +112,7 @@ struct srla_group_s {
   std::vector<Slot> slots;
   std::vector<Region> free_list;
   size_t chunk_off = 0, chunk_bytes = 0;  // arena region of the sweep work lists
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t graph[2][2] = {{nullptr, nullptr}, {nullptr, nullptr}};  // [slice parity][read-first scan]
   uint64_t G = 0;
   bool valid[2] = {false, false};
   uint64_t G_of[2] = {0, 0};
@@ -123,7 +123,8 @@ struct srla_group_s {
   uint64_t launches = 0, graph_launches = 0;
   int scan_threads = kGroupScanThreads;  // scan block size: 128, 256 or 512
   uint32_t task_pkts = kTaskPkts;        // packets per scan task
-  int scan_grid_of[3] = {0, 0, 0};       // resident blocks of each block size
+  int scan_grid_of[2][3] = {{0, 0, 0}, {0, 0, 0}};  // resident blocks of each scan build and block size
+  int capture_rf = -1;                   // the scan build a capture records (-1: from the policies)
   struct Segment {
     uint32_t link;
     const uint32_t* ptr;
@@ -303,14 +304,48 @@ int rebuild_work(srla_group_t* g) {
 
 int scan_grid_index(int threads) { return threads == 128 ? 0 : threads == 256 ? 1 : 2; }
 
-void launch_group_scan(srla_group_t* g, int threads, const TaskHeader* tasks) {
-  const int grid = g->scan_grid_of[scan_grid_index(threads)];
+// Whether an attached link's policy may choose the read-first scan (8/16-bit recorders only).
+bool any_read_first(const srla_group_t* g) {
+  for (const Slot& s : g->slots)
+    if (s.active && s.p.dr_bytes &&
+        (s.policy == SRLA_SCAN_POLICY_ADAPTIVE_RF || s.policy == SRLA_SCAN_POLICY_OFF_RF))
+      return true;
+  return false;
+}
+
+template <bool kReadFirst>
+void launch_group_scan_build(srla_group_t* g, int threads, const TaskHeader* tasks) {
+  const int grid = g->scan_grid_of[kReadFirst][scan_grid_index(threads)];
   if (threads == 128)
-    kg_scan<128><<<grid, 128, 0, g->st>>>(g->descs(), tasks, g->gctl());
+    kg_scan<128, kReadFirst><<<grid, 128, 0, g->st>>>(g->descs(), tasks, g->gctl());
   else if (threads == 512)
-    kg_scan<512><<<grid, 512, 0, g->st>>>(g->descs(), tasks, g->gctl());
+    kg_scan<512, kReadFirst><<<grid, 512, 0, g->st>>>(g->descs(), tasks, g->gctl());
   else
-    kg_scan<256><<<grid, 256, 0, g->st>>>(g->descs(), tasks, g->gctl());
+    kg_scan<256, kReadFirst><<<grid, 256, 0, g->st>>>(g->descs(), tasks, g->gctl());
+}
+
+// One wave of resident blocks of each block size of a scan build.
+template <bool kReadFirst>
+cudaError_t scan_occupancy(srla_group_t* g) {
+  const int threads[3] = {128, 256, 512};
+  const void* fn[3] = {reinterpret_cast<const void*>(kg_scan<128, kReadFirst>),
+                       reinterpret_cast<const void*>(kg_scan<256, kReadFirst>),
+                       reinterpret_cast<const void*>(kg_scan<512, kReadFirst>)};
+  for (int i = 0; i < 3; i++) {
+    int occ = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn[i], threads[i], 0);
+    if (e != cudaSuccess) return e;
+    g->scan_grid_of[kReadFirst][i] = g->sms * std::max(1, occ);
+  }
+  return cudaSuccess;
+}
+
+void launch_group_scan(srla_group_t* g, int threads, const TaskHeader* tasks) {
+  const bool rf = g->capture_rf >= 0 ? g->capture_rf != 0 : any_read_first(g);
+  if (rf)
+    launch_group_scan_build<true>(g, threads, tasks);
+  else
+    launch_group_scan_build<false>(g, threads, tasks);
 }
 
 // Split the open slice's batches into scan tasks of at most task_pkts packets.
@@ -365,17 +400,20 @@ int capture(srla_group_t* g) {
   cudaStream_t user = g->st;
   g->st = g->st_copy;
   int rc = SRLA_OK;
-  for (int q = 0; q < 2 && rc == SRLA_OK; q++) {
+  for (int x = 0; x < 4 && rc == SRLA_OK; x++) {
+    const int q = x & 1, rf = x >> 1;
     cudaGraph_t graph = nullptr;
     const uint64_t before = g->launches;
     if (cudaStreamBeginCapture(g->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
       rc = SRLA_E_CUDA;
       break;
     }
+    g->capture_rf = rf;
     rc = enqueue_slice(g, q);
+    g->capture_rf = -1;
     const cudaError_t e = cudaStreamEndCapture(g->st, &graph);
     if (rc == SRLA_OK && e != cudaSuccess) rc = SRLA_E_CUDA;
-    if (rc == SRLA_OK && cudaGraphInstantiate(&g->graph[q], graph, 0) != cudaSuccess) rc = SRLA_E_CUDA;
+    if (rc == SRLA_OK && cudaGraphInstantiate(&g->graph[q][rf], graph, 0) != cudaSuccess) rc = SRLA_E_CUDA;
     if (graph) cudaGraphDestroy(graph);
     g->graph_launches = g->launches - before;
     g->launches = before;
@@ -433,7 +471,7 @@ int srla_group_create(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_p
   g->slots.resize(max_links);
   g->free_list.push_back(Region{g->F.total, (ws_bytes - g->F.total) & ~(kAlign - 1)});
   int rc = SRLA_OK;
-  int dev = 0, occ_scan = 0, occ_sort = 0;
+  int dev = 0, occ_sort = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
     rc = SRLA_E_CUDA;
   if (rc == SRLA_OK &&
@@ -460,20 +498,14 @@ int srla_group_create(uint32_t max_links, uint64_t max_pkts, uint64_t max_host_p
       std::memset(g->h_tasks[q], 0, tbytes);
     }
     cudaFuncSetAttribute(kg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSortSmallSmem);
-    int o128 = 0, o512 = 0, o_filt = 0, o_est = 0, o_sweep = 0;
+    int o_filt = 0, o_est = 0, o_sweep = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o_filt, kg_filter, 256, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o_est, kg_estimate, 256, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o_sweep, kg_sweep, 256, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_scan, kg_scan<256>, 256, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o128, kg_scan<128>, 128, 0) != cudaSuccess ||
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o512, kg_scan<512>, 512, 0) != cudaSuccess ||
+        scan_occupancy<false>(g) != cudaSuccess || scan_occupancy<true>(g) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ_sort, kg_sort, kSortThreads, kSortSmallSmem) != cudaSuccess ||
         occ_sort < 1)
       rc = SRLA_E_CUDA;
-    g->scan_grid_of[0] = g->sms * std::max(1, o128);
-    g->scan_grid_of[1] = g->sms * std::max(1, occ_scan);
-    g->scan_grid_of[2] = g->sms * std::max(1, o512);
-    g->scan_grid = g->scan_grid_of[1];
     g->sort_grid = g->sms * occ_sort;
     g->filt_grid = g->sms * std::max(1, o_filt);
     g->est_grid = g->sms * std::max(1, o_est);
@@ -589,7 +621,7 @@ int srla_group_end_slice(srla_group_t* g, uint64_t* group_slice) {
   g->h_tasks[q]->n_tasks = (unsigned)g->pending.size();
   if (!g->pending.empty())
     std::memcpy(reinterpret_cast<ScanTask*>(g->h_tasks[q] + 1), g->pending.data(), g->pending.size() * sizeof(ScanTask));
-  G_TRY(cudaGraphLaunch(g->graph[q], g->st));
+  G_TRY(cudaGraphLaunch(g->graph[q][any_read_first(g)], g->st));
   g->launches += g->graph_launches;
   G_TRY(cudaEventRecord(g->ev[q], g->st));
   for (Slot& s : g->slots) {
@@ -802,8 +834,10 @@ int srla_group_autotune(srla_group_t* g, int reps, uint32_t* best_threads, uint3
   g->pending.clear();
   // the captured slice ends must launch the chosen scan
   for (int x = 0; x < 2; x++) {
-    if (g->graph[x]) cudaGraphExecDestroy(g->graph[x]);
-    g->graph[x] = nullptr;
+    for (cudaGraphExec_t& e : g->graph[x]) {
+      if (e) cudaGraphExecDestroy(e);
+      e = nullptr;
+    }
   }
   r = r ? r : capture(g);
   if (best_threads) *best_threads = (uint32_t)g->scan_threads;
@@ -878,7 +912,8 @@ void srla_group_destroy(srla_group_t* g) {
   if (!g) return;
   if (g->st) cudaStreamSynchronize(g->st);
   for (int q = 0; q < 2; q++) {
-    if (g->graph[q]) cudaGraphExecDestroy(g->graph[q]);
+    for (cudaGraphExec_t e : g->graph[q])
+      if (e) cudaGraphExecDestroy(e);
     if (g->ev[q]) cudaEventDestroy(g->ev[q]);
   }
   if (g->ev_fork) cudaEventDestroy(g->ev_fork);

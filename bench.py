@@ -131,6 +131,38 @@ def _scan_traffic(workload, pkts_per_launch):
     return t["bytes_per_launch"]
 
 
+def _h2d_copy_rate(host, dev):
+    """The H2D ceiling of the end-to-end loop on this machine (GB/s): plain copies of the same
+    pinned step batches into device memory, each split in two parts on two streams as the
+    library's staging does, with nothing else running; the better of two passes.  The rate
+    depends on the host (PCIe generation, which socket's memory the buffers sit in), so the
+    e2e figure is judged against this, measured in the same run.  None without cuda-bindings."""
+    import torch
+
+    try:
+        from cuda.bindings import runtime as rt
+    except ImportError:
+        return None
+    sizes = [b.numel() * b.element_size() for b in host]
+    dst = torch.empty(max(sizes), dtype=torch.uint8, device=dev)
+    streams = [torch.cuda.Stream(dev) for _ in range(2)]
+    best = 0.0
+    for _ in range(2):
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for b, n in zip(host, sizes):
+            half = (n // 2) & ~15
+            for j, (off, m) in enumerate(((0, half), (half, n - half))):
+                err, = rt.cudaMemcpyAsync(dst.data_ptr() + off, b.data_ptr() + off, m,
+                                          rt.cudaMemcpyKind.cudaMemcpyHostToDevice, streams[j].cuda_stream)
+                if err != rt.cudaError_t.cudaSuccess:
+                    return None
+        torch.cuda.synchronize(dev)
+        best = max(best, sum(sizes) / (time.perf_counter() - t0) / 1e9)
+    del dst
+    return round(best, 2)
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -361,22 +393,36 @@ def bench_srla(args):
 
     # ---- end to end through the public API with host buffers (pinned), H2D inside the timed region
     host = [b.cpu().pin_memory() for b in batches]
-    d2h = []
+
+    def e2e_pass():
+        """One step per host batch: push (H2D through the staging), close, fetch the previous
+        slice's report (D2H).  Returns (host ms, report bytes per step)."""
+        d2h = []
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        pending = None
+        for i in range(K):
+            link.push(host[i])
+            sid = link.end_slice()
+            if pending is not None:
+                r = link.report(pending)
+                d2h.append(64 + 16 * len(r["aip"]))
+            pending = sid
+        r = link.report(pending)
+        d2h.append(64 + 16 * len(r["aip"]))
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) * 1e3, d2h
+
+    # The warm-up is one untimed pass over all K batches, so that the timed pass re-reads
+    # buffers that have been copied once before, as a pool of pinned buffers in steady state
+    # does; the first DMA reads of freshly written pinned buffers run about 10 % slower, and
+    # that pass's rate is reported beside (first_pass).
+    first_ms, _ = e2e_pass()
+    first_pass, _ = job_throughput(pkts, first_ms, world, dev)
     barrier()
-    torch.cuda.synchronize(dev)
-    t0 = time.perf_counter()
-    pending = None
-    for i in range(K):
-        link.push(host[i])
-        sid = link.end_slice()
-        if pending is not None:
-            r = link.report(pending)
-            d2h.append(64 + 16 * len(r["aip"]))
-        pending = sid
-    r = link.report(pending)
-    d2h.append(64 + 16 * len(r["aip"]))
-    torch.cuda.synchronize(dev)
-    e2e, _ = job_throughput(pkts, (time.perf_counter() - t0) * 1e3, world, dev)
+    e2e_ms, d2h = e2e_pass()
+    e2e, _ = job_throughput(pkts, e2e_ms, world, dev)
+    copy_gbs = _h2d_copy_rate(host, dev)
 
     peak, peak_kind = _peaks()
     bpp = _algorithmic_bytes_per_pkt(w, tau)
@@ -398,7 +444,10 @@ def bench_srla(args):
                      "kernel": "k_scan", "bytes_per_pkt": bpp, "peak_kind": peak_kind,
                      "store_roofline": store_roof, "l2": l2_roof},
         "e2e": {"value": round(e2e, 3), "unit": "Mpkts/s", "h2d_bytes_per_step": int(8 * per_launch_pkts),
-                "d2h_bytes_per_step": int(statistics.mean(d2h))},
+                "d2h_bytes_per_step": int(statistics.mean(d2h)),
+                "first_pass": round(first_pass, 3),
+                "h2d_gbs": round(e2e * 8e-3 / world, 2), "h2d_copy_only_gbs": copy_gbs,
+                "h2d_frac": round(e2e * 8e-3 / world / copy_gbs, 3) if copy_gbs else None},
         "gpu_launches": int(launches),
         "slice_end_graph": link.uses_graph(),
         "clocks": clk.summary(),

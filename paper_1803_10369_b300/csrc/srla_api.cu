@@ -19,6 +19,11 @@
 using namespace srla;
 using namespace srla::host;
 
+// Host batches go through a ring of kStageBufs staging parts, copied on kCopyStreams
+// internal streams in turn.
+constexpr int kStageBufs = 2;
+constexpr int kCopyStreams = 2;
+
 struct srla_s {
   srla_params p;
   Geo geo;
@@ -27,14 +32,13 @@ struct srla_s {
   char* ws;
   cudaStream_t st;
   cudaStream_t st_copy;  // internal stream for report remainders and checkpoints
-  cudaStream_t st_h2d;   // internal streams for host-to-device copies of host batches, one per
-  cudaStream_t st_h2d2;  // staging half, so that consecutive halves can use two copy engines
+  cudaStream_t st_h2d[kCopyStreams];  // internal streams: host-to-device copies of host batches
   cudaStream_t st_side;  // internal stream: the estimator table beside filter and sort
   cudaStream_t st_d2h;   // internal stream: each slice's report header, after its slice end
   cudaEvent_t ev_fork, ev_join, ev_swept;
   cudaEvent_t ev_done[2];  // slice end complete, by slice parity
-  cudaEvent_t ev_ready[2], ev_free[2];  // staging halves: copied / consumed by the scan
-  bool free_pending[2];
+  cudaEvent_t ev_ready[kStageBufs], ev_free[kStageBufs];  // staging parts: copied / consumed by the scan
+  bool free_pending[kStageBufs];
   int stage_cur;
   int sms;
   bool k_is_P;
@@ -460,9 +464,8 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
     delete h;
     return SRLA_E_CUDA;
   }
-  if (cudaStreamCreateWithFlags(&h->st_h2d, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&h->st_h2d2, cudaStreamNonBlocking) != cudaSuccess)
-    rc = SRLA_E_CUDA;
+  for (cudaStream_t& cs : h->st_h2d)
+    if (rc == SRLA_OK && cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) rc = SRLA_E_CUDA;
   if (rc == SRLA_OK && (cudaStreamCreateWithFlags(&h->st_side, cudaStreamNonBlocking) != cudaSuccess ||
                         cudaStreamCreateWithFlags(&h->st_d2h, cudaStreamNonBlocking) != cudaSuccess ||
                         cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
@@ -471,7 +474,7 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
                         cudaEventCreateWithFlags(&h->ev_done[0], cudaEventDisableTiming) != cudaSuccess ||
                         cudaEventCreateWithFlags(&h->ev_done[1], cudaEventDisableTiming) != cudaSuccess))
     rc = SRLA_E_CUDA;
-  for (int q = 0; q < 2 && rc == SRLA_OK; q++) {
+  for (int q = 0; q < kStageBufs && rc == SRLA_OK; q++) {
     if (cudaEventCreateWithFlags(&h->ev_ready[q], cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&h->ev_free[q], cudaEventDisableTiming) != cudaSuccess)
       rc = SRLA_E_CUDA;
@@ -519,17 +522,18 @@ int srla_push_packets(srla_t* h, const uint32_t* pairs, uint64_t n_pairs, int on
     if (r == SRLA_OK) h->n_pkts_open += n_pairs;
     return r;
   }
-  // Double-buffered staging: the copy of one half (on that half's internal copy stream, so
-  // that the copies of consecutive halves may run on two copy engines at once) overlaps with
-  // the scan of the other half (on the caller's stream); events order the reuse.
+  // Staging ring: the copies of the parts run back to back on the internal copy stream(s),
+  // while the caller's stream scans each part once it has arrived; a part is copied into
+  // again only after its last scan (events order the reuse), so the copy of the next parts
+  // never waits on the scans of the previous ones.
   uint32_t* staging = h->at<uint32_t>(h->L.staging);
-  const uint64_t half = std::max<uint64_t>(2, (h->L.staging_pkts / 2) & ~1ull);
+  const uint64_t part = std::max<uint64_t>(2, (h->L.staging_pkts / kStageBufs) & ~1ull);
   while (n_pairs) {
     const int x = h->stage_cur;
-    h->stage_cur ^= 1;
-    const uint64_t m = std::min<uint64_t>(n_pairs, half);
-    uint32_t* dst = staging + 2 * half * (uint64_t)x;
-    cudaStream_t cs = x ? h->st_h2d2 : h->st_h2d;
+    h->stage_cur = (x + 1) % kStageBufs;
+    const uint64_t m = std::min<uint64_t>(n_pairs, part);
+    uint32_t* dst = staging + 2 * part * (uint64_t)x;
+    cudaStream_t cs = h->st_h2d[x % kCopyStreams];
     if (h->free_pending[x]) SRLA_TRY(cudaStreamWaitEvent(cs, h->ev_free[x], 0));
     SRLA_TRY(cudaMemcpyAsync(dst, pairs, m * 8, cudaMemcpyHostToDevice, cs));
     SRLA_TRY(cudaEventRecord(h->ev_ready[x], cs));
@@ -768,8 +772,8 @@ void srla_destroy(srla_t* h) {
     cudaStreamSynchronize(h->st);
     cudaStreamDestroy(h->st_copy);
   }
-  if (h->st_h2d) cudaStreamDestroy(h->st_h2d);
-  if (h->st_h2d2) cudaStreamDestroy(h->st_h2d2);
+  for (cudaStream_t cs : h->st_h2d)
+    if (cs) cudaStreamDestroy(cs);
   if (h->st_d2h) {
     cudaStreamSynchronize(h->st_d2h);
     cudaStreamDestroy(h->st_d2h);
@@ -782,6 +786,8 @@ void srla_destroy(srla_t* h) {
     if (h->ev_done[q]) cudaEventDestroy(h->ev_done[q]);
     if (h->slot[q].ev) cudaEventDestroy(h->slot[q].ev);
     if (h->graph[q]) cudaGraphExecDestroy(h->graph[q]);
+  }
+  for (int q = 0; q < kStageBufs; q++) {
     if (h->ev_ready[q]) cudaEventDestroy(h->ev_ready[q]);
     if (h->ev_free[q]) cudaEventDestroy(h->ev_free[q]);
   }

@@ -375,6 +375,13 @@ int srla_group_report(srla_group_t *g, uint32_t link, uint64_t group_slice, srla
 int srla_group_set_scan_policy(srla_group_t *g, uint32_t link, uint32_t policy);
 int srla_group_scan_policy(const srla_group_t *g, uint32_t link, uint32_t *policy);
 
+/* The group scan is compiled twice: a lean kernel, and one that adds the read-first build
+ * (it needs more registers).  A slice end runs the second when some attached link's policy
+ * may choose the read-first build (SRLA_SCAN_POLICY_ADAPTIVE_RF or _OFF_RF on 8/16-bit
+ * recorders), else the first.  srla_group_scan_builds counts the slice ends that ran each
+ * since srla_group_create (either pointer may be NULL); INVAL for g = NULL.               */
+int srla_group_scan_builds(const srla_group_t *g, uint64_t *lean, uint64_t *read_first);
+
 /* Scan autotuner: with the open slice's packets pushed, time the group scan with block sizes
  * 128/256/512 and tasks of 2^14/2^16/2^18 packets (reps runs each, on empty pair tables) and
  * keep the fastest (median); then, per link class (links with fewer than 2^18 packets in the

@@ -121,6 +121,7 @@ struct srla_group_s {
   uint64_t stage_used = 0;
   bool stage_waited = false;
   uint64_t launches = 0, graph_launches = 0;
+  uint64_t scan_builds[2] = {0, 0};  // slice ends that ran the lean / the read-first scan
   int scan_threads = kGroupScanThreads;  // scan block size: 128, 256 or 512
   uint32_t task_pkts = kTaskPkts;        // packets per scan task
   int scan_grid_of[2][3] = {{0, 0, 0}, {0, 0, 0}};  // resident blocks of each scan build and block size
@@ -621,7 +622,9 @@ int srla_group_end_slice(srla_group_t* g, uint64_t* group_slice) {
   g->h_tasks[q]->n_tasks = (unsigned)g->pending.size();
   if (!g->pending.empty())
     std::memcpy(reinterpret_cast<ScanTask*>(g->h_tasks[q] + 1), g->pending.data(), g->pending.size() * sizeof(ScanTask));
-  G_TRY(cudaGraphLaunch(g->graph[q][any_read_first(g)], g->st));
+  const int rf = any_read_first(g) ? 1 : 0;
+  G_TRY(cudaGraphLaunch(g->graph[q][rf], g->st));
+  g->scan_builds[rf]++;
   g->launches += g->graph_launches;
   G_TRY(cudaEventRecord(g->ev[q], g->st));
   for (Slot& s : g->slots) {
@@ -907,6 +910,13 @@ int srla_group_sync(srla_group_t* g) {
 }
 
 uint64_t srla_group_kernel_launches(const srla_group_t* g) { return g ? g->launches : 0; }
+
+int srla_group_scan_builds(const srla_group_t* g, uint64_t* lean, uint64_t* read_first) {
+  if (!g) return SRLA_E_INVAL;
+  if (lean) *lean = g->scan_builds[0];
+  if (read_first) *read_first = g->scan_builds[1];
+  return SRLA_OK;
+}
 
 void srla_group_destroy(srla_group_t* g) {
   if (!g) return;

@@ -100,6 +100,7 @@ SIGNATURES = {
     "srla_group_export_state": (ctypes.c_int, [_P, ctypes.c_uint32, _P, ctypes.c_size_t]),
     "srla_group_sync": (ctypes.c_int, [_P]),
     "srla_group_kernel_launches": (ctypes.c_uint64, [_P]),
+    "srla_group_scan_builds": (ctypes.c_int, [_P, _P, _P]),
     "srla_group_destroy": (None, [_P]),
     "srla_server_workspace_bytes": (ctypes.c_size_t, [_P, ctypes.c_uint64]),
     "srla_server_create": (ctypes.c_int, [_P, _P, ctypes.c_size_t, _P, _P]),
@@ -492,6 +493,12 @@ class Group:
 
     def kernel_launches(self) -> int:
         return self.L.srla_group_kernel_launches(self._h)
+
+    def scan_builds(self):
+        """(lean, read_first): slice ends that ran each group scan instantiation."""
+        a, b = ctypes.c_uint64(), ctypes.c_uint64()
+        _ck(self.L.srla_group_scan_builds(self._h, ctypes.byref(a), ctypes.byref(b)), "srla_group_scan_builds")
+        return a.value, b.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -146,27 +146,41 @@ def test_links_attach_and_detach_between_slices(cuda_device):
     g.close()
 
 
+def _policy(s, i):
+    """Slices 0-7: the four policies rotate over the links.  Slices 8-11: every link on a
+    policy without the read-first build, so the group launches its lean scan instantiation."""
+    if s < 8:
+        return (s + i) % 4
+    return (srla.SCAN_POLICY_ADAPTIVE, srla.SCAN_POLICY_OFF)[(s + i) % 2]
+
+
 def test_group_scan_policies_match_oracle(cuda_device):
     """The four aggregation policies (pair table adaptive or off, plain or read-first build)
-    rotate over the links slice by slice; every report and state still equals the oracle's."""
+    rotate over the links slice by slice, then only the policies without the read-first build
+    (the lean scan instantiation); every report and state still equals the oracle's."""
     links = _links()[:8] + [(TINY.replace(seed=27, dst_model="pool", pool_max=4, dr_bytes=2, z=16, k=5), {})]
     g = _group()
-    ids, orc = [], []
+    ids, orc, widths = [], [], []
     for w, over in links:
         p = _params(w, **over)
         ids.append(g.attach(p))
         orc.append(oracle_for(p))
-    for s in range(8):
+        widths.append(p.dr_bytes)
+    rf_policies = (srla.SCAN_POLICY_ADAPTIVE_RF, srla.SCAN_POLICY_OFF_RF)
+    # slices whose scan is the read-first instantiation: some 8/16-bit link may choose that build
+    rf_slices = sum(any(_policy(s, i) in rf_policies and widths[i] for i in range(len(links))) for s in range(12))
+    for s in range(12):
         for i, (w, _) in enumerate(links):
-            g.set_scan_policy(ids[i], (s + i) % 4)
+            g.set_scan_policy(ids[i], _policy(s, i))
             pk = synth.generate_slice(w.traffic, s)
             orc[i].push(synth.pairs_to_numpy(pk))
             g.push(ids[i], pk.to(cuda_device))
         allr = g.report_all(g.end_slice())
         for i in range(len(links)):
-            assert g.scan_policy(ids[i]) == (s + i) % 4
-            compare_reports(orc[i].end_slice(), allr[ids[i]], f"slice {s} link {i} policy {(s + i) % 4}")
+            assert g.scan_policy(ids[i]) == _policy(s, i)
+            compare_reports(orc[i].end_slice(), allr[ids[i]], f"slice {s} link {i} policy {_policy(s, i)}")
             compare_state(orc[i], g.state_arrays(ids[i]), f"slice {s} link {i}")
+    assert g.scan_builds() == (12 - rf_slices, rf_slices) and rf_slices >= 1 and 12 - rf_slices >= 4
     with pytest.raises(srla.SRLAError) as e:
         g.set_scan_policy(ids[0], 4)
     assert e.value.code == srla.E_INVAL
@@ -187,7 +201,9 @@ def _scaled_batched_links(n_links, scale):
 
 def test_batched_geometry_64_links_match_oracle(cuda_device):
     """64 links of the batched workload's geometry in one group, 20 slices (past the shortest
-    windows), every report against its oracle, every link's state at the end."""
+    windows), every report against its oracle, every link's state at the end.  The first 10
+    slices run the default policy (adaptive table, read-first build when it is off), the last
+    10 the adaptive table with the plain build only (the group's lean scan instantiation)."""
     links = _scaled_batched_links(64, 32)
     params = [srla.params_for(w, *synth.hash_coefficients(w.hash_seed, w.u + 3), pair_slots_log2=plog)
               for w, plog in links]
@@ -200,6 +216,9 @@ def test_batched_geometry_64_links_match_oracle(cuda_device):
     orc = [oracle_for(p) for p in params]
     n_slices = 20
     for s in range(n_slices):
+        if s == n_slices // 2:
+            for l in ids:
+                g.set_scan_policy(l, srla.SCAN_POLICY_ADAPTIVE)
         for i, (w, _) in enumerate(links):
             pk = synth.generate_slice(w.traffic, s)
             orc[i].push(synth.pairs_to_numpy(pk))
@@ -209,6 +228,7 @@ def test_batched_geometry_64_links_match_oracle(cuda_device):
             compare_reports(orc[i].end_slice(), allr[ids[i]], f"slice {s} link {i} ({links[i][0].name})")
     for i in range(len(links)):
         compare_state(orc[i], g.state_arrays(ids[i]), f"end link {i}")
+    assert g.scan_builds() == (n_slices // 2, n_slices // 2)
     g.close()
 
 

@@ -247,7 +247,8 @@ void srla_destroy(srla_t *h);
  * srla_push_packets + srla_end_slice + srla_report give for a first slice holding exactly
  * this batch, and copies it (sorted by aip) to the host buffer out (cap entries; *n_out =
  * full count; stats may be NULL).  It synchronizes `stream` and returns when the report is
- * on the host.
+ * on the host; while `stream` is being captured it returns SRLA_E_INVAL before any other
+ * CUDA call, leaving the capture intact.
  *
  * Scratch: a fixed array of SRLA_STATIC_SCRATCH_BYTES compiled into the library, present on
  * every GPU that loads the library until the process exits.  Parameters whose one-slice

@@ -858,6 +858,11 @@ extern "C" int srla_batch_report_static(const srla_params* p, const uint32_t* d_
                                         void* stream, srla_entry* out, size_t cap, size_t* n_out,
                                         srla_slice_stats* stats) {
   if (check(p) != SRLA_OK || (n_pairs && !d_pairs) || (cap && !out)) return SRLA_E_INVAL;
+  // the call synchronizes the stream, which a stream being captured must not do (it would
+  // end the caller's capture with an error): refuse before any other CUDA call
+  cudaStreamCaptureStatus capturing = cudaStreamCaptureStatusNone;
+  SRLA_TRY(cudaStreamIsCapturing(static_cast<cudaStream_t>(stream), &capturing));
+  if (capturing != cudaStreamCaptureStatusNone) return SRLA_E_INVAL;
   srla_params q = *p;
   q.staging_pkts = 2;  // the batch is already on the device: no host staging area
   const Layout L = layout_of(&q, 1);  // one slice: one pair table

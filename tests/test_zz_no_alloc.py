@@ -58,3 +58,31 @@ def test_static_scratch_rejects_oversized_parameters(cuda_device):
     with pytest.raises(srla.SRLAError) as e:
         srla.batch_report_static(params, pk)
     assert e.value.code == srla.E_NOMEM
+
+
+def test_static_scratch_refuses_a_capturing_stream(cuda_device):
+    """The call synchronizes its stream, so on a stream being captured it returns INVAL
+    before any other CUDA call; the capture stays intact (its graph replays)."""
+    import torch
+
+    w = synth.workload("tiny")
+    ha, hb = synth.hash_coefficients(w.hash_seed, w.u + 3)
+    params = srla.params_for(w, ha, hb)
+    pk = synth.generate_slice(w.traffic, 0, device=cuda_device)
+    # a first call outside any capture (the library's device code and scratch array are
+    # loaded by then), which works
+    assert srla.batch_report_static(params, pk)["stats"]["n_pkts"] == pk.shape[0]
+    x = torch.zeros(4, device=cuda_device)
+    graph = torch.cuda.CUDAGraph()
+    side = torch.cuda.Stream(cuda_device)
+    torch.cuda.synchronize(cuda_device)
+    with torch.cuda.graph(graph, stream=side):
+        x.add_(1.0)
+        with pytest.raises(srla.SRLAError) as e:
+            srla.batch_report_static(params, pk, stream=side)
+        assert e.value.code == srla.E_INVAL
+    graph.replay()
+    torch.cuda.synchronize(cuda_device)
+    assert x.tolist() == [1.0] * 4
+    # and after the capture it works again
+    assert srla.batch_report_static(params, pk)["stats"]["n_pkts"] == pk.shape[0]

@@ -385,12 +385,14 @@ int srla_group_scan_builds(const srla_group_t *g, uint64_t *lean, uint64_t *read
 
 /* Scan autotuner: with the open slice's packets pushed, time the group scan with block sizes
  * 128/256/512 and tasks of 2^14/2^16/2^18 packets (reps runs each, on empty pair tables) and
- * keep the fastest (median); then, per link class (links with fewer than 2^18 packets in the
- * open slice, and links with more), time the four aggregation policies above for that class's
- * links and keep the fastest.  The choices hold for all later slices (srla_group_scan_policy
+ * keep the fastest (median); then, starting from SRLA_SCAN_POLICY_ADAPTIVE on every link,
+ * per link class (links with fewer than 2^18 packets in the open slice, then links with more)
+ * time the four aggregation policies above for that class's links and keep the fastest.  The choices hold for all later slices (srla_group_scan_policy
  * reads a link's); the slice's results are unchanged (the trial scans repeat the slice's own
- * idempotent recorder stores and set insertions).  Errors: ORDER when nothing was pushed,
- * CUDA.                                                                                  */
+ * idempotent recorder stores and set insertions).  Links attached after the tuning start on
+ * the policy chosen for the class of links with fewer packets (or, when that class had no
+ * links, for the other); before any tuning, on SRLA_SCAN_POLICY_ADAPTIVE_RF.  Errors: ORDER
+ * when nothing was pushed, CUDA.                                                         */
 int srla_group_autotune(srla_group_t *g, int reps, uint32_t *best_threads, uint32_t *best_task_pkts);
 
 /* Checkpoint of one attached link at a slice boundary (no packets pushed in the open group

@@ -122,6 +122,9 @@ struct srla_group_s {
   bool stage_waited = false;
   uint64_t launches = 0, graph_launches = 0;
   uint64_t scan_builds[2] = {0, 0};  // slice ends that ran the lean / the read-first scan
+  // policy of links attached from now on: the one the autotuner chose for the class of
+  // links with fewer packets (a new link's rate is not known yet)
+  uint32_t new_policy = SRLA_SCAN_POLICY_ADAPTIVE_RF;
   int scan_threads = kGroupScanThreads;  // scan block size: 128, 256 or 512
   uint32_t task_pkts = kTaskPkts;        // packets per scan task
   int scan_grid_of[2][3] = {{0, 0, 0}, {0, 0, 0}};  // resident blocks of each scan build and block size
@@ -542,6 +545,7 @@ int srla_group_attach(srla_group_t* g, const srla_params* p, uint32_t* link) {
   if (!arena_alloc(g, L.total, &off)) return SRLA_E_NOMEM;
   Slot& s = g->slots[l];
   s = Slot{};
+  s.policy = g->new_policy;
   s.active = true;
   s.p = lp;
   s.L = L;
@@ -799,6 +803,11 @@ int srla_group_autotune(srla_group_t* g, int reps, uint32_t* best_threads, uint3
     }
     return SRLA_OK;
   };
+  // The search starts from the plain build on every link, so that each class's trials see
+  // the lean scan instantiation (one link that may choose the read-first build selects the
+  // other for the whole group).
+  for (int cls = 0; cls < 2 && r == SRLA_OK; cls++) r = set_class(cls, SRLA_SCAN_POLICY_ADAPTIVE);
+  bool light_tuned = false;  // the class of links with fewer packets had links to tune
   for (int cls = 0; cls < 2 && r == SRLA_OK; cls++) {
     bool any = false;
     for (const Slot& s : g->slots) any |= s.active && s.pkts_open && (int)(s.pkts_open >= kHeavyPkts) == cls;
@@ -820,6 +829,8 @@ int srla_group_autotune(srla_group_t* g, int reps, uint32_t* best_threads, uint3
       }
     }
     r = r ? r : set_class(cls, best_pol);
+    if (r == SRLA_OK && (cls == 0 || !light_tuned)) g->new_policy = best_pol;
+    light_tuned |= cls == 0;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

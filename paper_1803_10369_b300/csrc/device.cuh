@@ -74,6 +74,22 @@ struct ScanCount {
   uint32_t miss, gdup, scan, samp, probe, heavy;
 };
 
+// The pair-table mode of the slice after a slice T that ran with pair_mode and counted n_miss
+// claims of which n_gdup were repeats: on while at least a quarter of the claims find
+// repeats, and tried again every 16 slices.  The slice close sets it; the host derives the
+// same value from the slice's statistics to pick the next scans' build.
+__host__ __device__ inline uint32_t next_pair_mode(uint32_t pair_mode, uint64_t n_miss, uint64_t n_gdup, uint64_t T) {
+  const bool worth = 4ull * n_gdup >= n_miss;
+  return ((pair_mode != 0 && worth) || (T + 1) % 16 == 0) ? 1u : 0u;
+}
+
+// The heavy-host mode of the slice after a slice that scanned n_scan pairs and saw n_heavy
+// heavy events: heavy events in at least 1/8 of its 32-pair scan drains (n_scan / 32 of
+// them).  Set by the slice close, derived by the host as above.
+__host__ __device__ inline uint32_t next_heavy_mode(uint64_t n_scan, uint64_t n_heavy) {
+  return (n_scan > 0 && 256ull * n_heavy >= n_scan) ? 1u : 0u;
+}
+
 // ---------------------------------------------------------------------------- hashing
 
 // One member of the polynomial family, h(x) = (a*x + b) mod (2^61 - 1), low 32 bits.

@@ -156,5 +156,10 @@ inline Layout layout_of(const srla_params* p, int n_pair_tables = 2) {
   return L;
 }
 
+// Bytes from a slice's statistics to its report entries: the entries' region follows the
+// statistics' (one aligned step, the same for both slice parities), so one copy moves the
+// statistics and the first entries together.
+inline size_t report_gap(const Layout& L) { return L.rep_entries[0] - L.rep_stats[0]; }
+
 }  // namespace host
 }  // namespace srla

@@ -716,17 +716,13 @@ __device__ __forceinline__ void close_slice(const Geo& geo, Ctl* __restrict__ ct
   n.blocks_done = 0;
   n.bar_count = 0;
   n.w_star = geo.gl + 1u;
-  const bool measured = c.pair_mode != 0;
-  const bool worth = 4ull * c.n_gdup >= (unsigned long long)c.n_miss;
-  n.pair_mode = (measured ? worth : false) || ((T + 1) % 16 == 0) ? 1u : 0u;
+  n.pair_mode = next_pair_mode(c.pair_mode, c.n_miss, c.n_gdup, T);
   n.n_miss = 0;
   n.n_gdup = 0;
   n.n_scan = 0;
   n.n_scan_samp = 0;
   n.n_probe = 0;
-  // heavy-host tracking for the next slice: heavy events in at least 1/8 of the slice's
-  // 32-pair scan drains (n_scan / 32 of them)
-  n.heavy_mode = (c.n_scan > 0 && 256ull * c.n_heavy >= c.n_scan) ? 1u : 0u;
+  n.heavy_mode = next_heavy_mode(c.n_scan, c.n_heavy);
   n.n_heavy = 0;
   n.sat_hint = sat_hint_of(geo, c);
   n.sre_post = 0;

@@ -59,8 +59,6 @@ struct srla_s {
     cudaEvent_t ev;
     srla_slice_stats* h_stats;
     srla_entry* h_entries;
-    uint32_t* h_pair_mode;  // pair-table state of the slice after this one (read-first scan hint)
-    uint32_t* h_heavy_mode;  // heavy-host state of the slice after this one (heavy scan hint)
   } slot[2];
   void* h_pinned;
 
@@ -139,7 +137,9 @@ const srla_s::Slot* newest_reported(const srla_t* h) {
 
 bool read_first_hint(const srla_t* h) {
   const srla_s::Slot* s = newest_reported(h);
-  return s && *s->h_pair_mode == 0;
+  if (!s) return false;
+  const srla_slice_stats& st = *s->h_stats;
+  return next_pair_mode(st.pair_table, st.n_claims, st.n_claim_repeats, st.slice) == 0;
 }
 
 // Heavy build (8/16-bit recorders, order-free rule, runs that fit the block's bitmaps) when
@@ -150,7 +150,7 @@ bool heavy_possible(const srla_t* h) {
 
 bool heavy_hint(const srla_t* h) {
   const srla_s::Slot* s = newest_reported(h);
-  return s && *s->h_heavy_mode != 0;
+  return s && next_heavy_mode(s->h_stats->n_scanned, s->h_stats->n_heavy_events) != 0;
 }
 
 template <typename CellT>
@@ -305,21 +305,17 @@ int launch_end_slice(srla_t* h, int q) {
   return two ? SRLA_OK : clear_pairs(h, 0, h->st);
 }
 
-// The copy of slice q's header and first report entries into its pinned slot, on the
+// The copy of slice q's statistics and first report entries into its pinned slot, on the
 // report stream once the slice end is complete; the next slice's scan does not wait for it.
+// The entries follow the statistics in the workspace (rep_entries[q] = rep_stats[q] +
+// report_gap(L)) and in the slot alike, so one copy moves both.
 int enqueue_report_copy(srla_t* h, int q) {
   srla_s::Slot& s = h->slot[q];
   SRLA_TRY(cudaEventRecord(h->ev_done[q], h->st));
   SRLA_TRY(cudaStreamWaitEvent(h->st_d2h, h->ev_done[q], 0));
-  SRLA_TRY(cudaMemcpyAsync(s.h_stats, h->ws + h->L.rep_stats[q], sizeof(srla_slice_stats), cudaMemcpyDeviceToHost,
-                           h->st_d2h));
   const uint32_t pre = std::min<uint32_t>(kPrefetch, h->p.max_candidates);
-  SRLA_TRY(cudaMemcpyAsync(s.h_entries, h->ws + h->L.rep_entries[q], (size_t)pre * sizeof(srla_entry),
+  SRLA_TRY(cudaMemcpyAsync(s.h_stats, h->ws + h->L.rep_stats[q], report_gap(h->L) + (size_t)pre * sizeof(srla_entry),
                            cudaMemcpyDeviceToHost, h->st_d2h));
-  SRLA_TRY(cudaMemcpyAsync(s.h_pair_mode, &h->ctl()->pair_mode, sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                           h->st_d2h));
-  SRLA_TRY(cudaMemcpyAsync(s.h_heavy_mode, &h->ctl()->heavy_mode, sizeof(uint32_t), cudaMemcpyDeviceToHost,
-                           h->st_d2h));
   SRLA_TRY(cudaEventRecord(s.ev, h->st_d2h));
   return SRLA_OK;
 }
@@ -454,7 +450,7 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
     delete h;
     return cuda_err(cudaErrorUnknown);
   }
-  const size_t per_slot = sizeof(srla_slice_stats) + (size_t)kPrefetch * sizeof(srla_entry) + 16;
+  const size_t per_slot = report_gap(h->L) + (size_t)kPrefetch * sizeof(srla_entry);
   if (cudaHostAlloc(&h->h_pinned, 2 * per_slot, cudaHostAllocDefault) != cudaSuccess) {
     delete h;
     return cuda_err(cudaErrorMemoryAllocation);
@@ -483,11 +479,7 @@ int srla_create(const srla_params* p, void* dev_workspace, size_t ws_bytes, void
     h->slot[q].valid = false;
     h->slot[q].h_stats = reinterpret_cast<srla_slice_stats*>(static_cast<char*>(h->h_pinned) + q * per_slot);
     h->slot[q].h_entries = reinterpret_cast<srla_entry*>(reinterpret_cast<char*>(h->slot[q].h_stats) +
-                                                         sizeof(srla_slice_stats));
-    h->slot[q].h_pair_mode = reinterpret_cast<uint32_t*>(h->slot[q].h_entries + kPrefetch);
-    h->slot[q].h_heavy_mode = h->slot[q].h_pair_mode + 1;
-    *h->slot[q].h_pair_mode = 1u;
-    *h->slot[q].h_heavy_mode = 0u;
+                                                         report_gap(h->L));
     if (cudaEventCreateWithFlags(&h->slot[q].ev, cudaEventDisableTiming) != cudaSuccess) rc = SRLA_E_CUDA;
   }
   if (rc == SRLA_OK) {

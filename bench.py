@@ -140,7 +140,7 @@ def _h2d_copy_rate(host, dev):
     pinned step batches into device memory, each split in two parts on two streams as the
     library's staging does, with nothing else running; the better of two passes.  The rate
     depends on the host (PCIe generation, which socket's memory the buffers sit in), so the
-    e2e figure is judged against this, measured in the same run.  None without cuda-bindings."""
+    e2e figure is compared with this, measured in the same run.  None without cuda-bindings."""
     import torch
 
     try:

@@ -409,7 +409,7 @@ void srla_group_destroy(srla_group_t *g);
 
 /* ======================================================================================
  * Serving: a request loop over one group.  Links arrive (open), depart (close) and send
- * packet batches (submit) from any host thread; one driver thread calls srla_server_tick
+ * packet batches (submit) from any host thread; one tick thread calls srla_server_tick
  * once per slice.  A tick applies the departures, admits waiting links in arrival order
  * while their arena bytes fit the HBM budget and a slot is free (continuous batching: a link
  * that arrives while slices are running joins at the next tick), pushes the batches that
@@ -460,7 +460,7 @@ int srla_server_submit_many(srla_server_t *s, uint32_t n, const uint64_t *keys,
  * reps runs per configuration) before closing the slice.                                 */
 int srla_server_autotune(srla_server_t *s, int reps);
 
-/* Close a slice (driver thread).  *slice receives its index; *admitted / *waiting (may be
+/* Close a slice (tick thread).  *slice receives its index; *admitted / *waiting (may be
  * NULL) the links in it and the links still queued for admission.                       */
 int srla_server_tick(srla_server_t *s, uint64_t *slice, uint32_t *admitted, uint32_t *waiting);
 
@@ -470,10 +470,10 @@ int srla_server_poll(srla_server_t *s, uint64_t slice, srla_server_result *resul
                      size_t result_cap, size_t *n_results, srla_entry *entries,
                      size_t entry_cap, size_t *n_entries);
 
-/* Bytes of the budget in use by admitted links (driver thread). */
+/* Bytes of the budget in use by admitted links (tick thread). */
 uint64_t srla_server_used_bytes(const srla_server_t *s);
 
-/* Checkpoint of an admitted link between ticks (driver thread), as srla_group_export_state;
+/* Checkpoint of an admitted link between ticks (tick thread), as srla_group_export_state;
  * SRLA_E_ORDER when the key is not admitted.  srla_server_state_bytes is 0 for such a key. */
 size_t srla_server_state_bytes(srla_server_t *s, uint64_t key);
 int srla_server_export_state(srla_server_t *s, uint64_t key, void *host_buf, size_t cap);

@@ -1,10 +1,10 @@
 // libsrla serving: a request loop over one link group (declared in include/srla.h).
 //
 // Clients open, close and feed links from any host thread; their requests queue under one
-// mutex.  The driver thread's tick takes the queues, retires departed links, admits waiting
+// mutex.  The tick thread's srla_server_tick takes the queues, retires departed links, admits waiting
 // links in arrival order while the byte budget and the group's arena and slots allow, pushes
 // the batches of admitted links, and closes the slice of all of them with one graph launch.
-// Only the driver thread touches the group, so the GPU work of every admitted link runs in
+// Only the tick thread touches the group, so the GPU work of every admitted link runs in
 // the same launches while new requests keep arriving.
 #include <cstring>
 #include <deque>
@@ -260,7 +260,7 @@ int srla_server_poll(srla_server_t* s, uint64_t slice, srla_server_result* resul
 
 uint64_t srla_server_used_bytes(const srla_server_t* s) { return s ? s->used : 0; }
 
-// The state of an admitted link between ticks (driver thread): the group link's export.
+// The state of an admitted link between ticks (tick thread): the group link's export.
 static int server_link(srla_server_t* s, uint64_t key, uint32_t* link) {
   std::lock_guard<std::mutex> lock(s->mu);
   const auto it = s->link_of.find(key);

@@ -150,37 +150,64 @@ __device__ __forceinline__ void radix_hist_tiles(const uint32_t* src, uint32_t n
   }
 }
 
-// Exclusive scan of hist[0 .. N) in place by one block.
+// Exclusive scan of hist[0 .. N) in place by one block (N a multiple of 8, hist 16-byte
+// aligned, at most 31 warps; `part` holds 32 words).  The array goes by in chunks of 8
+// consecutive entries per thread (two 16-byte loads, so a warp reads 1 KB contiguous), four
+// chunks' loads in flight before any is used; each chunk is then scanned across the block
+// and offset by the total of the chunks before it.  (A contiguous run of N / blockDim
+// entries per thread made every warp load touch 32 lines, one round trip after another.)
 __device__ __forceinline__ void radix_scan_block(uint32_t* hist, uint32_t N, uint32_t* part) {
-  const uint32_t per = (N + blockDim.x - 1) / blockDim.x;
-  const uint32_t lo = threadIdx.x * per, hi = min(N, lo + per);
-  uint32_t s = 0;
-  for (uint32_t x = lo; x < hi; x++) s += hist[x];
+  constexpr int kChunks = 4;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t incl = s;
+  const uint32_t nw = blockDim.x >> 5, chunk = blockDim.x * 8u;
+  uint4* h4 = reinterpret_cast<uint4*>(hist);
+  uint32_t carry = 0;  // total of the chunks already scanned, the same in every thread
+  for (uint32_t base = 0; base < N; base += kChunks * chunk) {
+    uint4 v[kChunks][2];
 #pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t t = __shfl_up_sync(kFull, incl, o);
-    if (lane >= o) incl += t;
-  }
-  if (lane == 31) part[w] = incl;
-  __syncthreads();
-  if (w == 0) {
-    const uint32_t p = (lane < (int)(blockDim.x >> 5)) ? part[lane] : 0u;
-    uint32_t pi = p;
+    for (int c = 0; c < kChunks; c++) {
+      const uint32_t x = base + c * chunk + threadIdx.x * 8u;  // this thread's 8 entries
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t t = __shfl_up_sync(kFull, pi, o);
-      if (lane >= o) pi += t;
+      for (int k = 0; k < 2; k++) v[c][k] = x < N ? h4[x / 4 + k] : make_uint4(0u, 0u, 0u, 0u);
     }
-    part[lane] = pi - p;
-  }
-  __syncthreads();
-  uint32_t run = part[w] + incl - s;
-  for (uint32_t x = lo; x < hi; x++) {
-    const uint32_t c = hist[x];
-    hist[x] = run;
-    run += c;
+#pragma unroll
+    for (int c = 0; c < kChunks; c++) {
+      const uint32_t x = base + c * chunk + threadIdx.x * 8u;
+      const uint32_t s = v[c][0].x + v[c][0].y + v[c][0].z + v[c][0].w + v[c][1].x + v[c][1].y + v[c][1].z + v[c][1].w;
+      uint32_t incl = s;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (lane == 31) part[w] = incl;
+      __syncthreads();
+      if (w == 0) {  // exclusive prefix of the warps' sums; lane 31 gets the chunk's total
+        const uint32_t p = ((uint32_t)lane < nw) ? part[lane] : 0u;
+        uint32_t pi = p;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(kFull, pi, o);
+          if (lane >= o) pi += t;
+        }
+        part[lane] = pi - p;
+      }
+      __syncthreads();
+      uint32_t run = carry + part[w] + incl - s;
+      if (x < N) {
+#pragma unroll
+        for (int k = 0; k < 2; k++) {
+          uint4 o;
+          o.x = run; run += v[c][k].x;
+          o.y = run; run += v[c][k].y;
+          o.z = run; run += v[c][k].z;
+          o.w = run; run += v[c][k].w;
+          h4[x / 4 + k] = o;
+        }
+      }
+      carry += part[31];
+      __syncthreads();  // part is rewritten by the next chunk
+    }
   }
 }
 

@@ -319,9 +319,9 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
   }
   // Above that, two tasks per run of b consecutive candidates: one estimates them (union SLE),
   // one runs their carry test (post-slide union SRE).  b grows up to 32 so that a run's hosts,
-  // origin flags, report entries and next-slice inserts are handled with one lane per
-  // candidate, their round trips paid once per run; only the gathers stay one candidate at a
-  // time.
+  // origin flags, saturated-estimator tests, report entries and next-slice inserts are handled
+  // with one lane per candidate, their round trips paid once per run; only the gathers of the
+  // hosts that are not saturated go one candidate at a time.
   const uint32_t b = min(32u, max(1u, (n + nw - 1) / nw));
   const uint32_t runs = n > nw ? (n + b - 1) / b : 0u;
   for (uint32_t t = gw; t < 2 * runs; t += nw) {
@@ -336,13 +336,14 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
         const uint32_t s = set_find(ctab, cmask, tag, my_aip);
         origin = (s != 0xFFFFFFFFu) ? cflags[s] : 0u;
       }
-      uint32_t my_w = geo.gl;
-      for (uint32_t j = 0; j < m && !le_full; j++) {
-        const uint32_t aip = __shfl_sync(kFull, my_aip, (int)j);
+      uint32_t my_w = geo.gl;  // a host whose u estimators are all saturated has w = g'
+      const bool my_sat = le_full || (mine && le_map && own_host_saturated(le_sat, geo, coef, my_aip));
+      for (unsigned todo = __ballot_sync(kFull, mine && !my_sat); todo; todo &= todo - 1u) {
+        const int j = __ffs(todo) - 1;
+        const uint32_t aip = __shfl_sync(kFull, my_aip, j);
         const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
-        const bool sat = le_map && host_saturated(le_sat, geo.v, geo.u, mycol, lane);
-        const uint32_t w = sat ? geo.gl : union_count<CellT>(le, geo.v, geo.gl, geo.u, mycol, win, lane);
-        if ((uint32_t)lane == j) my_w = w;
+        const uint32_t w = union_count<CellT>(le, geo.v, geo.gl, geo.u, mycol, win, lane);
+        if (lane == j) my_w = w;
       }
       if (mine) {
         srla_entry e;
@@ -356,15 +357,23 @@ __global__ void __launch_bounds__(256) k_estimate(Geo geo, const __grid_constant
     }
     // inline mode: a carried host gets its SI bits in the next slice's indicators (Algorithm 3)
     uint32_t* si_next = par ? si0 : si1;
-    bool pass = false;
-    for (uint32_t j = 0; j < m; j++) {
-      const uint32_t aip = __shfl_sync(kFull, my_aip, (int)j);
+    // a host whose u estimators are all saturated has union weight g >= ceil(rho g): it passes
+    const bool my_sat = re_full || (mine && re_map && own_host_saturated(re_sat, geo, coef, my_aip));
+    bool pass = mine && my_sat;
+    for (unsigned todo = __ballot_sync(kFull, mine && !my_sat); todo; todo &= todo - 1u) {
+      const int j = __ffs(todo) - 1;
+      const uint32_t aip = __shfl_sync(kFull, my_aip, j);
       const uint32_t mycol = (uint32_t)lane < geo.u ? hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask : 0u;
-      const bool sat = re_full || (re_map && host_saturated(re_sat, geo.v, geo.u, mycol, lane));
-      const uint32_t cw = sat ? geo.g : union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, win_post, lane);
-      if ((uint32_t)lane == j) pass = cw >= geo.rho_g;
-      if (cw >= geo.rho_g && si_next && (uint32_t)lane < geo.u)
-        atomicOr(si_next + (size_t)lane * geo.v + mycol, 1u << si_bit(coef, geo.u, aip));
+      const uint32_t cw = union_count<CellT>(re, geo.v, geo.g, geo.u, mycol, win_post, lane);
+      if (lane == j) pass = cw >= geo.rho_g;
+    }
+    if (si_next) {
+      for (unsigned pm = __ballot_sync(kFull, pass); pm; pm &= pm - 1u) {
+        const uint32_t aip = __shfl_sync(kFull, my_aip, __ffs(pm) - 1);
+        if ((uint32_t)lane < geo.u)
+          atomicOr(si_next + (size_t)lane * geo.v + (hash61(coef.a[lane], coef.b[lane], aip) & geo.vmask),
+                   1u << si_bit(coef, geo.u, aip));
+      }
     }
     // the run's carried hosts join the next slice's candidate set and list together
     int r = -2;

@@ -601,6 +601,17 @@ __device__ __forceinline__ bool host_saturated(const uint8_t* __restrict__ sat, 
   return __all_sync(kFull, s);
 }
 
+// The same test for the host `aip` of this lane alone (its u estimators' bytes, all loads in
+// flight), so that a warp tests the hosts of a whole run of candidates at once.
+__device__ __forceinline__ bool own_host_saturated(const uint8_t* __restrict__ sat, const Geo& geo, const Coef& coef,
+                                                   uint32_t aip) {
+  uint32_t all = 1u;
+#pragma unroll 4
+  for (uint32_t i = 0; i < geo.u; i++)
+    all &= __ldcg(sat + (size_t)i * geo.v + (hash61(coef.a[i], coef.b[i], aip) & geo.vmask)) != 0 ? 1u : 0u;
+  return all != 0u;
+}
+
 // ---------------------------------------------------------------- state export
 //
 // Recorder stamps -> the paper's distances (2^z - 1 = empty), at the open slice: the

@@ -105,8 +105,8 @@ def _algorithmic_bytes_per_pkt(w, tau):
 # capture of that kernel (dram__bytes_read.sum + dram__bytes_write.sum), valid only for the
 # kernel sources it was taken on.
 SCAN_TRAFFIC = {
-    "sources": "5ee1d01340d8f43b",
-    "paper-1link-u8-v16384-g128-gl256-z16-k300-5Mpps": {"bytes_per_launch": 103.843328e6 + 56.135424e6,
+    "sources": "eefb450be023508b",
+    "paper-1link-u8-v16384-g128-gl256-z16-k300-5Mpps": {"bytes_per_launch": 103.875840e6 + 56.142592e6,
                                                          "pkts": 5_000_000},
 }
 

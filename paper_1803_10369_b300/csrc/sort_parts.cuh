@@ -223,12 +223,15 @@ __device__ __forceinline__ void radix_scatter_tiles(const uint32_t* src, uint32_
     rank_tile(src, t * kSortTile, n, shift, wcnt, key, rank, valid);
     __syncthreads();
     warp_prefix(wcnt, tot);
+    // the tile's output offset of every digit, read once into shared memory (tot's tile
+    // counts are not needed here)
+    for (int d = threadIdx.x; d < kRadix; d += blockDim.x) tot[d] = hist[(size_t)d * ntiles + t];
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < 8; r++) {
       if (valid[r]) {
         const uint32_t d = (key[r] >> shift) & 0xFFu;
-        dst[hist[(size_t)d * ntiles + t] + wcnt[w][d] + rank[r]] = key[r];
+        dst[tot[d] + wcnt[w][d] + rank[r]] = key[r];
       }
     }
     __syncthreads();
